@@ -1,0 +1,248 @@
+"""FP64 CPU oracle: formal solution, Jacobi ALI and outputs (test infrastructure only).
+
+Follows Davis, Stone & Jiang (2012):
+  * ``formal_solution``  - one short-characteristics formal solution J = Lambda[S]
+    (Sec. 3.3, Eq. 25 with linear interpolation), also returning the diagonal
+    Lambda* (Sec. 3.4, Olson & Kunasz 1987) and, on request, H and K (Eqs. 23-24).
+    The sweep itself is the C function in ``sc_oracle.c``.
+  * ``init_ghosts``      - first-iteration periodic ghost intensities: I = S of the
+    periodic image cell (the paper lags incoming periodic/subdomain intensities
+    by one iteration, Sec. 3; with no previous iteration the image S is used).
+  * ``ali_solve``        - Jacobi ALI (Eq. 30):
+        dS = [(1 - eps) J + eps B - S] / [1 - (1 - eps) Lambda*],  S <- S + dS,
+    stopped when max |dS|/S <= delta_c (Eq. 31); when every eps = 1 the test uses
+    the change of J between consecutive formal solutions (Sec. 3.4).  The
+    iteration count is the number of formal solutions performed.
+  * ``heating_rate``     - Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu) (Sec. 4, Q^int).
+
+Parity: pinned by tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import build as _build
+from .quadrature import level_symmetric
+
+PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build_oracle()
+        lib = ctypes.CDLL(path)
+        d = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_formal_solution.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, ip, ip, ctypes.c_int, d, d, d, d, d, d, d, d, d, d, d, d,
+            ctypes.c_int]
+        lib.orc_formal_solution.restype = ctypes.c_int
+        lib.orc_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Grid:
+    """Uniform Cartesian grid with per-face boundary types and its angle set."""
+
+    def __init__(self, nx, ny, nz, n_mu, bc_lo=(PERIODIC, PERIODIC, THERMAL),
+                 bc_hi=(PERIODIC, PERIODIC, VACUUM), dx=1.0, dy=1.0, dz=1.0):
+        self.n = (int(nx), int(ny), int(nz))
+        self.d = (float(dx), float(dy), float(dz))
+        self.bc_lo = tuple(int(b) for b in bc_lo)
+        self.bc_hi = tuple(int(b) for b in bc_hi)
+        for a in range(3):
+            if (self.bc_lo[a] == PERIODIC) != (self.bc_hi[a] == PERIODIC):
+                raise ValueError("a periodic axis must be periodic on both faces")
+        self.two_d = self.n[2] == 1
+        self.mu, self.w = level_symmetric(n_mu, two_d=self.two_d)
+        self.na = len(self.w)
+        nx, ny, nz = self.n
+        self.face = (nz * ny, nz * nx, ny * nx)
+        self.goff = (0, self.face[0], self.face[0] + self.face[1])
+        self.gsize = sum(self.face)
+
+    @classmethod
+    def from_problem(cls, p):
+        return cls(p.nx, p.ny, p.nz, p.n_mu, p.bc_lo, p.bc_hi, p.dx, p.dy, p.dz)
+
+    @property
+    def cells(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+
+def init_ghosts(grid: Grid, S: np.ndarray) -> np.ndarray:
+    """Ghost block [na][gsize] holding S of the periodic image of each ghost vertex.
+
+    The image of the upwind ghost along axis a is the outflow cell of that axis
+    (index n_a - 1 for mu_a > 0, 0 for mu_a < 0)."""
+    S = np.asarray(S, dtype=np.float64).reshape(grid.shape)
+    G = np.zeros((grid.na, grid.gsize))
+    for k in range(grid.na):
+        for a in range(3):
+            if grid.bc_lo[a] != PERIODIC:
+                continue
+            out = grid.n[a] - 1 if grid.mu[k, a] >= 0 else 0
+            if a == 0:
+                face = S[:, :, out]          # [nz][ny]
+            elif a == 1:
+                face = S[:, out, :]          # [nz][nx]
+            else:
+                face = S[out, :, :]          # [ny][nx]
+            G[k, grid.goff[a]:grid.goff[a] + grid.face[a]] = face.ravel()
+    return G
+
+
+def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=False,
+                    nthreads=1):
+    """One formal solution for one frequency.
+
+    ``G_prev`` defaults to ``init_ghosts(grid, S)``; ``I_fixed`` is the user
+    incident-intensity array for RT_BC_FIXED faces
+    ([6][na][face cells], faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi).
+    Returns a dict with J, lstar, G_next (and H [3], K [6] when ``moments``)."""
+    lib = _load()
+    C = grid.cells
+    chi = np.ascontiguousarray(chi, dtype=np.float64).reshape(-1)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(-1)
+    B = np.ascontiguousarray(B, dtype=np.float64).reshape(-1)
+    if G_prev is None:
+        G_prev = init_ghosts(grid, S)
+    G_prev = np.ascontiguousarray(G_prev, dtype=np.float64)
+    G_next = G_prev.copy()
+    if I_fixed is not None:
+        I_fixed = np.ascontiguousarray(I_fixed, dtype=np.float64).reshape(-1)
+        need = 2 * grid.na * sum(grid.face)
+        if I_fixed.size != need:
+            raise ValueError(f"I_fixed must hold {need} values")
+    J = np.empty(C)
+    L = np.empty(C)
+    H = np.empty(3 * C) if moments else None
+    K = np.empty(6 * C) if moments else None
+    bl = (ctypes.c_int * 3)(*grid.bc_lo)
+    bh = (ctypes.c_int * 3)(*grid.bc_hi)
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    rc = lib.orc_formal_solution(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
+                                 grid.d[2], bl, bh, grid.na, _ptr(mu), _ptr(grid.w),
+                                 _ptr(chi), _ptr(S), _ptr(B), _ptr(I_fixed), _ptr(G_prev),
+                                 _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
+                                 int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle formal solution failed ({rc})")
+    out = dict(J=J.reshape(grid.shape), lstar=L.reshape(grid.shape), G_next=G_next)
+    if moments:
+        H = H.reshape((3,) + grid.shape)
+        K = K.reshape((6,) + grid.shape)
+        if grid.two_d:
+            # 2D keeps only mu_z > 0; the mirrored rays (mu_z -> -mu_z) carry the
+            # same intensity (Sec. 3.2), so moments odd in mu_z vanish.
+            H[2] = 0.0
+            K[4] = 0.0
+            K[5] = 0.0
+        out["H"] = H
+        out["K"] = K
+    return out
+
+
+def max_relative_change(dS: np.ndarray, S: np.ndarray) -> float:
+    """max_i |dS_i|/|S_i| (Eq. 31); a cell with S_i = 0 counts 0 if dS_i = 0, else inf."""
+    a = np.abs(dS)
+    s = np.abs(S)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(s > 0, a / np.where(s > 0, s, 1.0), np.where(a > 0, np.inf, 0.0))
+    return float(r.max()) if r.size else 0.0
+
+
+def heating_rate(chi, eps, J, B, freq_w):
+    """Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)  (integral form, Sec. 4)."""
+    fw = np.asarray(freq_w, dtype=np.float64).reshape((-1,) + (1,) * (np.ndim(J) - 1))
+    return 4.0 * math.pi * np.sum(fw * eps * chi * (J - B), axis=0)
+
+
+def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_init=None,
+              I_fixed=None, nthreads=1, moments=True):
+    """Jacobi ALI to max|dS|/S <= tol (Eqs. 30-31), all frequencies per iteration.
+
+    chi, eps, B: [nf][nz][ny][nx].  I_fixed: None or a list (per frequency) of
+    user boundary arrays.  Returns dict(S, J, lstar, H, K, f, Q, iters, resid,
+    converged, history); J, H, K are those of the last formal solution, S is the
+    source function after the last update."""
+    chi = np.asarray(chi, dtype=np.float64).reshape((-1,) + grid.shape)
+    eps = np.asarray(eps, dtype=np.float64).reshape(chi.shape)
+    B = np.asarray(B, dtype=np.float64).reshape(chi.shape)
+    nf = chi.shape[0]
+    fw = np.ones(nf) if freq_w is None else np.asarray(freq_w, dtype=np.float64)
+    S = B.copy() if S_init is None else np.asarray(S_init, dtype=np.float64).reshape(chi.shape).copy()
+    G = [init_ghosts(grid, S[f]) for f in range(nf)]
+    lte = bool(np.all(eps == 1.0))
+    fixed = (lambda f: None) if I_fixed is None else (lambda f: I_fixed[f])
+    lstar = np.empty_like(chi)
+    J = np.empty_like(chi)
+    J_prev = None
+    history = []
+    r = math.inf
+    it = 0
+    S_fs, G_fs = S, G
+    for it in range(1, max_iter + 1):
+        G_new = []
+        for f in range(nf):
+            res = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f), nthreads=nthreads)
+            J[f] = res["J"]
+            if it == 1:
+                lstar[f] = res["lstar"]
+            G_new.append(res["G_next"])
+        S_fs, G_fs = S, G
+        G = G_new
+        if lte:
+            r = math.inf if J_prev is None else max_relative_change(J - J_prev, J)
+        else:
+            dS = ((1.0 - eps) * J + eps * B - S) / (1.0 - (1.0 - eps) * lstar)
+            S = S + dS
+            r = max_relative_change(dS, S)
+        J_prev = J.copy()
+        history.append(r)
+        if r <= tol:
+            break
+    out = dict(S=S, J=J.copy(), lstar=lstar, iters=it, resid=r, converged=r <= tol,
+               history=history, Q=heating_rate(chi, eps, J, B, fw))
+    if moments:
+        H = np.empty((nf, 3) + grid.shape)
+        K = np.empty((nf, 6) + grid.shape)
+        for f in range(nf):
+            res = formal_solution(grid, chi[f], S_fs[f], B[f], G_fs[f], fixed(f), moments=True,
+                                  nthreads=nthreads)
+            H[f] = res["H"]
+            K[f] = res["K"]
+        out["H"] = H
+        out["K"] = K
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out["f"] = K / J[:, None]
+    return out
+
+
+def solve_problem(p, **kw):
+    """ALI solve of a ``workloads.Problem``."""
+    g = Grid.from_problem(p)
+    kw.setdefault("tol", p.tol)
+    return g, ali_solve(g, p.chi, p.eps, p.B, p.freq_w, **kw)
