@@ -1,0 +1,178 @@
+/*
+ * rt_sc.h -- C ABI of the GB300 short-characteristics radiative-transfer library.
+ *
+ * The library solves the time-independent, multi-frequency transfer equation
+ *     n . grad I_nu = chi_nu (S_nu - I_nu),   S_nu = eps_nu B_nu + (1 - eps_nu) J_nu
+ * (Davis, Stone & Jiang 2012, Eqs. 3-5) on a uniform 3D or 2D Cartesian grid with
+ *   - the short-characteristics formal solution with linear upwind-face
+ *     interpolation and exponential segment weights (Sec. 3.3, Eq. 25),
+ *   - the discrete moments J, H, K (Eqs. 22-24) and the diagonal Lambda*
+ *     (Sec. 3.4, Olson & Kunasz 1987),
+ *   - Jacobi accelerated Lambda iteration (Sec. 3.4, Eq. 30) with the
+ *     max |dS|/S convergence test (Eq. 31),
+ *   - the integral-form heating rate and the Eddington tensor K/J (Sec. 4).
+ *
+ * Conventions shared by every call:
+ *   - Status codes, never exceptions.  On failure rt_last_error() describes why.
+ *   - Cell arrays are float64, C order [nf][nz][ny][nx] (x fastest).
+ *   - Inputs are copied in; the caller keeps ownership of its pointers and
+ *     allocates every output buffer.  The library owns all device state of a grid.
+ *   - on_device = 0: pointers are host memory.  on_device = 1: pointers are device
+ *     memory on the grid's device, read/written on the call's stream.
+ *   - Calls that return host scalars (iteration counts, residuals) or write host
+ *     buffers synchronise the stream before returning.
+ *   - A grid is not thread-safe: one host thread at a time per grid.
+ *   - All compute runs in the library's CUDA kernels; there is no CPU fallback.
+ */
+#ifndef RT_SC_H
+#define RT_SC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_grid_s *rt_grid;   /* opaque handle; owns all device state */
+
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_ARG = -1,            /* invalid argument or input value */
+  RT_ERR_OOM = -2,            /* device allocation failed */
+  RT_ERR_CUDA = -3,           /* a CUDA call failed (message has the CUDA error) */
+  RT_ERR_NOT_CONVERGED = -4,  /* max_iter formal solutions without meeting tol */
+  RT_ERR_TIMEOUT = -5,        /* reserved: a bounded device-side wait gave up */
+  RT_ERR_STATE = -6           /* call out of order (e.g. solve before set_opacity_source) */
+} rt_status;
+
+/* Boundary type of one face (Sec. 3.5).
+ *   PERIODIC: incoming intensity is the outgoing intensity of the opposite face
+ *             from the previous formal solution (lagged by one iteration);
+ *             both faces of an axis must be periodic together.
+ *   VACUUM:   no incoming intensity.
+ *   THERMAL:  incoming intensity I = B of the adjacent boundary layer.
+ *   FIXED:    incoming intensity given per angle with rt_set_boundary_intensity.
+ * At every non-periodic face the ghost opacity and source function copy the
+ * adjacent boundary layer. */
+typedef enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_THERMAL = 2, RT_BC_FIXED = 3 } rt_bc;
+
+/* Arithmetic of the formal solution.
+ *   FP64:  everything in double precision.
+ *   MIXED: the sweep (interpolation, segment weights, intensities, the per-sweep
+ *          angle sums) in float32 with a Taylor form of the segment weights for
+ *          small optical depth; J summed across sweeps, Lambda*, the ALI update,
+ *          its denominator and the convergence test in double precision. */
+typedef enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 } rt_precision;
+
+typedef struct {
+  int nx, ny, nz;        /* cells per axis; nz == 1 selects 2D (z-invariant) */
+  double dx, dy, dz;     /* cell spacing (dz ignored in 2D) */
+  int n_mu;              /* polar angles: 2, 4, 6, 8, 10 or 12 -> n_mu (n_mu + 2) rays (half in 2D) */
+  int nfreq;             /* independent frequency bins, >= 1 */
+  rt_bc bc_lo[3];        /* boundary of the low face of x, y, z */
+  rt_bc bc_hi[3];        /* boundary of the high face of x, y, z */
+  rt_precision prec;
+} rt_grid_desc;
+
+typedef struct {
+  double tol;            /* delta_c of Eq. 31 (e.g. 1e-6) */
+  int max_iter;          /* maximum formal solutions per solve */
+  int check_every;       /* formal solutions enqueued between host checks; 0 = automatic */
+  void *stream;          /* cudaStream_t to run on; NULL = the grid's own stream */
+} rt_solve_opts;
+
+/* Create a grid on the current CUDA device.  Builds the level-symmetric angle set
+ * (Sec. 3.2) and allocates device state sized by desc.  *out is set on success.
+ * Errors: RT_ERR_ARG (bad sizes, n_mu, or a half-periodic axis), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out);
+
+/* Release all device state of a grid.  NULL is accepted. */
+rt_status rt_destroy_grid(rt_grid g);
+
+/* Number of rays and the angle table: mu [n_angles][3] (direction cosines) and
+ * w [n_angles] (weights, sum 1; Eq. 22 carries no 4 pi).  Either pointer may be
+ * NULL.  Order: octant o = 0..7 with signs (-1 if o&1, -1 if o&2, -1 if o&4) for
+ * (x, y, z), in 2D only the octants with mu_z > 0 (weights doubled); within an
+ * octant level indices i outer, j inner, l = n_mu/2 + 2 - i - j. */
+int rt_num_angles(rt_grid g);
+rt_status rt_get_angles(rt_grid g, double *mu, double *w);
+
+/* The same angle table without a grid (host only, no GPU needed): writes
+ * n_angles rows into mu [n][3] and w [n] when they are non-NULL and returns
+ * n_angles, or a negative rt_status for an unsupported n_mu.  Sec. 3.2. */
+int rt_angle_table(int n_mu, int two_d, double *mu, double *w);
+
+/* Set the medium (Sec. 2, step 1): total opacity chi_tot >= 0, photon destruction
+ * probability 0 < eps <= 1, thermal source function B >= 0, all [nf][nz][ny][nx],
+ * and the frequency quadrature weights freq_w [nf] used by the heating rate
+ * (NULL = all 1).  No NaN/Inf allowed.  Copies the inputs, computes Lambda*
+ * (depends on chi only) and resets S to B and the periodic ghosts to the image
+ * cells' S.  Errors: RT_ERR_ARG for out-of-range or non-finite values. */
+rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *eps,
+                                const double *B, const double *freq_w, int on_device);
+
+/* Incident intensity for a face declared RT_BC_FIXED.  face = 2*axis + side
+ * (0 x-lo, 1 x-hi, 2 y-lo, 3 y-hi, 4 z-lo, 5 z-hi).  I is
+ * [nf][n_angles][face cells], face cells ordered x-face [nz][ny], y-face [nz][nx],
+ * z-face [ny][nx]; only rays entering through the face are used.  Values are
+ * used for the ghost vertex just outside each face cell (and, at edges and
+ * corners, for the ghost whose first non-periodic out-of-range axis in the order
+ * z, y, x is this face's).  Host pointer.  Errors: RT_ERR_ARG, RT_ERR_STATE if
+ * the face is not RT_BC_FIXED. */
+rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I);
+
+/* One formal solution J = Lambda[S] (Sec. 3.4, Eq. 26) without an S update.
+ * S: [nf][nz][ny][nx] or NULL to use the grid's current S; when S is given the
+ * periodic ghosts are reset to the image cells' S (first-iteration semantics),
+ * otherwise the lagged ghosts of the previous formal solution are used and
+ * advanced.  J_out, lstar_out: [nf][nz][ny][nx] or NULL.  opts may be NULL.
+ * Errors: RT_ERR_STATE before rt_set_opacity_source. */
+rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out,
+                          int on_device, const rt_solve_opts *opts);
+
+/* Jacobi ALI to max|dS|/S <= opts->tol (Eqs. 30-31).  S_init [nf][nz][ny][nx]
+ * (device or host per on_device) or NULL to start from S = B.  Periodic ghosts
+ * start as the image cells' S.  When every eps == 1 the stopping test uses the
+ * change of J between consecutive formal solutions.  iters_out: formal
+ * solutions performed; resid_out: the last max relative change.  Returns
+ * RT_ERR_NOT_CONVERGED (state kept) if max_iter is reached first. */
+rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
+                       int *iters_out, double *resid_out);
+
+/* Outputs of the last formal solution of the latest solve (Sec. 4): J [nf][cells],
+ * H [nf][3][cells], K [nf][6][cells] (xx, yy, zz, xy, xz, yz), the variable
+ * Eddington tensor f = K/J [nf][6][cells], and the heating rate
+ * Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu) [cells].  Any pointer may be NULL.
+ * Recomputes that formal solution with moment accumulation.
+ * Errors: RT_ERR_STATE if no formal solution has run. */
+rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, double *Q,
+                     int on_device, const rt_solve_opts *opts);
+
+/* Current source function S [nf][nz][ny][nx]. */
+rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts);
+
+/* Device-time record of the latest rt_ali_solve / rt_formal_solve call, taken
+ * with CUDA events on the launching stream when enabled.  sweep_ms: summed
+ * duration of the formal-solution kernel launches; sweep_launches: how many;
+ * total_ms: the whole solve; kernel_launches: all kernels the library launched. */
+typedef struct {
+  int iters;
+  double resid;
+  double sweep_ms;
+  int sweep_launches;
+  double total_ms;
+  long long kernel_launches;
+  long long updates;       /* cell * ray * frequency updates performed */
+} rt_stats;
+rt_status rt_enable_timing(rt_grid g, int enable);
+rt_status rt_get_stats(rt_grid g, rt_stats *out);
+
+/* Tuning of the sweep launch (0 = automatic): angles per sweep group and CTAs per
+ * thread-block cluster along the plane. */
+rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads);
+
+/* Message describing the last error on this thread (never NULL). */
+const char *rt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_SC_H */

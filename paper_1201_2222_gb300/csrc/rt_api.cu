@@ -1,0 +1,1021 @@
+// Host side of the C ABI declared in include/rt_sc.h.
+//
+// Owns the grid's device state, builds the angle quadrature and the sweep
+// groups, and enqueues the kernels of rt_kernels.cu.  Every numerical step runs
+// on the GPU; this file only plans, allocates, copies and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "rt_common.cuh"
+#include "rt_kernels.h"
+#include "rt_sc.h"
+
+using rtk::AngleParam;
+using rtk::GroupParam;
+using rtk::RayGeom;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+rt_status fail(rt_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA,         \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// ------------------------------------------------------------------ quadrature
+// Level-symmetric LQ_n set (Sec. 3.2 constraints: octant-identical, invariant under
+// 90-degree rotations).  Levels mu_i^2 = a + (i-1) 2(1-3a)/(n_mu-2); octant nodes
+// (i, j, l) with i + j + l = n_mu/2 + 2; permutation classes share a weight; a and
+// the class weights satisfy sum w = 1 and sum w mu_z^(2p) = 1/(2p+1),
+// p = 2 .. n_classes + 1 (one more equation than weights: a is where they agree).
+
+struct LQSystem {
+  int nc;
+  std::vector<std::array<int, 3>> nodes;
+  std::vector<int> node_class;
+};
+
+LQSystem lq_structure(int n_mu) {
+  LQSystem s;
+  const int half = n_mu / 2;
+  std::vector<std::array<int, 3>> classes;
+  for (int i = 1; i <= half; ++i)
+    for (int j = 1; j <= half; ++j) {
+      const int l = half + 2 - i - j;
+      if (l >= 1) s.nodes.push_back({i, j, l});
+    }
+  for (auto n : s.nodes) {
+    std::array<int, 3> c = n;
+    std::sort(c.begin(), c.end());
+    if (std::find(classes.begin(), classes.end(), c) == classes.end()) classes.push_back(c);
+  }
+  std::sort(classes.begin(), classes.end());
+  for (auto n : s.nodes) {
+    std::array<int, 3> c = n;
+    std::sort(c.begin(), c.end());
+    s.node_class.push_back((int)(std::find(classes.begin(), classes.end(), c) - classes.begin()));
+  }
+  s.nc = (int)classes.size();
+  return s;
+}
+
+// rows: [count | moments p = 2..nc+1], columns: classes, plus the right-hand side
+void lq_rows(const LQSystem &s, int n_mu, double a, std::vector<double> &M, std::vector<double> &b) {
+  const int nc = s.nc, half = n_mu / 2;
+  std::vector<double> mu2(half);
+  for (int i = 0; i < half; ++i) mu2[i] = a + i * 2.0 * (1.0 - 3.0 * a) / (n_mu - 2);
+  M.assign((nc + 1) * nc, 0.0);
+  b.assign(nc + 1, 0.0);
+  for (size_t q = 0; q < s.nodes.size(); ++q) {
+    const int c = s.node_class[q];
+    M[0 * nc + c] += 1.0;
+    for (int p = 2; p <= nc + 1; ++p) M[(p - 1) * nc + c] += std::pow(mu2[s.nodes[q][2] - 1], p);
+  }
+  b[0] = 1.0;
+  for (int p = 2; p <= nc + 1; ++p) b[p - 1] = 1.0 / (2 * p + 1);
+}
+
+// determinant (and optional solve) by Gaussian elimination with partial pivoting
+double gauss(std::vector<double> A, int n, std::vector<double> *rhs) {
+  double det = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[piv * n + k])) piv = i;
+    if (A[piv * n + k] == 0.0) return 0.0;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+      if (rhs) std::swap((*rhs)[k], (*rhs)[piv]);
+      det = -det;
+    }
+    det *= A[k * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      const double m = A[i * n + k] / A[k * n + k];
+      for (int j = k; j < n; ++j) A[i * n + j] -= m * A[k * n + j];
+      if (rhs) (*rhs)[i] -= m * (*rhs)[k];
+    }
+  }
+  if (rhs) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = (*rhs)[i];
+      for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * (*rhs)[j];
+      (*rhs)[i] = s / A[i * n + i];
+    }
+  }
+  return det;
+}
+
+double lq_consistency(const LQSystem &s, int n_mu, double a) {
+  std::vector<double> M, b;
+  lq_rows(s, n_mu, a, M, b);
+  const int n = s.nc + 1;
+  std::vector<double> Aug(n * n);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < s.nc; ++j) Aug[i * n + j] = M[i * s.nc + j];
+    Aug[i * n + s.nc] = b[i];
+  }
+  return gauss(Aug, n, nullptr);
+}
+
+// weights at a consistent a: the square subsystem (one row dropped) with the largest |det|
+bool lq_weights(const LQSystem &s, int n_mu, double a, std::vector<double> &w) {
+  std::vector<double> M, b;
+  lq_rows(s, n_mu, a, M, b);
+  const int nc = s.nc;
+  double best = -1.0;
+  for (int drop = 0; drop <= nc; ++drop) {
+    std::vector<double> A, r;
+    for (int i = 0; i <= nc; ++i) {
+      if (i == drop) continue;
+      for (int j = 0; j < nc; ++j) A.push_back(M[i * nc + j]);
+      r.push_back(b[i]);
+    }
+    const double d = std::fabs(gauss(A, nc, nullptr));
+    if (d > best) {
+      best = d;
+      gauss(A, nc, &r);
+      w = r;
+    }
+  }
+  for (int i = 0; i <= nc; ++i) {
+    double s2 = 0.0;
+    for (int j = 0; j < nc; ++j) s2 += M[i * nc + j] * w[j];
+    if (std::fabs(s2 - b[i]) > 1e-12) return false;
+  }
+  for (double x : w)
+    if (!(x > 0.0)) return false;
+  return true;
+}
+
+bool level_symmetric(int n_mu, bool two_d, std::vector<double> &mu, std::vector<double> &wq) {
+  std::vector<std::array<double, 3>> omu;
+  std::vector<double> ow;
+  if (n_mu == 2) {
+    const double m = 1.0 / std::sqrt(3.0);
+    omu.push_back({m, m, m});
+    ow.push_back(1.0);
+  } else {
+    if (n_mu < 4 || n_mu > 12 || (n_mu & 1)) return false;
+    const LQSystem s = lq_structure(n_mu);
+    const int nscan = 4001;
+    const double lo = 1e-6, hi = 1.0 / 3.0 - 1e-6;
+    double a_prev = lo, f_prev = lq_consistency(s, n_mu, lo);
+    bool found = false;
+    double a_root = 0.0;
+    std::vector<double> wcls;
+    for (int k = 1; k < nscan && !found; ++k) {
+      const double a = lo + (hi - lo) * k / (nscan - 1);
+      const double fa = lq_consistency(s, n_mu, a);
+      if (f_prev == 0.0 || f_prev * fa < 0.0) {
+        double x0 = a_prev, x1 = a, f0 = f_prev;
+        for (int it = 0; it < 200 && x1 - x0 > 0.0; ++it) {
+          const double xm = 0.5 * (x0 + x1);
+          if (xm <= x0 || xm >= x1) break;
+          const double fm = lq_consistency(s, n_mu, xm);
+          if ((fm < 0) == (f0 < 0) && fm != 0.0) { x0 = xm; f0 = fm; }
+          else x1 = xm;
+        }
+        const double r = f0 == 0.0 ? x0 : 0.5 * (x0 + x1);
+        std::vector<double> w;
+        if (lq_weights(s, n_mu, r, w)) {
+          bool pos = true;
+          for (int i = 0; i < n_mu / 2; ++i)
+            if (!(r + i * 2.0 * (1.0 - 3.0 * r) / (n_mu - 2) > 0.0)) pos = false;
+          if (pos) { found = true; a_root = r; wcls = w; }
+        }
+      }
+      a_prev = a;
+      f_prev = fa;
+    }
+    if (!found) return false;
+    const int half = n_mu / 2;
+    std::vector<double> lev(half);
+    for (int i = 0; i < half; ++i) lev[i] = std::sqrt(a_root + i * 2.0 * (1.0 - 3.0 * a_root) / (n_mu - 2));
+    for (size_t q = 0; q < s.nodes.size(); ++q) {
+      omu.push_back({lev[s.nodes[q][0] - 1], lev[s.nodes[q][1] - 1], lev[s.nodes[q][2] - 1]});
+      ow.push_back(wcls[s.node_class[q]]);
+    }
+  }
+  mu.clear();
+  wq.clear();
+  for (int o = 0; o < 8; ++o) {
+    const double sx = (o & 1) ? -1.0 : 1.0, sy = (o & 2) ? -1.0 : 1.0, sz = (o & 4) ? -1.0 : 1.0;
+    if (two_d && sz < 0) continue;
+    for (size_t q = 0; q < omu.size(); ++q) {
+      mu.push_back(sx * omu[q][0]);
+      mu.push_back(sy * omu[q][1]);
+      mu.push_back(sz * omu[q][2]);
+      wq.push_back(ow[q] / 8.0 * (two_d ? 2.0 : 1.0));
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ grid
+
+struct rt_grid_s {
+  rt_grid_desc desc{};
+  int device = 0;
+  rtk::Dims d{};
+  bool two_d = false;
+  int na = 0;
+  std::vector<double> mu, wq;
+  std::vector<RayGeom> rays;
+  int used_axis[3] = {0, 0, 0};
+  size_t tsize = 8;
+
+  // sweep plan
+  int apg = 0, amax = 1, cluster = 1, threads = 256;
+  size_t smem = 0;
+  int req_apg = 0, req_cluster = 0, req_threads = 0;
+  std::vector<GroupParam> groups;
+  std::vector<int> group_angles;   // angle index per AngleParam slot
+
+  // device buffers
+  double *chi = nullptr, *eps = nullptr, *B = nullptr, *fw = nullptr;
+  double *S = nullptr, *Sfs = nullptr, *J = nullptr, *Jprev = nullptr;
+  double *lstar = nullptr, *oml = nullptr;
+  void *chiP[3] = {nullptr, nullptr, nullptr};
+  void *SP[3] = {nullptr, nullptr, nullptr};
+  void *G[2] = {nullptr, nullptr};
+  void *Ibc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *user_bc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void *Jpart = nullptr;
+  size_t jpart_groups = 0;
+  void *Mpart = nullptr;
+  size_t mpart_groups = 0;
+  void *angp = nullptr;
+  GroupParam *grp = nullptr;
+  RayGeom *rays_d = nullptr;
+  rtk::SolveState *st = nullptr;
+  int *counts = nullptr;
+  double *tmp = nullptr;           // scratch for host-side outputs
+  size_t tmp_n = 0;
+  cudaStream_t own = nullptr;
+
+  bool have_medium = false;
+  bool lte = false;
+  int fs_total = 0;                // formal solutions since the ghosts were initialised
+  bool last_fs_from_Sfs = false;   // the latest formal solution used Sfs (ALI) or S
+
+  bool timing = false;
+  rt_stats stats{};
+  long long launches = 0;
+};
+
+namespace {
+
+cudaStream_t pick_stream(rt_grid g, const rt_solve_opts *o) {
+  return (o && o->stream) ? (cudaStream_t)o->stream : g->own;
+}
+
+long long N_of(rt_grid g) { return g->d.cells * g->d.nf; }
+
+void build_rays(rt_grid g) {
+  const double *dd = &g->desc.dx;
+  int count[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  g->rays.resize(g->na);
+  for (int k = 0; k < g->na; ++k) {
+    RayGeom r{};
+    const double *m = &g->mu[3 * k];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+      r.sgn[a] = m[a] >= 0.0 ? 1 : -1;
+      t[a] = (a == 2 && g->two_d) ? std::numeric_limits<double>::infinity() : dd[a] / std::fabs(m[a]);
+    }
+    const double tmin = std::min(t[0], std::min(t[1], t[2]));
+    // first-crossed face; a tie (the ray leaves through an edge) gives identical
+    // interpolants on either face, so tied rays go to the least-loaded sweep group
+    int best = -1;
+    for (int a = 2; a >= 0; --a) {
+      if (t[a] != tmin) continue;
+      const int sd = r.sgn[a] > 0 ? 0 : 1;
+      if (best < 0 || count[a][sd] < count[best][r.sgn[best] > 0 ? 0 : 1]) best = a;
+    }
+    r.axis = best;
+    r.s = t[best];
+    r.w = g->wq[k];
+    for (int a = 0; a < 3; ++a) {
+      if (a == best) r.frac[a] = 1.0;
+      else if (a == 2 && g->two_d) r.frac[a] = 0.0;
+      else r.frac[a] = std::min(1.0, r.s * std::fabs(m[a]) / dd[a]);
+    }
+    count[best][r.sgn[best] > 0 ? 0 : 1]++;
+    g->used_axis[best] = 1;
+    g->rays[k] = r;
+  }
+}
+
+// Largest dynamic shared memory a sweep CTA may use.
+constexpr size_t kSweepSmemBudget = 200 * 1024;
+
+size_t sweep_smem(rt_grid g, int amax, int C) {
+  size_t s = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (!g->used_axis[a]) continue;
+    int cax[3];
+    rtk::plane_axes(a, cax);
+    const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
+    s = std::max(s, (size_t)2 * amax * Rmax * g->d.n[cax[0]] * g->tsize);
+  }
+  return s;
+}
+
+int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)); }
+
+void plan_groups(rt_grid g) {
+  std::vector<int> per_key[6];
+  for (int k = 0; k < g->na; ++k) {
+    const RayGeom &r = g->rays[k];
+    per_key[2 * r.axis + (r.sgn[r.axis] > 0 ? 0 : 1)].push_back(k);
+  }
+  int nmax = 1;
+  for (auto &v : per_key) nmax = std::max(nmax, (int)v.size());
+  int minNv = 1 << 30;
+  for (int a = 0; a < 3; ++a) {
+    if (!g->used_axis[a]) continue;
+    int cax[3];
+    rtk::plane_axes(a, cax);
+    minNv = std::min(minNv, g->d.n[cax[1]]);
+  }
+  const int Cmax = std::min(16, minNv);
+  int apg = g->req_apg > 0 ? g->req_apg : 4;
+  apg = std::min(std::max(apg, 1), 8);
+  apg = std::min(apg, nmax);
+  // fewer rays per group when even the largest cluster cannot hold the planes
+  while (apg > 1 && sweep_smem(g, amax_for(apg), Cmax) > kSweepSmemBudget) apg = (apg + 1) / 2;
+  g->apg = apg;
+  g->amax = amax_for(apg);
+  g->groups.clear();
+  g->group_angles.clear();
+  for (int key = 0; key < 6; ++key) {
+    const auto &v = per_key[key];
+    if (v.empty()) continue;
+    const int nchunk = ((int)v.size() + apg - 1) / apg;
+    size_t pos = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      const int sz = (int)(v.size() - pos) / (nchunk - c);
+      GroupParam gp{};
+      gp.axis = key / 2;
+      gp.sa = (key % 2) ? -1 : 1;
+      gp.a0 = (int)g->group_angles.size();
+      gp.na = sz;
+      for (int q = 0; q < sz; ++q) g->group_angles.push_back(v[pos + q]);
+      pos += sz;
+      g->groups.push_back(gp);
+    }
+  }
+  // strips per plane: enough CTAs to cover the GPU twice, within the shared-memory budget
+  const long long inst = (long long)g->groups.size() * g->d.nf;
+  int C = g->req_cluster > 0 ? g->req_cluster : (int)std::max(1LL, (2 * 152 + inst - 1) / inst);
+  if (g->req_cluster <= 0) C = std::min(C, 8);
+  C = std::max(1, std::min(C, Cmax));
+  while (sweep_smem(g, g->amax, C) > kSweepSmemBudget && C < Cmax) ++C;
+  g->cluster = C;
+  g->smem = sweep_smem(g, g->amax, C);
+  size_t cells_strip = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (!g->used_axis[a]) continue;
+    int cax[3];
+    rtk::plane_axes(a, cax);
+    const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
+    cells_strip = std::max(cells_strip, (size_t)Rmax * g->d.n[cax[0]]);
+  }
+  int th = g->req_threads > 0 ? g->req_threads : (int)std::min<size_t>(512, ((cells_strip + 31) / 32) * 32);
+  g->threads = std::max(32, std::min(512, th));
+}
+
+template <typename T>
+rt_status upload_plan(rt_grid g) {
+  std::vector<AngleParam<T>> ap(g->group_angles.size());
+  for (size_t gi = 0; gi < g->groups.size(); ++gi) {
+    const GroupParam &gp = g->groups[gi];
+    int cax[3];
+    rtk::plane_axes(gp.axis, cax);
+    for (int q = 0; q < gp.na; ++q) {
+      const int k = g->group_angles[gp.a0 + q];
+      const RayGeom &r = g->rays[k];
+      const double fu = r.frac[cax[0]], fv = r.frac[cax[1]];
+      AngleParam<T> p{};
+      p.wq = (T)r.w;
+      p.hs = (T)(0.5 * r.s);
+      p.wa = (T)((1.0 - fu) * (1.0 - fv));
+      p.wb = (T)(fu * (1.0 - fv));
+      p.wc = (T)((1.0 - fu) * fv);
+      p.wd = (T)(fu * fv);
+      for (int a = 0; a < 3; ++a) p.mu[a] = (T)g->mu[3 * k + a];
+      p.su = r.sgn[cax[0]];
+      p.sv = r.sgn[cax[1]];
+      p.angle = k;
+      ap[gp.a0 + q] = p;
+    }
+  }
+  if (g->angp) cudaFree(g->angp);
+  if (g->grp) cudaFree(g->grp);
+  g->angp = nullptr;
+  g->grp = nullptr;
+  CU(cudaMalloc(&g->angp, std::max<size_t>(1, ap.size()) * sizeof(AngleParam<T>)));
+  CU(cudaMalloc((void **)&g->grp, std::max<size_t>(1, g->groups.size()) * sizeof(GroupParam)));
+  CU(cudaMemcpy(g->angp, ap.data(), ap.size() * sizeof(AngleParam<T>), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(g->grp, g->groups.data(), g->groups.size() * sizeof(GroupParam), cudaMemcpyHostToDevice));
+  const size_t need = g->groups.size();
+  if (need > g->jpart_groups) {
+    if (g->Jpart) cudaFree(g->Jpart);
+    g->Jpart = nullptr;
+    CU(cudaMalloc(&g->Jpart, need * (size_t)N_of(g) * sizeof(T)));
+    g->jpart_groups = need;
+  }
+  return RT_OK;
+}
+
+rt_status upload_plan_any(rt_grid g) {
+  return g->desc.prec == RT_PREC_FP64 ? upload_plan<double>(g) : upload_plan<float>(g);
+}
+
+rt_status ensure_tmp(rt_grid g, size_t n) {
+  if (n <= g->tmp_n) return RT_OK;
+  if (g->tmp) cudaFree(g->tmp);
+  g->tmp = nullptr;
+  g->tmp_n = 0;
+  CU(cudaMalloc((void **)&g->tmp, n * sizeof(double)));
+  g->tmp_n = n;
+  return RT_OK;
+}
+
+rt_status copy_in(rt_grid g, double *dst, const double *src, size_t n, int on_device, cudaStream_t s) {
+  CU(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  (void)g;
+  return RT_OK;
+}
+
+rt_status copy_out(double *dst, const double *src, size_t n, int on_device, cudaStream_t s) {
+  CU(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  return RT_OK;
+}
+
+template <typename T>
+rt_status permute_into(rt_grid g, const double *src, void *const dst[3], cudaStream_t s) {
+  T *d0 = g->used_axis[0] ? (T *)dst[0] : nullptr;
+  T *d1 = g->used_axis[1] ? (T *)dst[1] : nullptr;
+  T *d2 = g->used_axis[2] ? (T *)dst[2] : nullptr;
+  CU(rtk::launch_permute<T>(g->d, src, d0, d1, d2, s));
+  g->launches++;
+  return RT_OK;
+}
+
+rt_status permute_any(rt_grid g, const double *src, void *const dst[3], cudaStream_t s) {
+  return g->desc.prec == RT_PREC_FP64 ? permute_into<double>(g, src, dst, s)
+                                      : permute_into<float>(g, src, dst, s);
+}
+
+template <typename T>
+rt_status init_ghosts(rt_grid g, const double *S, cudaStream_t s) {
+  CU(rtk::launch_init_ghosts<T>(g->d, g->na, g->rays_d, S, (T *)g->G[0], s));
+  CU(rtk::launch_state_op(g->st, 2, 0, 0.0, 0, s));
+  g->launches += 2;
+  g->fs_total = 0;
+  return RT_OK;
+}
+
+rt_status init_ghosts_any(rt_grid g, const double *S, cudaStream_t s) {
+  return g->desc.prec == RT_PREC_FP64 ? init_ghosts<double>(g, S, s) : init_ghosts<float>(g, S, s);
+}
+
+template <typename T>
+rt_status fill_bc(rt_grid g, int face, cudaStream_t s) {
+  const int ax = face / 2, side = face % 2;
+  const int bc = side ? g->desc.bc_hi[ax] : g->desc.bc_lo[ax];
+  if (g->d.periodic[ax]) return RT_OK;
+  CU(rtk::launch_fill_bc<T>(g->d, g->na, face, bc, g->B, g->user_bc[face], (T *)g->Ibc[face], s));
+  g->launches++;
+  return RT_OK;
+}
+
+rt_status fill_bc_any(rt_grid g, int face, cudaStream_t s) {
+  return g->desc.prec == RT_PREC_FP64 ? fill_bc<double>(g, face, s) : fill_bc<float>(g, face, s);
+}
+
+template <typename T>
+rtk::SweepArgs<T> sweep_args(rt_grid g) {
+  rtk::SweepArgs<T> A{};
+  A.d = g->d;
+  A.na = g->na;
+  for (int a = 0; a < 3; ++a) {
+    A.chiP[a] = (const T *)g->chiP[a];
+    A.SP[a] = (const T *)g->SP[a];
+  }
+  A.G[0] = (T *)g->G[0];
+  A.G[1] = (T *)g->G[1];
+  for (int f = 0; f < 6; ++f) A.Ibc[f] = (const T *)g->Ibc[f];
+  A.ang = (const AngleParam<T> *)g->angp;
+  A.grp = g->grp;
+  A.ngroups = (int)g->groups.size();
+  A.Jpart = (T *)g->Jpart;
+  A.Mpart = (T *)g->Mpart;
+  A.st = g->st;
+  A.parity_offset = 0;
+  A.write_ghosts = 1;
+  A.skip_if_done = 1;
+  A.cluster = g->cluster;
+  return A;
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+template <typename T>
+rt_status enqueue_sweep(rt_grid g, rtk::SweepArgs<T> &A, bool moments, cudaStream_t s,
+                        std::vector<EventPair> *ev) {
+  EventPair p;
+  if (ev) {
+    CU(cudaEventCreate(&p.a));
+    CU(cudaEventCreate(&p.b));
+    CU(cudaEventRecord(p.a, s));
+  }
+  CU(rtk::launch_sweep<T>(A, g->amax, moments, g->threads, g->smem, s));
+  g->launches++;
+  if (ev) {
+    CU(cudaEventRecord(p.b, s));
+    ev->push_back(p);
+  }
+  return RT_OK;
+}
+
+rt_status collect_events(std::vector<EventPair> &ev, double *ms_out, int *n_out) {
+  double ms = 0.0;
+  for (auto &p : ev) {
+    float t = 0.0f;
+    CU(cudaEventElapsedTime(&t, p.a, p.b));
+    ms += t;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  *ms_out = ms;
+  *n_out = (int)ev.size();
+  ev.clear();
+  return RT_OK;
+}
+
+template <typename T>
+rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *iters, double *resid,
+                   bool *converged) {
+  const double tol = opts ? opts->tol : 1e-6;
+  const int max_iter = opts && opts->max_iter > 0 ? opts->max_iter : 1000;
+  CU(rtk::launch_state_op(g->st, 0, max_iter, tol, g->lte ? 1 : 0, s));
+  g->launches++;
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  rtk::AliArgs<T> L{};
+  L.d = g->d;
+  L.ngroups_per_f = (int)g->groups.size();
+  L.Jpart = (const T *)g->Jpart;
+  L.eps = g->eps;
+  L.B = g->B;
+  L.oml = g->oml;
+  L.S64 = g->S;
+  L.Sfs = g->Sfs;
+  L.J64 = g->J;
+  L.Jprev = g->Jprev;
+  for (int a = 0; a < 3; ++a) L.SP[a] = g->used_axis[a] ? (T *)g->SP[a] : nullptr;
+  L.st = g->st;
+  L.lte = g->lte ? 1 : 0;
+  std::vector<EventPair> ev;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (g->timing) {
+    CU(cudaEventCreate(&t0));
+    CU(cudaEventCreate(&t1));
+    CU(cudaEventRecord(t0, s));
+  }
+  int enqueued = 0, batch = opts && opts->check_every > 0 ? opts->check_every : 4;
+  rtk::SolveState hs{};
+  while (true) {
+    const int m = std::min(batch, max_iter - enqueued);
+    for (int i = 0; i < m; ++i) {
+      rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
+      if (r != RT_OK) return r;
+      CU(rtk::launch_ali<T>(L, s));
+      CU(rtk::launch_finish(g->st, s));
+      g->launches += 2;
+    }
+    enqueued += m;
+    CU(cudaMemcpyAsync(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hs.err) return fail(RT_ERR_CUDA, "device bounds check failed (code %d, index %d)", hs.err, hs.err_info);
+    if (hs.done || enqueued >= max_iter) break;
+    if (!(opts && opts->check_every > 0)) batch = std::min(batch * 2, 64);
+  }
+  if (g->timing) {
+    CU(cudaEventRecord(t1, s));
+    CU(cudaEventSynchronize(t1));
+    float tt = 0.0f;
+    CU(cudaEventElapsedTime(&tt, t0, t1));
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    g->stats.total_ms = tt;
+    rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches);
+    if (r != RT_OK) return r;
+  }
+  *iters = hs.iter;
+  *resid = hs.last_resid;
+  *converged = hs.converged != 0;
+  g->fs_total = hs.fs_count;
+  g->last_fs_from_Sfs = !g->lte;
+  return RT_OK;
+}
+
+template <typename T>
+rt_status formal_once(rt_grid g, cudaStream_t s) {
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  A.skip_if_done = 0;
+  std::vector<EventPair> ev;
+  rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
+  if (r != RT_OK) return r;
+  CU(rtk::launch_reduce_J<T>(g->d, (int)g->groups.size(), (const T *)g->Jpart, g->J, s));
+  CU(rtk::launch_state_op(g->st, 1, 0, 0.0, 0, s));
+  g->launches += 2;
+  if (g->timing) {
+    CU(cudaStreamSynchronize(s));
+    r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches);
+    if (r != RT_OK) return r;
+    g->stats.total_ms = g->stats.sweep_ms;
+  }
+  g->fs_total += 1;
+  g->last_fs_from_Sfs = false;
+  return RT_OK;
+}
+
+template <typename T>
+rt_status moments_sweep(rt_grid g, cudaStream_t s) {
+  const size_t need = g->groups.size();
+  if (need > g->mpart_groups) {
+    if (g->Mpart) cudaFree(g->Mpart);
+    g->Mpart = nullptr;
+    CU(cudaMalloc(&g->Mpart, need * 9 * (size_t)N_of(g) * sizeof(T)));
+    g->mpart_groups = need;
+  }
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  A.parity_offset = -1;
+  A.write_ghosts = 0;
+  A.skip_if_done = 0;
+  return enqueue_sweep<T>(g, A, true, s, nullptr);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_err.c_str(); }
+
+rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
+  if (!desc || !out) return fail(RT_ERR_ARG, "rt_create_grid: NULL argument");
+  *out = nullptr;
+  const rt_grid_desc &D = *desc;
+  if (D.nx < 1 || D.ny < 1 || D.nz < 1 || D.nfreq < 1)
+    return fail(RT_ERR_ARG, "grid sizes and nfreq must be >= 1");
+  if (!(D.dx > 0) || !(D.dy > 0) || (D.nz > 1 && !(D.dz > 0)))
+    return fail(RT_ERR_ARG, "cell spacings must be > 0");
+  if (D.prec != RT_PREC_FP64 && D.prec != RT_PREC_MIXED) return fail(RT_ERR_ARG, "bad precision");
+  for (int a = 0; a < 3; ++a) {
+    if (D.bc_lo[a] < 0 || D.bc_lo[a] > 3 || D.bc_hi[a] < 0 || D.bc_hi[a] > 3)
+      return fail(RT_ERR_ARG, "bad boundary type on axis %d", a);
+    if (a < 2 || D.nz > 1)
+      if ((D.bc_lo[a] == RT_BC_PERIODIC) != (D.bc_hi[a] == RT_BC_PERIODIC))
+        return fail(RT_ERR_ARG, "axis %d: a periodic axis must be periodic on both faces", a);
+  }
+  rt_grid g = new rt_grid_s();
+  g->desc = D;
+  g->two_d = D.nz == 1;
+  if (g->two_d) {   // z-invariant: the z faces are never crossed; treat z as periodic
+    g->desc.bc_lo[2] = g->desc.bc_hi[2] = RT_BC_PERIODIC;
+    g->desc.dz = 1.0;
+  }
+  if (!level_symmetric(D.n_mu, g->two_d, g->mu, g->wq)) {
+    delete g;
+    return fail(RT_ERR_ARG, "n_mu must be 2, 4, 6, 8, 10 or 12 (got %d)", D.n_mu);
+  }
+  g->na = (int)g->wq.size();
+  g->tsize = D.prec == RT_PREC_FP64 ? 8 : 4;
+  rtk::Dims &d = g->d;
+  d.n[0] = D.nx;
+  d.n[1] = D.ny;
+  d.n[2] = D.nz;
+  d.nf = D.nfreq;
+  d.cells = (long long)D.nx * D.ny * D.nz;
+  for (int a = 0; a < 3; ++a) {
+    d.bc_lo[a] = g->desc.bc_lo[a];
+    d.bc_hi[a] = g->desc.bc_hi[a];
+    d.periodic[a] = g->desc.bc_lo[a] == RT_BC_PERIODIC;
+  }
+  d.face[0] = (long long)D.nz * D.ny;
+  d.face[1] = (long long)D.nz * D.nx;
+  d.face[2] = (long long)D.ny * D.nx;
+  d.gsize = d.face[0] + d.face[1] + d.face[2];
+  build_rays(g);
+  plan_groups(g);
+
+  auto cleanup = [&](rt_status st) {
+    rt_destroy_grid(g);
+    return st;
+  };
+  cudaGetDevice(&g->device);
+  const size_t N = (size_t)d.cells * d.nf;
+  const size_t ts = g->tsize;
+#define ALLOC(ptr, bytes)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                              \
+    if (e_ != cudaSuccess)                                                              \
+      return cleanup(fail(RT_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", (size_t)(bytes), \
+                          cudaGetErrorString(e_)));                                     \
+  } while (0)
+  ALLOC(g->chi, N * 8);
+  ALLOC(g->eps, N * 8);
+  ALLOC(g->B, N * 8);
+  ALLOC(g->fw, (size_t)d.nf * 8);
+  ALLOC(g->S, N * 8);
+  ALLOC(g->Sfs, N * 8);
+  ALLOC(g->J, N * 8);
+  ALLOC(g->Jprev, N * 8);
+  ALLOC(g->lstar, N * 8);
+  ALLOC(g->oml, N * 8);
+  for (int a = 0; a < 3; ++a) {
+    if (!g->used_axis[a]) continue;
+    ALLOC(g->chiP[a], N * ts);
+    ALLOC(g->SP[a], N * ts);
+  }
+  const size_t gbytes = (size_t)d.nf * g->na * d.gsize * ts;
+  ALLOC(g->G[0], gbytes);
+  ALLOC(g->G[1], gbytes);
+  for (int f = 0; f < 6; ++f) {
+    if (d.periodic[f / 2]) continue;
+    ALLOC(g->Ibc[f], (size_t)d.nf * g->na * d.face[f / 2] * ts);
+  }
+  ALLOC(g->rays_d, (size_t)g->na * sizeof(RayGeom));
+  ALLOC(g->st, sizeof(rtk::SolveState));
+  ALLOC(g->counts, 2 * sizeof(int));
+#undef ALLOC
+  if (cudaMemset(g->st, 0, sizeof(rtk::SolveState)) != cudaSuccess ||
+      cudaMemset(g->G[0], 0, gbytes) != cudaSuccess || cudaMemset(g->G[1], 0, gbytes) != cudaSuccess ||
+      cudaMemcpy(g->rays_d, g->rays.data(), g->na * sizeof(RayGeom), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(fail(RT_ERR_CUDA, "initialisation copy failed"));
+  rt_status r = upload_plan_any(g);
+  if (r != RT_OK) return cleanup(r);
+  if (cudaStreamCreateWithFlags(&g->own, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(RT_ERR_CUDA, "stream creation failed"));
+  *out = g;
+  return RT_OK;
+}
+
+rt_status rt_destroy_grid(rt_grid g) {
+  if (!g) return RT_OK;
+  if (g->own) cudaStreamSynchronize(g->own);
+  void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml,
+                  g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
+                  g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
+                  g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
+                  g->Jpart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (g->own) cudaStreamDestroy(g->own);
+  delete g;
+  return RT_OK;
+}
+
+int rt_num_angles(rt_grid g) { return g ? g->na : 0; }
+
+int rt_angle_table(int n_mu, int two_d, double *mu, double *w) {
+  std::vector<double> m, q;
+  if (!level_symmetric(n_mu, two_d != 0, m, q)) {
+    fail(RT_ERR_ARG, "n_mu must be 2, 4, 6, 8, 10 or 12 (got %d)", n_mu);
+    return RT_ERR_ARG;
+  }
+  if (mu) std::memcpy(mu, m.data(), m.size() * sizeof(double));
+  if (w) std::memcpy(w, q.data(), q.size() * sizeof(double));
+  return (int)q.size();
+}
+
+rt_status rt_get_angles(rt_grid g, double *mu, double *w) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (mu) std::memcpy(mu, g->mu.data(), g->mu.size() * sizeof(double));
+  if (w) std::memcpy(w, g->wq.data(), g->wq.size() * sizeof(double));
+  return RT_OK;
+}
+
+rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (angles_per_group < 0 || angles_per_group > 8 || cluster_ctas < 0 || cluster_ctas > 16 ||
+      threads < 0 || threads > 512 || (threads % 32))
+    return fail(RT_ERR_ARG, "bad sweep configuration");
+  cudaStreamSynchronize(g->own);
+  g->req_apg = angles_per_group;
+  g->req_cluster = cluster_ctas;
+  g->req_threads = threads;
+  plan_groups(g);
+  if (g->smem > 227 * 1024) return fail(RT_ERR_ARG, "sweep configuration needs %zu bytes of shared memory", g->smem);
+  return upload_plan_any(g);
+}
+
+rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *eps, const double *B,
+                                const double *freq_w, int on_device) {
+  if (!g || !chi_tot || !eps || !B) return fail(RT_ERR_ARG, "rt_set_opacity_source: NULL argument");
+  cudaStream_t s = g->own;
+  const size_t N = (size_t)N_of(g);
+  rt_status r;
+  if ((r = copy_in(g, g->chi, chi_tot, N, on_device, s)) != RT_OK) return r;
+  if ((r = copy_in(g, g->eps, eps, N, on_device, s)) != RT_OK) return r;
+  if ((r = copy_in(g, g->B, B, N, on_device, s)) != RT_OK) return r;
+  if (freq_w) {
+    if ((r = copy_in(g, g->fw, freq_w, g->d.nf, on_device, s)) != RT_OK) return r;
+  } else {
+    std::vector<double> ones(g->d.nf, 1.0);
+    CU(cudaMemcpyAsync(g->fw, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  CU(cudaMemsetAsync(g->counts, 0, 2 * sizeof(int), s));
+  CU(rtk::launch_validate((long long)N, g->chi, g->eps, g->B, g->counts, s));
+  int counts[2] = {0, 0};
+  CU(cudaMemcpyAsync(counts, g->counts, sizeof counts, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  g->launches++;
+  if (counts[0]) {
+    g->have_medium = false;
+    return fail(RT_ERR_ARG, "%d input values violate chi >= 0, 0 < eps <= 1, B >= 0 or are not finite", counts[0]);
+  }
+  g->lte = counts[1] == 0;
+  if ((r = permute_any(g, g->chi, g->chiP, s)) != RT_OK) return r;
+  if (g->desc.prec == RT_PREC_FP64) {
+    CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+  } else {
+    CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+  }
+  g->launches++;
+  CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
+  if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  for (int f = 0; f < 6; ++f)
+    if ((r = fill_bc_any(g, f, s)) != RT_OK) return r;
+  g->have_medium = true;
+  return RT_OK;
+}
+
+rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I) {
+  if (!g || !I) return fail(RT_ERR_ARG, "rt_set_boundary_intensity: NULL argument");
+  if (face < 0 || face > 5) return fail(RT_ERR_ARG, "face must be 0..5");
+  const int ax = face / 2, side = face % 2;
+  const int bc = side ? g->desc.bc_hi[ax] : g->desc.bc_lo[ax];
+  if (bc != RT_BC_FIXED) return fail(RT_ERR_STATE, "face %d is not RT_BC_FIXED", face);
+  const size_t n = (size_t)g->d.nf * g->na * g->d.face[ax];
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(I[i]) || I[i] < 0.0) return fail(RT_ERR_ARG, "boundary intensity must be finite and >= 0");
+  if (!g->user_bc[face]) CU(cudaMalloc((void **)&g->user_bc[face], n * 8));
+  CU(cudaMemcpyAsync(g->user_bc[face], I, n * 8, cudaMemcpyHostToDevice, g->own));
+  rt_status r = fill_bc_any(g, face, g->own);
+  if (r != RT_OK) return r;
+  CU(cudaStreamSynchronize(g->own));
+  return RT_OK;
+}
+
+rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out, int on_device,
+                          const rt_solve_opts *opts) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) {   // order after the grid's own stream (set-up work)
+    CU(cudaStreamSynchronize(g->own));
+  }
+  const size_t N = (size_t)N_of(g);
+  rt_status r;
+  g->launches = 0;
+  if (S) {
+    if ((r = copy_in(g, g->S, S, N, on_device, s)) != RT_OK) return r;
+    if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+    if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  }
+  r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
+  if (r != RT_OK) return r;
+  if (J_out && (r = copy_out(J_out, g->J, N, on_device, s)) != RT_OK) return r;
+  if (lstar_out && (r = copy_out(lstar_out, g->lstar, N, on_device, s)) != RT_OK) return r;
+  if (!on_device || !opts || !opts->stream) CU(cudaStreamSynchronize(s));
+  g->stats.iters = 1;
+  g->stats.updates = (long long)g->d.cells * g->na * g->d.nf;
+  g->stats.kernel_launches = g->launches;
+  return RT_OK;
+}
+
+rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
+                       int *iters_out, double *resid_out) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  const size_t N = (size_t)N_of(g);
+  rt_status r;
+  g->launches = 0;
+  if (S_init) {
+    if ((r = copy_in(g, g->S, S_init, N, on_device, s)) != RT_OK) return r;
+  } else {
+    CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  int iters = 0;
+  double resid = 0.0;
+  bool conv = false;
+  r = g->desc.prec == RT_PREC_FP64 ? ali_loop<double>(g, opts, s, &iters, &resid, &conv)
+                                   : ali_loop<float>(g, opts, s, &iters, &resid, &conv);
+  if (r != RT_OK) return r;
+  if (iters_out) *iters_out = iters;
+  if (resid_out) *resid_out = resid;
+  g->stats.iters = iters;
+  g->stats.resid = resid;
+  g->stats.updates = (long long)g->d.cells * g->na * g->d.nf * iters;
+  g->stats.kernel_launches = g->launches;
+  if (!conv) return fail(RT_ERR_NOT_CONVERGED, "not converged after %d formal solutions (residual %g)", iters, resid);
+  return RT_OK;
+}
+
+rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, double *Q, int on_device,
+                     const rt_solve_opts *opts) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->have_medium || g->fs_total < 1) return fail(RT_ERR_STATE, "no formal solution to take moments of");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  const size_t N = (size_t)N_of(g);
+  rt_status r;
+  // device outputs: J(N) H(3N) K(6N) F(6N) Q(cells)
+  if ((r = ensure_tmp(g, 16 * N + (size_t)g->d.cells)) != RT_OK) return r;
+  double *dJ = g->tmp, *dH = dJ + N, *dK = dH + 3 * N, *dF = dK + 6 * N, *dQ = dF + 6 * N;
+  const double *Ssrc = g->last_fs_from_Sfs ? g->Sfs : g->S;
+  if ((r = permute_any(g, Ssrc, g->SP, s)) != RT_OK) return r;
+  if (g->desc.prec == RT_PREC_FP64) {
+    if ((r = moments_sweep<double>(g, s)) != RT_OK) return r;
+    CU(rtk::launch_reduce_moments<double>(g->d, (int)g->groups.size(), (const double *)g->Jpart,
+                                          (const double *)g->Mpart, dJ, dH, dK, dF, g->two_d, s));
+  } else {
+    if ((r = moments_sweep<float>(g, s)) != RT_OK) return r;
+    CU(rtk::launch_reduce_moments<float>(g->d, (int)g->groups.size(), (const float *)g->Jpart,
+                                         (const float *)g->Mpart, dJ, dH, dK, dF, g->two_d, s));
+  }
+  CU(rtk::launch_heating(g->d, g->fw, g->chi, g->eps, dJ, g->B, dQ, s));
+  if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  if (J && (r = copy_out(J, dJ, N, on_device, s)) != RT_OK) return r;
+  if (H && (r = copy_out(H, dH, 3 * N, on_device, s)) != RT_OK) return r;
+  if (K && (r = copy_out(K, dK, 6 * N, on_device, s)) != RT_OK) return r;
+  if (f && (r = copy_out(f, dF, 6 * N, on_device, s)) != RT_OK) return r;
+  if (Q && (r = copy_out(Q, dQ, (size_t)g->d.cells, on_device, s)) != RT_OK) return r;
+  CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts) {
+  if (!g || !S) return fail(RT_ERR_ARG, "NULL argument");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  rt_status r = copy_out(S, g->S, (size_t)N_of(g), on_device, s);
+  if (r != RT_OK) return r;
+  CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_enable_timing(rt_grid g, int enable) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  g->timing = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_get_stats(rt_grid g, rt_stats *out) {
+  if (!g || !out) return fail(RT_ERR_ARG, "NULL argument");
+  *out = g->stats;
+  return RT_OK;
+}
+
+}  // extern "C"

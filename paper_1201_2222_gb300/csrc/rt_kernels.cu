@@ -1,0 +1,712 @@
+// CUDA kernels of the short-characteristics library (sm_103a).
+//
+//   sc_sweep_kernel   formal solution of one sweep group for one frequency (Sec. 3.3)
+//   ali_update_kernel Jacobi ALI update, FP64 (Sec. 3.4, Eq. 30) + max |dS|/S (Eq. 31)
+//   lstar_kernel      diagonal Lambda* = sum_k w_k Psi0_k (Sec. 3.4)
+//   finish_kernel     convergence decision and ghost-parity advance (one thread)
+//   plus set-up kernels: validation, permuted sweep copies, ghost initialisation,
+//   boundary intensities, J / moment reductions and the heating rate (Sec. 4).
+//
+// No kernel waits on another block: the only cross-CTA synchronisation is the
+// hardware cluster barrier inside one cluster, which every CTA of the cluster
+// reaches the same number of times.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "rt_common.cuh"
+#include "rt_kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace rtk {
+
+#ifdef RT_DEBUG_BOUNDS
+// Debug builds: every indexed access is checked; a bad index is recorded in the
+// solve state and replaced by 0 so that no access leaves its buffer.
+__device__ __forceinline__ long long chk(long long i, long long n, SolveState *st, int code) {
+  if (i < 0 || i >= n) {
+    atomicCAS(&st->err, 0, code);
+    st->err_info = (int)i;
+    return 0;
+  }
+  return i;
+}
+#define RT_IDX(i, n, code) chk((i), (n), A.st, (code))
+#else
+#define RT_IDX(i, n, code) (i)
+#endif
+
+// ----------------------------------------------------------------- segment weights
+// Linear short-characteristics weights for one segment of optical depth dtau:
+// E = exp(-dtau), Psi0 = 1 - (1 - E)/dtau (weight of S at the cell), and
+// om = 1 - Psi0, all without cancellation: below the threshold Psi0 is the
+// Taylor series of 1 - (1 - e^-x)/x = sum_{n>=1} (-1)^(n+1) x^n/(n+1)!.
+
+__device__ __forceinline__ void seg_weights(float dtau, float &E, float &psi0, float &om) {
+  E = __expf(-dtau);
+  const float q = __fdividef(1.0f - E, dtau);
+  const float x = dtau;
+  const float ser =
+      x * (1.0f / 2 - x * (1.0f / 6 - x * (1.0f / 24 - x * (1.0f / 120 - x * (1.0f / 720 -
+      x * (1.0f / 5040 - x * (1.0f / 40320 - x * (1.0f / 362880))))))));
+  const bool small = dtau < 0.5f;
+  psi0 = small ? ser : 1.0f - q;
+  om = small ? 1.0f - ser : q;
+}
+
+__device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0, double &om) {
+  E = exp(-dtau);
+  if (dtau < 1e-2) {
+    const double x = dtau;
+    psi0 = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 -
+           x * (1.0 / 5040 - x * (1.0 / 40320)))))));
+    om = 1.0 - psi0;
+  } else {
+    om = -expm1(-dtau) / dtau;
+    psi0 = 1.0 - om;
+  }
+}
+
+// ------------------------------------------------------------------------ sweep
+
+template <typename T>
+__device__ __forceinline__ long long face_cell(const Dims &d, int ax, const int m[3]) {
+  return ax == 0 ? (long long)m[2] * d.n[1] + m[1]
+                 : (ax == 1 ? (long long)m[2] * d.n[0] + m[0] : (long long)m[1] * d.n[0] + m[0]);
+}
+
+// Intensity at an upwind vertex outside the domain (plane coordinates u, v, w).
+// If any out-of-range axis is non-periodic, the inflow intensity of the first such
+// face in the order z, y, x; otherwise the image cell's intensity from the previous
+// formal solution (lagged periodic ghost), read from the face buffer of the first
+// out-of-range axis in the same order.
+template <typename T>
+__device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
+                                     int Nw, int f, int angle, const T *Gp, int u, int v, int w) {
+  int crd[3];
+  crd[cax[0]] = u;
+  crd[cax[1]] = v;
+  crd[cax[2]] = w;
+  int m[3], oor[3], side[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = A.d.n[ax];
+    const int c = crd[ax];
+    oor[ax] = (c < 0) || (c >= n);
+    side[ax] = c >= n;
+    m[ax] = !oor[ax] ? c : (A.d.periodic[ax] ? (c < 0 ? c + n : c - n) : (c < 0 ? 0 : n - 1));
+  }
+#pragma unroll
+  for (int ax = 2; ax >= 0; --ax) {
+    if (oor[ax] && !A.d.periodic[ax]) {
+      const int face = 2 * ax + side[ax];
+      const long long idx = ((long long)f * A.na + angle) * A.d.face[ax] + face_cell<T>(A.d, ax, m);
+      return A.Ibc[face][RT_IDX(idx, (long long)A.d.nf * A.na * A.d.face[ax], 11)];
+    }
+  }
+  const long long gb = ((long long)f * A.na + angle) * A.d.gsize;
+  const int ax = oor[2] ? 2 : (oor[1] ? 1 : 0);
+  const int mu_ = m[cax[0]], mv_ = m[cax[1]], mw_ = m[cax[2]];
+  long long off;
+  if (ax == cax[2]) off = (long long)mv_ * Nu + mu_;
+  else if (ax == cax[0]) off = (long long)Nu * Nv + (long long)mw_ * Nv + mv_;
+  else off = (long long)Nu * Nv + (long long)Nw * Nv + (long long)mw_ * Nu + mu_;
+  return Gp[RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 12)];
+}
+
+// One sweep group (rays sharing the crossed-face axis a and sign(mu_a)) for one
+// frequency.  The plane normal to a is split into C strips of rows (v) over the C
+// CTAs of a cluster.  Every step computes one plane from the previous plane:
+//   I- , S-, chi- bilinear on the upwind face (weights wa..wd of the ray),
+//   dtau = (chi- + chi0) s/2,  I0 = S- + E (I- - S-) + Psi0 (S0 - S-),
+// which equals I- E + Psi- S- + Psi0 S0 with Psi- = 1 - E - Psi0 (Eq. 25, linear).
+// The previous plane's intensities live in shared memory (double-buffered); a
+// strip's edge row comes from the neighbouring CTA's shared memory (DSMEM).
+// J partial of the group is the FP-T sum over its rays, written once per cell.
+template <typename T, int AMAX, bool MOM>
+__global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
+  if (A.skip_if_done && A.st->done) return;
+  const int C = A.cluster;
+  const int rank = blockIdx.x % C;
+  const int inst = blockIdx.x / C;
+  const int gi = inst % A.ngroups;
+  const int f = inst / A.ngroups;
+  const GroupParam gp = A.grp[gi];
+  int cax[3];
+  plane_axes(gp.axis, cax);
+  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
+  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int v0 = (int)(((long long)rank * Nv) / C);
+  const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
+  const int R = v1 - v0;
+  const int Rmax = (Nv + C - 1) / C;
+  const long long plane = (long long)Nu * Nv;
+  const long long cells = A.d.cells;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ibuf = reinterpret_cast<T *>(smem_raw);
+  const int bufstride = AMAX * Rmax * Nu;
+#ifdef RT_DEBUG_BOUNDS
+  const long long smem_n = 2LL * bufstride;
+#endif
+
+  __shared__ AngleParam<T> P[AMAX];
+  if (threadIdx.x < gp.na) P[threadIdx.x] = A.ang[gp.a0 + threadIdx.x];
+  __syncthreads();
+
+  const int fs = A.st->fs_count + A.parity_offset;
+  const int prev = fs & 1;
+  const T *Gp = A.G[prev];
+  T *Gn = A.G[prev ^ 1];
+  const T *chiP = A.chiP[gp.axis] + (long long)f * cells;
+  const T *SP = A.SP[gp.axis] + (long long)f * cells;
+  T *Jout = A.Jpart + ((long long)gi * A.d.nf + f) * cells;
+  const int sa = gp.sa;
+  const int wlast = sa > 0 ? Nw - 1 : 0;
+  cg::cluster_group cluster = cg::this_cluster();
+
+  for (int t = 0; t < Nw; ++t) {
+    const int w = sa > 0 ? t : Nw - 1 - t;
+    const int wp = w - sa;
+    const bool wp_in = t > 0;
+    const int wpm = wp_in ? wp : (perW ? (wp < 0 ? wp + Nw : wp - Nw) : w);
+    T *cur = Ibuf + (t & 1) * bufstride;
+    const T *prv = Ibuf + ((t + 1) & 1) * bufstride;
+    const long long pbase = (long long)wpm * plane;
+    for (int c = threadIdx.x; c < R * Nu; c += blockDim.x) {
+      const int u = c % Nu;
+      const int lv = c / Nu;
+      const int v = v0 + lv;
+      const long long pidx = ((long long)w * Nv + v) * Nu + u;
+      const T chi0 = chiP[RT_IDX(pidx, cells, 1)];
+      const T S0 = SP[RT_IDX(pidx, cells, 2)];
+      int crd[3];
+      crd[cax[0]] = u;
+      crd[cax[1]] = v;
+      crd[cax[2]] = w;
+      const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+      T Jacc = T(0);
+      T Hm[3] = {T(0), T(0), T(0)};
+      T Km[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a) {
+        if (a < gp.na) {
+          const AngleParam<T> &p = P[a];
+          const int ua = u - p.su, vb = v - p.sv;
+          const bool ua_in = (unsigned)ua < (unsigned)Nu;
+          const bool vb_in = (unsigned)vb < (unsigned)Nv;
+          const int um = ua_in ? ua : (perU ? (ua < 0 ? ua + Nu : ua - Nu) : u);
+          const int vm = vb_in ? vb : (perV ? (vb < 0 ? vb + Nv : vb - Nv) : v);
+          const long long iA = pbase + (long long)v * Nu + u;
+          const long long iB = pbase + (long long)v * Nu + um;
+          const long long iC = pbase + (long long)vm * Nu + u;
+          const long long iD = pbase + (long long)vm * Nu + um;
+          const T cA = chiP[RT_IDX(iA, cells, 3)], cB = chiP[RT_IDX(iB, cells, 3)];
+          const T cC = chiP[RT_IDX(iC, cells, 3)], cD = chiP[RT_IDX(iD, cells, 3)];
+          const T sA = SP[RT_IDX(iA, cells, 4)], sB = SP[RT_IDX(iB, cells, 4)];
+          const T sC = SP[RT_IDX(iC, cells, 4)], sD = SP[RT_IDX(iD, cells, 4)];
+          T IA, IB, IC, ID;
+          if (wp_in) {
+            const int rowA = (a * Rmax + lv) * Nu;
+            IA = prv[RT_IDX(rowA + u, smem_n, 5)];
+            IB = ua_in ? prv[RT_IDX(rowA + ua, smem_n, 5)]
+                       : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, v, wp);
+            if (vb_in) {
+              const T *src = prv;
+              int lvb = vb - v0;
+              if (vb < v0 || vb >= v1) {
+                const int rr = vb < v0 ? rank - 1 : rank + 1;
+                const int rv0 = (int)(((long long)rr * Nv) / C);
+                src = cluster.map_shared_rank(const_cast<T *>(prv), rr);
+                lvb = vb - rv0;
+              }
+              const int rowC = (a * Rmax + lvb) * Nu;
+              IC = src[RT_IDX(rowC + u, smem_n, 6)];
+              ID = ua_in ? src[RT_IDX(rowC + ua, smem_n, 6)]
+                         : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+            } else {
+              IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, vb, wp);
+              ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+            }
+          } else {
+            IA = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, v, wp);
+            IB = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, v, wp);
+            IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, vb, wp);
+            ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+          }
+          const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
+          const T Sm = p.wa * sA + p.wb * sB + p.wc * sC + p.wd * sD;
+          const T Im = p.wa * IA + p.wb * IB + p.wc * IC + p.wd * ID;
+          const T dtau = (chim + chi0) * p.hs;
+          T E, psi0, om;
+          seg_weights(dtau, E, psi0, om);
+          const T I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
+          cur[RT_IDX((a * Rmax + lv) * Nu + u, smem_n, 7)] = I0;
+          const T wI = p.wq * I0;
+          Jacc += wI;
+          if (MOM) {
+            Hm[0] += wI * p.mu[0];
+            Hm[1] += wI * p.mu[1];
+            Hm[2] += wI * p.mu[2];
+            Km[0] += wI * p.mu[0] * p.mu[0];
+            Km[1] += wI * p.mu[1] * p.mu[1];
+            Km[2] += wI * p.mu[2] * p.mu[2];
+            Km[3] += wI * p.mu[0] * p.mu[1];
+            Km[4] += wI * p.mu[0] * p.mu[2];
+            Km[5] += wI * p.mu[1] * p.mu[2];
+          }
+          if (A.write_ghosts) {
+            const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+            const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+            if (perW && w == wlast) Gn[RT_IDX(gb + (long long)v * Nu + u, gn, 8)] = I0;
+            if (perU && u == (p.su > 0 ? Nu - 1 : 0))
+              Gn[RT_IDX(gb + plane + (long long)w * Nv + v, gn, 9)] = I0;
+            if (perV && v == (p.sv > 0 ? Nv - 1 : 0))
+              Gn[RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u, gn, 10)] = I0;
+          }
+        }
+      }
+      Jout[RT_IDX(canon, cells, 13)] = Jacc;
+      if (MOM) {
+        T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
+        const long long qs = (long long)A.d.nf * cells;
+        const long long o = (long long)f * cells + canon;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[q];
+      }
+    }
+    if (C > 1) cluster.sync();
+    else __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------- ALI update
+
+__device__ __forceinline__ double rel_change(double d, double x) {
+  const double ad = fabs(d), ax = fabs(x);
+  return ax > 0.0 ? ad / ax : (ad > 0.0 ? INFINITY : 0.0);
+}
+
+__device__ __forceinline__ void block_max_to(double r, unsigned long long *dst) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = r;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0 && r > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+__device__ __forceinline__ long long perm_index(const Dims &d, int a, long long cell) {
+  const int x = (int)(cell % d.n[0]);
+  const int y = (int)((cell / d.n[0]) % d.n[1]);
+  const int z = (int)(cell / ((long long)d.n[0] * d.n[1]));
+  if (a == 2) return cell;
+  if (a == 1) return ((long long)y * d.n[2] + z) * d.n[0] + x;   // [y][z][x]
+  return ((long long)x * d.n[2] + z) * d.n[1] + y;                 // [x][z][y]
+}
+
+// Jacobi ALI (Eq. 30): dS = [(1-eps) J + eps B - S] / [1 - (1-eps) Lambda*], with
+// the denominator formed as eps + (1-eps)(1 - Lambda*) from the separately summed
+// 1 - Lambda* (no cancellation in thick cells).  All of it in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) ali_update_kernel(const AliArgs<T> A) {
+  if (A.st->done) return;
+  const long long cells = A.d.cells;
+  const long long N = cells * A.d.nf;
+  const bool first = A.st->iter == 0;
+  double rmax = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / cells, c = i - f * cells;
+    double J = 0.0;
+    for (int p = 0; p < A.ngroups_per_f; ++p) J += (double)A.Jpart[((long long)p * A.d.nf + f) * cells + c];
+    A.J64[i] = J;
+    double r;
+    if (A.lte) {
+      const double Jp = A.Jprev[i];
+      r = first ? INFINITY : rel_change(J - Jp, J);
+      A.Jprev[i] = J;
+    } else {
+      const double S = A.S64[i], e = A.eps[i];
+      const double dS = ((1.0 - e) * J + e * A.B[i] - S) / (e + (1.0 - e) * A.oml[i]);
+      const double Sn = S + dS;
+      A.S64[i] = Sn;
+      A.Sfs[i] = S;
+      r = rel_change(dS, Sn);
+      const T Snt = (T)Sn;
+      for (int a = 0; a < 3; ++a)
+        if (A.SP[a]) A.SP[a][f * cells + perm_index(A.d, a, c)] = Snt;
+    }
+    rmax = fmax(rmax, r);
+  }
+  block_max_to(rmax, &A.st->resid_bits);
+}
+
+// Convergence decision after one ALI iteration (single thread).
+__global__ void finish_kernel(SolveState *st) {
+  if (st->done) return;
+  const double r = __longlong_as_double((long long)st->resid_bits);
+  st->resid_bits = 0ULL;
+  st->fs_count += 1;
+  st->iter += 1;
+  st->last_resid = r;
+  if (r <= st->tol) {
+    st->done = 1;
+    st->converged = 1;
+  } else if (st->iter >= st->max_iter) {
+    st->done = 1;
+  }
+}
+
+// Small state edits, in stream order.
+__global__ void state_op_kernel(SolveState *st, int op, int a, double b, int c) {
+  if (op == 0) {           // reset for a new ALI solve
+    st->fs_count = 0;
+    st->iter = 0;
+    st->done = 0;
+    st->converged = 0;
+    st->max_iter = a;
+    st->tol = b;
+    st->lte = c;
+    st->resid_bits = 0ULL;
+    st->last_resid = INFINITY;
+  } else if (op == 1) {    // one formal solution completed outside an ALI loop
+    st->fs_count += 1;
+  } else if (op == 2) {    // reset the ghost parity (ghosts re-initialised)
+    st->fs_count = 0;
+    st->done = 0;
+  }
+}
+
+// ------------------------------------------------------------------- Lambda*
+// Lambda*_ii = sum_k w_k Psi0_k(i) and 1 - Lambda*_ii = sum_k w_k (1 - Psi0_k(i)),
+// from chi alone, with the sweep's precision T for the segment weights and FP64 sums.
+template <typename T>
+__global__ void __launch_bounds__(256) lstar_kernel(Dims d, const double *chi, const RayGeom *rays,
+                                                    int na, double *lstar, double *oml) {
+  const long long cells = d.cells;
+  const long long N = cells * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / cells, c = i - f * cells;
+    const int c0[3] = {(int)(c % d.n[0]), (int)((c / d.n[0]) % d.n[1]),
+                       (int)(c / ((long long)d.n[0] * d.n[1]))};
+    const double *chf = chi + f * cells;
+    const T chi0 = (T)chf[c];
+    double L = 0.0, O = 0.0;
+    for (int k = 0; k < na; ++k) {
+      const RayGeom r = rays[k];
+      const int ax = r.axis, b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+      T chim = T(0);
+      for (int d1 = 0; d1 < 2; ++d1) {
+        for (int d2 = 0; d2 < 2; ++d2) {
+          const double wv = (d1 ? r.frac[b1] : 1.0 - r.frac[b1]) * (d2 ? r.frac[b2] : 1.0 - r.frac[b2]);
+          int cc[3];
+          cc[ax] = c0[ax] - r.sgn[ax];
+          cc[b1] = c0[b1] - d1 * r.sgn[b1];
+          cc[b2] = c0[b2] - d2 * r.sgn[b2];
+          for (int q = 0; q < 3; ++q) {
+            if (cc[q] < 0) cc[q] = d.periodic[q] ? cc[q] + d.n[q] : 0;
+            else if (cc[q] >= d.n[q]) cc[q] = d.periodic[q] ? cc[q] - d.n[q] : d.n[q] - 1;
+          }
+          chim += (T)wv * (T)chf[((long long)cc[2] * d.n[1] + cc[1]) * d.n[0] + cc[0]];
+        }
+      }
+      const T dtau = (chim + chi0) * (T)(0.5 * r.s);
+      T E, psi0, om;
+      seg_weights(dtau, E, psi0, om);
+      L += r.w * (double)psi0;
+      O += r.w * (double)om;
+    }
+    lstar[i] = L;
+    oml[i] = O;
+  }
+}
+
+// ------------------------------------------------------------------- set-up kernels
+
+// Counts inputs outside chi >= 0, 0 < eps <= 1, B >= 0 (or non-finite), and eps != 1.
+__global__ void validate_kernel(long long n, const double *chi, const double *eps, const double *B,
+                                int *counts) {
+  int bad = 0, non1 = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double c = chi[i], e = eps[i], b = B[i];
+    if (!(c >= 0.0) || !isfinite(c) || !(e > 0.0) || !(e <= 1.0) || !(b >= 0.0) || !isfinite(b)) ++bad;
+    if (e != 1.0) ++non1;
+  }
+  if (bad) atomicAdd(&counts[0], bad);
+  if (non1) atomicAdd(&counts[1], non1);
+}
+
+// Sweep-precision copies of a canonical FP64 field in the three permuted layouts.
+template <typename T>
+__global__ void permute_kernel(Dims d, const double *src, T *dst0, T *dst1, T *dst2) {
+  const long long cells = d.cells;
+  const long long N = cells * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / cells, c = i - f * cells;
+    const T v = (T)src[i];
+    if (dst0) dst0[f * cells + perm_index(d, 0, c)] = v;
+    if (dst1) dst1[f * cells + perm_index(d, 1, c)] = v;
+    if (dst2) dst2[f * cells + perm_index(d, 2, c)] = v;
+  }
+}
+
+// Lagged ghosts before the first formal solution: S of each ghost's periodic image.
+template <typename T>
+__global__ void init_ghosts_kernel(Dims d, int na, const RayGeom *rays, const double *S, T *G) {
+  const long long per_f = (long long)na * d.gsize;
+  const long long N = per_f * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / per_f;
+    const long long r = i - f * per_f;
+    const int k = (int)(r / d.gsize);
+    long long j = r - (long long)k * d.gsize;
+    const RayGeom g = rays[k];
+    int cax[3];
+    plane_axes(g.axis, cax);
+    const int Nu = d.n[cax[0]], Nv = d.n[cax[1]], Nw = d.n[cax[2]];
+    const int su = g.sgn[cax[0]], sv = g.sgn[cax[1]], sw = g.sgn[cax[2]];
+    int u, v, w;
+    if (j < (long long)Nu * Nv) {
+      v = (int)(j / Nu); u = (int)(j % Nu); w = sw > 0 ? Nw - 1 : 0;
+    } else if ((j -= (long long)Nu * Nv) < (long long)Nw * Nv) {
+      w = (int)(j / Nv); v = (int)(j % Nv); u = su > 0 ? Nu - 1 : 0;
+    } else {
+      j -= (long long)Nw * Nv;
+      w = (int)(j / Nu); u = (int)(j % Nu); v = sv > 0 ? Nv - 1 : 0;
+    }
+    int crd[3];
+    crd[cax[0]] = u;
+    crd[cax[1]] = v;
+    crd[cax[2]] = w;
+    G[i] = (T)S[f * d.cells + ((long long)crd[2] * d.n[1] + crd[1]) * d.n[0] + crd[0]];
+  }
+}
+
+// Inflow intensities of one non-periodic face [nf][na][face cells]:
+// mode VACUUM -> 0, THERMAL -> B of the adjacent layer, FIXED -> user values.
+template <typename T>
+__global__ void fill_bc_kernel(Dims d, int na, int face, int mode, const double *B,
+                               const double *user, T *dst) {
+  const int ax = face / 2, side = face % 2;
+  const long long fc = d.face[ax];
+  const long long N = (long long)d.nf * na * fc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (mode == BC_VACUUM) { dst[i] = T(0); continue; }
+    if (mode == BC_FIXED) { dst[i] = user ? (T)user[i] : T(0); continue; }
+    const long long f = i / ((long long)na * fc);
+    const long long p = i % fc;
+    int x, y, z;
+    const int edge = side ? d.n[ax] - 1 : 0;
+    if (ax == 0) { x = edge; z = (int)(p / d.n[1]); y = (int)(p % d.n[1]); }
+    else if (ax == 1) { y = edge; z = (int)(p / d.n[0]); x = (int)(p % d.n[0]); }
+    else { z = edge; y = (int)(p / d.n[0]); x = (int)(p % d.n[0]); }
+    dst[i] = (T)B[f * d.cells + ((long long)z * d.n[1] + y) * d.n[0] + x];
+  }
+}
+
+// J = sum of the sweep groups' partials (fixed group order), FP64.
+template <typename T>
+__global__ void reduce_J_kernel(Dims d, int ngroups, const T *Jpart, double *J) {
+  const long long N = d.cells * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < ngroups; ++p) s += (double)Jpart[(long long)p * N + i];
+    J[i] = s;
+  }
+}
+
+// J, H, K from the moment partials; f = K/J; 2D drops moments odd in mu_z.
+template <typename T>
+__global__ void reduce_moments_kernel(Dims d, int ngroups, const T *Jpart, const T *Mpart,
+                                      double *J, double *H, double *K, double *F, int two_d) {
+  const long long cells = d.cells;
+  const long long N = cells * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / cells, c = i - f * cells;
+    double s = 0.0, m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = 0; p < ngroups; ++p) {
+      s += (double)Jpart[(long long)p * N + i];
+      const T *M = Mpart + (long long)p * 9 * N;
+      for (int q = 0; q < 9; ++q) m[q] += (double)M[q * N + i];
+    }
+    if (two_d) { m[2] = 0.0; m[7] = 0.0; m[8] = 0.0; }
+    J[i] = s;
+    for (int q = 0; q < 3; ++q) H[(f * 3 + q) * cells + c] = m[q];
+    for (int q = 0; q < 6; ++q) {
+      K[(f * 6 + q) * cells + c] = m[3 + q];
+      F[(f * 6 + q) * cells + c] = m[3 + q] / s;
+    }
+  }
+}
+
+// Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)  (integral form, Sec. 4).
+__global__ void heating_kernel(Dims d, const double *fw, const double *chi, const double *eps,
+                               const double *J, const double *B, double *Q) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    double q = 0.0;
+    for (int f = 0; f < d.nf; ++f) {
+      const long long i = (long long)f * d.cells + c;
+      q += fw[f] * eps[i] * chi[i] * (J[i] - B[i]);
+    }
+    Q[c] = 4.0 * M_PI * q;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T, int AMAX, bool MOM>
+static cudaError_t launch_sweep_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
+  auto kern = sc_sweep_kernel<T, AMAX, MOM>;
+  static size_t set_smem = 0;
+  static bool nonportable = false;
+  if (smem > set_smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_smem = smem;
+  }
+  if (A.cluster > 8 && !nonportable) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    nonportable = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)A.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = A.cluster > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, A);
+}
+
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                         cudaStream_t s) {
+  switch (amax) {
+    case 1: return moments ? launch_sweep_t<T, 1, true>(A, threads, smem, s) : launch_sweep_t<T, 1, false>(A, threads, smem, s);
+    case 2: return moments ? launch_sweep_t<T, 2, true>(A, threads, smem, s) : launch_sweep_t<T, 2, false>(A, threads, smem, s);
+    case 4: return moments ? launch_sweep_t<T, 4, true>(A, threads, smem, s) : launch_sweep_t<T, 4, false>(A, threads, smem, s);
+    case 8: return moments ? launch_sweep_t<T, 8, true>(A, threads, smem, s) : launch_sweep_t<T, 8, false>(A, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s) {
+  const long long n = A.d.cells * A.d.nf;
+  ali_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(SolveState *st, cudaStream_t s) {
+  finish_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cudaStream_t s) {
+  state_op_kernel<<<1, 1, 0, s>>>(st, op, a, b, c);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lstar(const Dims &d, const double *chi, const RayGeom *rays, int na, double *lstar,
+                         double *oml, cudaStream_t s) {
+  lstar_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, chi, rays, na, lstar, oml);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(long long n, const double *chi, const double *eps, const double *B,
+                            int *counts, cudaStream_t s) {
+  validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, chi, eps, B, counts);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_permute(const Dims &d, const double *src, T *d0, T *d1, T *d2, cudaStream_t s) {
+  permute_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, src, d0, d1, d2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init_ghosts(const Dims &d, int na, const RayGeom *rays, const double *S, T *G,
+                               cudaStream_t s) {
+  init_ghosts_kernel<T><<<grid_for((long long)na * d.gsize * d.nf, 256), 256, 0, s>>>(d, na, rays, S, G);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fill_bc(const Dims &d, int na, int face, int mode, const double *B,
+                           const double *user, T *dst, cudaStream_t s) {
+  const long long n = (long long)d.nf * na * d.face[face / 2];
+  fill_bc_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(d, na, face, mode, B, user, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_J(const Dims &d, int ngroups, const T *Jpart, double *J, cudaStream_t s) {
+  reduce_J_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, ngroups, Jpart, J);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, const T *Mpart,
+                                  double *J, double *H, double *K, double *F, int two_d,
+                                  cudaStream_t s) {
+  reduce_moments_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, ngroups, Jpart, Mpart, J, H, K, F, two_d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, const double *eps,
+                           const double *J, const double *B, double *Q, cudaStream_t s) {
+  heating_kernel<<<grid_for(d.cells, 256), 256, 0, s>>>(d, fw, chi, eps, J, B, Q);
+  return cudaGetLastError();
+}
+
+#define RT_INSTANTIATE(T)                                                                          \
+  template cudaError_t launch_sweep<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template cudaError_t launch_ali<T>(const AliArgs<T> &, cudaStream_t);                             \
+  template cudaError_t launch_lstar<T>(const Dims &, const double *, const RayGeom *, int, double *, \
+                                       double *, cudaStream_t);                                     \
+  template cudaError_t launch_permute<T>(const Dims &, const double *, T *, T *, T *, cudaStream_t);  \
+  template cudaError_t launch_init_ghosts<T>(const Dims &, int, const RayGeom *, const double *, T *, \
+                                             cudaStream_t);                                         \
+  template cudaError_t launch_fill_bc<T>(const Dims &, int, int, int, const double *, const double *, \
+                                         T *, cudaStream_t);                                        \
+  template cudaError_t launch_reduce_J<T>(const Dims &, int, const T *, double *, cudaStream_t);     \
+  template cudaError_t launch_reduce_moments<T>(const Dims &, int, const T *, const T *, double *,   \
+                                                double *, double *, double *, int, cudaStream_t);
+
+RT_INSTANTIATE(float)
+RT_INSTANTIATE(double)
+
+}  // namespace rtk

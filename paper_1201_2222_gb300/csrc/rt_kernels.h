@@ -1,0 +1,71 @@
+// Argument blocks and launchers of the library's kernels (see rt_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rt_common.cuh"
+
+namespace rtk {
+
+template <typename T>
+struct SweepArgs {
+  Dims d;
+  int na;                    // rays in the full angle table
+  const T *chiP[3];          // sweep-precision opacity, permuted per sweep axis, [nf][cells]
+  const T *SP[3];            // sweep-precision source function, same layouts
+  T *G[2];                   // lagged periodic ghosts [nf][na][gsize], selected by parity
+  const T *Ibc[6];           // inflow intensity of non-periodic faces [nf][na][face cells]
+  const AngleParam<T> *ang;  // rays in group order
+  const GroupParam *grp;
+  int ngroups;               // groups per frequency
+  T *Jpart;                  // [ngroups][nf][cells] canonical
+  T *Mpart;                  // [ngroups][9][nf][cells] (moments launches only)
+  SolveState *st;
+  int parity_offset;         // ghost parity = (st->fs_count + parity_offset) & 1
+  int write_ghosts;
+  int skip_if_done;
+  int cluster;               // CTAs per cluster = strips per plane
+};
+
+template <typename T>
+struct AliArgs {
+  Dims d;
+  int ngroups_per_f;
+  const T *Jpart;
+  const double *eps, *B, *oml;
+  double *S64, *Sfs, *J64, *Jprev;
+  T *SP[3];                  // permuted sweep copies of S to refresh (NULL = axis unused)
+  SolveState *st;
+  int lte;
+};
+
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s);
+cudaError_t launch_finish(SolveState *st, cudaStream_t s);
+cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lstar(const Dims &d, const double *chi, const RayGeom *rays, int na, double *lstar,
+                         double *oml, cudaStream_t s);
+cudaError_t launch_validate(long long n, const double *chi, const double *eps, const double *B,
+                            int *counts, cudaStream_t s);
+template <typename T>
+cudaError_t launch_permute(const Dims &d, const double *src, T *d0, T *d1, T *d2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_ghosts(const Dims &d, int na, const RayGeom *rays, const double *S, T *G,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_fill_bc(const Dims &d, int na, int face, int mode, const double *B,
+                           const double *user, T *dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_reduce_J(const Dims &d, int ngroups, const T *Jpart, double *J, cudaStream_t s);
+template <typename T>
+cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, const T *Mpart,
+                                  double *J, double *H, double *K, double *F, int two_d,
+                                  cudaStream_t s);
+cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, const double *eps,
+                           const double *J, const double *B, double *Q, cudaStream_t s);
+
+}  // namespace rtk

@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in ``include/rt_sc.h`` (argument marshalling only).
+
+Arrays may be NumPy (host memory, ``on_device = 0``) or CUDA ``torch`` tensors
+(device memory on the grid's device, ``on_device = 1``, run on torch's current
+stream).  Outputs come back in the kind of memory the inputs were in.  Every
+computation happens in the CUDA library; if ``librtsc.so`` is missing this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+
+RT_OK = 0
+RT_ERR_ARG = -1
+RT_ERR_OOM = -2
+RT_ERR_CUDA = -3
+RT_ERR_NOT_CONVERGED = -4
+RT_ERR_TIMEOUT = -5
+RT_ERR_STATE = -6
+
+
+class rt_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("n_mu", ctypes.c_int), ("nfreq", ctypes.c_int),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("prec", ctypes.c_int)]
+
+
+class rt_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class rt_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("resid", ctypes.c_double), ("sweep_ms", ctypes.c_double),
+                ("sweep_launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong)]
+
+
+class RTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rt status {status}: {msg}")
+        self.status = status
+
+
+# symbol -> (restype, argtypes); mirrors include/rt_sc.h
+_VP = ctypes.c_void_p
+_SIGS = {
+    "rt_create_grid": (ctypes.c_int, [ctypes.POINTER(rt_grid_desc), ctypes.POINTER(_VP)]),
+    "rt_destroy_grid": (ctypes.c_int, [_VP]),
+    "rt_num_angles": (ctypes.c_int, [_VP]),
+    "rt_get_angles": (ctypes.c_int, [_VP, _VP, _VP]),
+    "rt_set_opacity_source": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "rt_set_boundary_intensity": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "rt_formal_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts)]),
+    "rt_ali_solve": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "rt_moments": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int,
+                                  ctypes.POINTER(rt_solve_opts)]),
+    "rt_get_S": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts)]),
+    "rt_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(rt_stats)]),
+    "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "rt_angle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "rt_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path(debug=os.environ.get("RT_SC_DEBUG", "0") == "1")
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                               "paper_1201_2222_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st):
+    if st != RT_OK:
+        raise RTError(st, load().rt_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch") and hasattr(x, "data_ptr")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def angle_table(n_mu, two_d=False):
+    """The library's angle table (mu [n][3], w [n]) computed on the host."""
+    lib = load()
+    n = lib.rt_angle_table(n_mu, 1 if two_d else 0, None, None)
+    if n < 0:
+        _check(n)
+    mu = np.empty((n, 3))
+    w = np.empty(n)
+    lib.rt_angle_table(n_mu, 1 if two_d else 0, mu.ctypes.data, w.ctypes.data)
+    return mu, w
+
+
+class Grid:
+    """A transfer problem on the GPU: grid, angle set, medium and solver state."""
+
+    def __init__(self, nx, ny, nz, n_mu=4, nfreq=1, bc_lo=(PERIODIC, PERIODIC, THERMAL),
+                 bc_hi=(PERIODIC, PERIODIC, VACUUM), dx=1.0, dy=1.0, dz=1.0, prec=MIXED):
+        lib = load()
+        if isinstance(prec, str):
+            prec = {"fp64": FP64, "mixed": MIXED}[prec.lower()]
+        d = rt_grid_desc(nx, ny, nz, dx, dy, dz, n_mu, nfreq, (ctypes.c_int * 3)(*bc_lo),
+                         (ctypes.c_int * 3)(*bc_hi), prec)
+        h = _VP()
+        _check(lib.rt_create_grid(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.shape = (nfreq, nz, ny, nx)
+        self.cells = nx * ny * nz
+        self.nfreq = nfreq
+        self.prec = prec
+        self.n_angles = lib.rt_num_angles(h)
+
+    @classmethod
+    def from_problem(cls, p, prec=MIXED):
+        return cls(p.nx, p.ny, p.nz, p.n_mu, p.nf, p.bc_lo, p.bc_hi, p.dx, p.dy, p.dz, prec)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rt_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- helpers
+    def _in(self, x, n=None):
+        """(pointer, on_device, keepalive) for an input array of n float64 values."""
+        n = int(np.prod(self.shape)) if n is None else n
+        if _is_torch(x):
+            torch = _torch()
+            if not x.is_cuda:
+                x = x.detach().numpy()
+            else:
+                if x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != n:
+                    raise ValueError("device inputs must be contiguous float64 with the grid's size")
+                return x.data_ptr(), 1, x
+        a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        if a.size != n:
+            raise ValueError(f"expected {n} values, got {a.size}")
+        return a.ctypes.data, 0, a
+
+    def _opts(self, tol=1e-6, max_iter=1000, check_every=0, on_device=False):
+        s = None
+        if on_device:
+            s = _torch().cuda.current_stream().cuda_stream
+        return rt_solve_opts(tol, max_iter, check_every, s)
+
+    def _out(self, shape, on_device):
+        if on_device:
+            torch = _torch()
+            return torch.empty(shape, dtype=torch.float64, device="cuda")
+        return np.empty(shape, dtype=np.float64)
+
+    @staticmethod
+    def _ptr(a):
+        return a.data_ptr() if _is_torch(a) else a.ctypes.data
+
+    # -- API
+    def angles(self):
+        mu = np.empty((self.n_angles, 3))
+        w = np.empty(self.n_angles)
+        _check(load().rt_get_angles(self._h, mu.ctypes.data, w.ctypes.data))
+        return mu, w
+
+    def set_sweep_config(self, angles_per_group=0, cluster_ctas=0, threads=0):
+        _check(load().rt_set_sweep_config(self._h, angles_per_group, cluster_ctas, threads))
+
+    def set_opacity_source(self, chi, eps, B, freq_w=None):
+        pc, dc, kc = self._in(chi)
+        pe, de, ke = self._in(eps)
+        pb, db, kb = self._in(B)
+        if len({dc, de, db}) != 1:
+            raise ValueError("chi, eps and B must all be host or all be device arrays")
+        pw = None
+        kw = None
+        if freq_w is not None:
+            pw, dw, kw = self._in(freq_w, self.nfreq)
+            if dw != dc:
+                raise ValueError("freq_w must live where chi lives")
+        if dc:
+            _torch().cuda.current_stream().synchronize()
+        _check(load().rt_set_opacity_source(self._h, pc, pe, pb, pw, dc))
+        del kc, ke, kb, kw
+
+    def set_boundary_intensity(self, face, I):
+        a = np.ascontiguousarray(I, dtype=np.float64).reshape(-1)
+        _check(load().rt_set_boundary_intensity(self._h, int(face), a.ctypes.data))
+
+    def formal_solve(self, S=None, want_lstar=False, on_device=None):
+        ps, ds, ks = (None, 0, None) if S is None else self._in(S)
+        dev = bool(ds) if on_device is None else bool(on_device)
+        J = self._out(self.shape, dev)
+        L = self._out(self.shape, dev) if want_lstar else None
+        o = self._opts(on_device=dev)
+        _check(load().rt_formal_solve(self._h, ps, self._ptr(J), None if L is None else self._ptr(L),
+                                      1 if dev else 0, ctypes.byref(o)))
+        if dev:
+            _torch().cuda.current_stream().synchronize()
+        return (J, L) if want_lstar else J
+
+    def ali_solve(self, S_init=None, tol=1e-6, max_iter=1000, check_every=0, raise_on_fail=True):
+        ps, ds, ks = (None, 0, None) if S_init is None else self._in(S_init)
+        o = self._opts(tol, max_iter, check_every, on_device=bool(ds))
+        it = ctypes.c_int(0)
+        r = ctypes.c_double(0.0)
+        st = load().rt_ali_solve(self._h, ps, ds, ctypes.byref(o), ctypes.byref(it), ctypes.byref(r))
+        if st != RT_OK and (raise_on_fail or st != RT_ERR_NOT_CONVERGED):
+            _check(st)
+        return it.value, r.value, st
+
+    def moments(self, on_device=False):
+        nf = self.nfreq
+        sp = self.shape[1:]
+        out = dict(J=self._out((nf,) + sp, on_device), H=self._out((nf, 3) + sp, on_device),
+                   K=self._out((nf, 6) + sp, on_device), f=self._out((nf, 6) + sp, on_device),
+                   Q=self._out(sp, on_device))
+        o = self._opts(on_device=on_device)
+        _check(load().rt_moments(self._h, self._ptr(out["J"]), self._ptr(out["H"]), self._ptr(out["K"]),
+                                 self._ptr(out["f"]), self._ptr(out["Q"]), 1 if on_device else 0,
+                                 ctypes.byref(o)))
+        return out
+
+    def get_S(self, on_device=False):
+        S = self._out(self.shape, on_device)
+        o = self._opts(on_device=on_device)
+        _check(load().rt_get_S(self._h, self._ptr(S), 1 if on_device else 0, ctypes.byref(o)))
+        return S
+
+    def enable_timing(self, on=True):
+        _check(load().rt_enable_timing(self._h, 1 if on else 0))
+
+    def stats(self):
+        s = rt_stats()
+        _check(load().rt_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in rt_stats._fields_}

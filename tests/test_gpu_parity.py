@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances: the FP64 path must match the oracle to 1e-5 relative (it agrees to
+round-off in practice, so the tests use 1e-10); the mixed path (float32 sweeps,
+FP64 ALI) to 1e-3 relative in J, S and the heating rate, with the heating rate
+gated as |dQ| <= 1e-3 |Q| + 1e-6 4 pi chi_abs B where J ~ B makes Q cancel; the
+ALI iteration count must agree within one iteration.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1201_2222_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P, V, T, F = 0, 1, 2, 3
+TOL = {"fp64": 1e-10, "mixed": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1201_2222_gb300 import build, rt as _rt
+    build.build()
+    return _rt
+
+
+def make(rt, p, prec, **cfg):
+    g = rt.Grid.from_problem(p, prec=prec)
+    if cfg:
+        g.set_sweep_config(**cfg)
+    g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+    return g
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+# ------------------------------------------------------------- formal solution
+
+FS_CASES = [
+    # (nx, ny, nz, n_mu, bc_lo, bc_hi, sweep config)
+    (8, 7, 6, 4, (P, P, T), (P, P, V), {}),
+    (9, 5, 11, 6, (P, P, P), (P, P, P), dict(angles_per_group=2, cluster_ctas=3)),
+    (6, 8, 7, 8, (V, T, T), (T, V, V), dict(angles_per_group=8, cluster_ctas=2)),
+    (13, 6, 1, 6, (P, T, P), (P, V, P), {}),                 # 2D
+    (5, 17, 9, 2, (T, P, V), (T, P, T), dict(angles_per_group=1, cluster_ctas=4)),
+    (33, 31, 29, 4, (P, P, T), (P, P, V), dict(cluster_ctas=8)),   # several strips, ragged
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(len(FS_CASES)))
+def test_formal_solution_and_lambda_star(rt, prec, case):
+    nx, ny, nz, n_mu, lo, hi, cfg = FS_CASES[case]
+    p = W.random_box(nx, ny, nz, seed=100 + case, n_mu=n_mu, bc_lo=lo, bc_hi=hi)
+    g = make(rt, p, prec, **cfg)
+    og = O.Grid.from_problem(p)
+    rng = np.random.default_rng(case)
+    S = rng.uniform(0.3, 2.0, p.chi.shape)
+    J, L = g.formal_solve(S, want_lstar=True)
+    G = O.init_ghosts(og, S[0])
+    ref = O.formal_solution(og, p.chi[0], S[0], p.B[0], G_prev=G)
+    assert rel(J[0], ref["J"]) < TOL[prec]
+    assert rel(L[0], ref["lstar"]) < (1e-10 if prec == "fp64" else 1e-5)
+    # lagged periodic ghosts: further formal solutions from the previous ones
+    G = ref["G_next"]
+    for _ in range(2):
+        J = g.formal_solve(None)
+        ref = O.formal_solution(og, p.chi[0], S[0], p.B[0], G_prev=G)
+        G = ref["G_next"]
+        assert rel(J[0], ref["J"]) < TOL[prec]
+
+
+def test_fixed_boundary_searchlight(rt):
+    """Beam test (Sec. 5.2) in vacuum with user incident intensities on one face."""
+    z = np.zeros((1, 10, 12, 12))
+    p = W.Problem(name="beam", nx=12, ny=12, nz=10, n_mu=4, chi=z, eps=np.ones_like(z), B=z,
+                  freq_w=np.ones(1), bc_lo=(P, P, F), bc_hi=(P, P, V))
+    og = O.Grid.from_problem(p)
+    I = np.zeros((1, og.na, 12, 12))
+    I[0, 0, 3, 4] = 2.0
+    I[0, 1, 7, 2] = 1.0
+    faces = [np.zeros(og.na * og.face[f // 2]) for f in range(6)]
+    faces[4] = I.reshape(-1)
+    Ifix = np.concatenate(faces)
+    for prec in ("fp64", "mixed"):
+        g = make(rt, p, prec)
+        g.set_boundary_intensity(4, I)
+        G = O.init_ghosts(og, p.B[0])
+        for it in range(3):
+            J = g.formal_solve(p.B if it == 0 else None)
+            ref = O.formal_solution(og, p.chi[0], p.B[0], p.B[0], G_prev=G, I_fixed=Ifix)
+            G = ref["G_next"]
+            np.testing.assert_allclose(J[0], ref["J"], rtol=TOL[prec], atol=1e-12)
+
+
+# ------------------------------------------------------------------ ALI solves
+
+def _compare_solve(rt, p, prec, tol=None, cfg=None, max_iter=3000):
+    tol = p.tol if tol is None else tol
+    og, ref = O.solve_problem(p, tol=tol, max_iter=max_iter)
+    g = make(rt, p, prec, **(cfg or {}))
+    iters, resid, st = g.ali_solve(tol=tol, max_iter=max_iter)
+    assert st == rt.RT_OK
+    assert abs(iters - ref["iters"]) <= 1, (iters, ref["iters"])
+    S = g.get_S()
+    m = g.moments()
+    t = TOL[prec]
+    if prec == "fp64":
+        assert iters == ref["iters"]
+        assert rel(S, ref["S"]) < 1e-8
+        assert rel(m["J"], ref["J"]) < 1e-8
+    else:
+        # both stop within delta_c of the same fixed point
+        assert rel(S, ref["S"]) < t
+        assert rel(m["J"], ref["J"]) < t
+    H = m["H"]
+    for q in range(3):
+        scale = np.abs(ref["J"]).max()
+        assert np.abs(H[:, q] - ref["H"][:, q]).max() < t * scale
+    assert rel(m["K"][:, 0] + m["K"][:, 1] + m["K"][:, 2], ref["K"][:, 0] + ref["K"][:, 1] + ref["K"][:, 2]) < max(t, 1e-8)
+    np.testing.assert_allclose(m["f"][:, 0] + m["f"][:, 1] + m["f"][:, 2], 1.0, rtol=1e-5 if prec == "mixed" else 1e-12)
+    floor = 1e-6 * 4 * math.pi * np.sum(p.freq_w[:, None, None, None] * p.eps * p.chi * p.B, axis=0)
+    dQ = np.abs(m["Q"] - ref["Q"])
+    assert np.all(dQ <= max(t, 1e-8) * np.abs(ref["Q"]) + floor + 1e-300)
+    return iters, ref["iters"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stratified_atmosphere_32(rt, prec):
+    """32^3 scattering atmosphere, eps = 1e-2, 24 rays, delta_c = 1e-6 (full size)."""
+    p = W.stratified_atmosphere(32)
+    it, rit = _compare_solve(rt, p, prec)
+    assert rit > 50
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_turbulent_box_small(rt, prec):
+    """Periodic log-normal box with 80 rays at 24^3 (the 128^3 workload's structure)."""
+    p = W.turbulent_box(24, n_mu=8)
+    _compare_solve(rt, p, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_multifrequency_small(rt, prec):
+    """Frequency-dependent absorption over 8 bins at 16^3 (all bins in one launch)."""
+    p = W.multifrequency_atmosphere(16, nf=8)
+    _compare_solve(rt, p, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_random_media_every_boundary(rt, prec):
+    p = W.random_box(7, 9, 6, seed=5, n_mu=6, nf=2, bc_lo=(T, P, V), bc_hi=(V, P, T))
+    _compare_solve(rt, p, prec, tol=1e-8)
+
+
+def test_lte_uses_change_of_J(rt):
+    """All eps = 1: S stays B and the stop test is the change of J (Sec. 3.4)."""
+    p = W.random_box(8, 8, 8, seed=7, n_mu=4, eps_range=(1.0, 1.0),
+                     bc_lo=(P, P, P), bc_hi=(P, P, P))
+    _compare_solve(rt, p, "fp64", tol=1e-9)
+
+
+def test_not_converged_keeps_state(rt):
+    p = W.stratified_atmosphere(16, nxy=8)
+    g = make(rt, p, "fp64")
+    iters, resid, st = g.ali_solve(tol=1e-12, max_iter=7, raise_on_fail=False)
+    assert st == rt.RT_ERR_NOT_CONVERGED and iters == 7 and resid > 1e-12
+    og = O.Grid.from_problem(p)
+    ref = O.ali_solve(og, p.chi, p.eps, p.B, tol=1e-12, max_iter=7, moments=False)
+    np.testing.assert_allclose(g.get_S(), ref["S"], rtol=1e-10)
+
+
+def test_warm_start_and_determinism(rt):
+    p = W.turbulent_box(16, n_mu=4)
+    g = make(rt, p, "mixed")
+    i1, _, _ = g.ali_solve(tol=1e-6)
+    S1 = g.get_S()
+    i2, _, _ = g.ali_solve(tol=1e-6)
+    assert np.array_equal(S1, g.get_S()) and i1 == i2      # bitwise repeatable
+    i3, _, _ = g.ali_solve(S_init=S1, tol=1e-6)            # warm start from the solution
+    assert i3 < i1 / 2
+
+
+def test_device_pointers_match_host(rt):
+    p = W.random_box(10, 9, 8, seed=3, n_mu=4, nf=2)
+    g = make(rt, p, "mixed")
+    Jh = g.formal_solve(p.B)
+    g2 = rt.Grid.from_problem(p, prec="mixed")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g2.set_opacity_source(dev(p.chi), dev(p.eps), dev(p.B), dev(p.freq_w))
+    Jd = g2.formal_solve(dev(p.B))
+    assert isinstance(Jd, torch.Tensor) and Jd.is_cuda
+    assert np.array_equal(Jh, Jd.cpu().numpy())
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_input_validation(rt):
+    p = W.random_box(4, 4, 4, seed=1)
+    g = rt.Grid.from_problem(p)
+    for bad in ("chi", "eps0", "eps2", "B", "nan"):
+        chi, eps, B = p.chi.copy(), p.eps.copy(), p.B.copy()
+        if bad == "chi":
+            chi[0, 1, 1, 1] = -1
+        elif bad == "eps0":
+            eps[0, 0, 0, 0] = 0.0
+        elif bad == "eps2":
+            eps[0, 0, 0, 0] = 1.5
+        elif bad == "B":
+            B[0, 2, 2, 2] = -0.1
+        else:
+            chi[0, 3, 3, 3] = np.nan
+        with pytest.raises(rt.RTError) as e:
+            g.set_opacity_source(chi, eps, B)
+        assert e.value.status == rt.RT_ERR_ARG
+    with pytest.raises(rt.RTError) as e:
+        g.ali_solve()
+    assert e.value.status == rt.RT_ERR_STATE
+    with pytest.raises(rt.RTError) as e:
+        rt.Grid(4, 4, 4, n_mu=5)
+    assert e.value.status == rt.RT_ERR_ARG
+    with pytest.raises(rt.RTError):
+        rt.Grid(4, 4, 4, bc_lo=(P, P, T), bc_hi=(V, P, V))   # half-periodic axis
+
+
+def test_moments_before_solve_is_state_error(rt):
+    p = W.random_box(4, 4, 4, seed=2)
+    g = make(rt, p, "mixed")
+    g.ali_solve()          # fine
+    g2 = rt.Grid.from_problem(p)
+    g2.set_opacity_source(p.chi, p.eps, p.B)
+    with pytest.raises(rt.RTError) as e:
+        g2.moments()
+    assert e.value.status == rt.RT_ERR_STATE
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 3), (6, 1, 4), (2, 3, 1), (1, 1, 7)])
+def test_degenerate_shapes(rt, shape):
+    nx, ny, nz = shape
+    p = W.random_box(nx, ny, nz, seed=11, n_mu=4, bc_lo=(P, P, T), bc_hi=(P, P, V))
+    g = make(rt, p, "fp64")
+    og = O.Grid.from_problem(p)
+    J = g.formal_solve(p.B)
+    ref = O.formal_solution(og, p.chi[0], p.B[0], p.B[0])
+    assert rel(J[0], ref["J"]) < 1e-10
+
+
+# ------------------------------------------------------------ full-size sample
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_turbulent_box_128_formal_solution(rt, prec):
+    """The 128^3, 80-ray box in the launch configuration the benchmark uses: one
+    formal solution against the oracle at full size (oracle on all host cores)."""
+    p = W.turbulent_box(128, n_mu=8)
+    g = make(rt, p, prec)
+    J = g.formal_solve(p.B)
+    og = O.Grid.from_problem(p)
+    ref = O.formal_solution(og, p.chi[0], p.B[0], p.B[0], nthreads=O.max_threads())
+    assert rel(J[0], ref["J"]) < TOL[prec]
