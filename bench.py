@@ -1,0 +1,365 @@
+"""Benchmark: converged short-characteristics + Jacobi-ALI solves of the 128^3 box.
+
+Workload: a 128^3 fully periodic box with a log-normal turbulent density
+(k^-11/3 Gaussian random fields, seeds 1 and 2), grey LTE absorption plus
+electron scattering, B = T^4, 80 rays (LQ8), float32 sweeps with the FP64 ALI
+update, solved to max|dS|/S <= 1e-6.  Synthetic inputs, generated here.
+
+One step = the whole hot path on resident device inputs: set the medium
+(validation, sweep-precision copies, Lambda*, ghosts), the ALI solve to
+convergence (formal solutions + updates), and the outputs (J, H, K, K/J, Q).
+Metric: cell*ray*frequency updates per second (updates = cells * rays *
+frequencies * formal solutions).  The L2 cache is flushed (256 MB written)
+before every timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own copy (independent solves, no data-path
+collective: weak scaling); rank 0 prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell*ray*nu updates/s"
+UNIT = "updates/s"
+N_BOX = 128
+N_MU = 8
+TOL = 1e-6
+FLOPS_PER_UPDATE = 36        # algorithmic FP32 operations of one cell*ray update
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload():
+    from paper_1201_2222_gb300 import workloads as W
+    return W.turbulent_box(N_BOX, n_mu=N_MU, tol=TOL)
+
+
+def config_dict(p, flush):
+    return {"workload": f"turbulent_box_{p.nx}^3_LQ{p.n_mu}_{p.n_angles}rays_grey_eps_var_tol{TOL:g}",
+            "cells": p.cells, "rays": p.n_angles, "frequencies": p.nf,
+            "precision": "float32 sweeps, FP64 ALI", "l2": flush}
+
+
+# --------------------------------------------------------------- multi-rank glue
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard(n_units: int, rank: int, world: int) -> list:
+    """Units (independent solves) owned by this rank: a contiguous balanced slice."""
+    base, extra = divmod(n_units, world)
+    lo = rank * base + min(rank, extra)
+    return list(range(lo, lo + base + (1 if rank < extra else 0)))
+
+
+def reduce_max_sum(t_local: float, u_local: float, dist) -> tuple:
+    """(max over ranks of the timed seconds, sum over ranks of the updates)."""
+    if dist is None:
+        return t_local, u_local
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([u_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv",
+                                          "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[1].split()[0].isdigit():
+                continue
+            sm.append(float(parts[1].split()[0]))
+            mx.append(float(parts[2].split()[0]))
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- CPU baseline
+
+def oracle_rate(p, min_seconds=10.0, max_runs=3):
+    """The FP64 CPU oracle's formal-solution rate on this workload (all host cores)."""
+    from oracle import oracle as O
+    og = O.Grid.from_problem(p)
+    nt = O.max_threads()
+    S = p.B[0]
+    runs, t_total = 0, 0.0
+    while runs < max_runs and (runs == 0 or t_total < min_seconds):
+        t = time.perf_counter()
+        O.formal_solution(og, p.chi[0], S, p.B[0], nthreads=nt)
+        t_total += time.perf_counter() - t
+        runs += 1
+    upd = runs * og.cells * og.na * p.nf
+    return {"value": upd / t_total, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"{runs} FP64 formal solution(s) of the full {p.nx}^3 x {og.na}-ray box "
+                      f"({og.cells * og.na:,} updates each), {t_total:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = workload()
+    from oracle import oracle as O
+    og = O.Grid.from_problem(p)
+    nt = O.max_threads()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        O.formal_solution(og, p.chi[0], p.B[0], p.B[0], nthreads=nt)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    upd = og.cells * og.na * p.nf
+    value = upd * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(p, "n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": f"each step one FP64 formal solution of the full box "
+                                       f"({upd:,} updates)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_1201_2222_gb300 import build, rt
+    build.build()
+    p = workload()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chi = torch.from_numpy(p.chi).to(dev)
+    eps = torch.from_numpy(p.eps).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    fw = torch.from_numpy(p.freq_w).to(dev)
+    g = rt.Grid.from_problem(p, prec=rt.MIXED)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(out):
+        g.set_opacity_source(chi, eps, B, fw)
+        iters, resid, st = g.ali_solve(tol=TOL, max_iter=2000)
+        m = g.moments(on_device=True)
+        out.append((iters, resid, g.stats()))
+        return m
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    rec = []
+    ev = []
+    g.enable_timing(True)
+    launches0 = g.stats()["kernel_launches"]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(rec)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall1 = time.perf_counter()
+    clk = clocks.stop()
+    g.enable_timing(False)
+    launches = g.stats()["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    upd_local = float(sum(s["updates"] for _, _, s in rec))
+    t_max, upd_all = reduce_max_sum(t_local, upd_local, dist)
+    iters = [i for i, _, _ in rec]
+    sweep_ms = sum(s["sweep_ms"] for _, _, s in rec)
+    sweep_n = sum(s["sweep_launches"] for _, _, s in rec)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if True:
+        e2e_t = []
+        e2e_upd = 0
+        N = p.chi.size
+        h2d = 3 * N * 8 + p.nf * 8
+        d2h = (N + p.cells) * 8
+        for i in range(1 + max(2, args.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+            it, _, _ = g.ali_solve(tol=TOL, max_iter=2000)
+            m = g.moments(on_device=False)
+            _ = float(m["Q"].sum())
+            dt = time.perf_counter() - t
+            if i > 0:
+                e2e_t.append(dt)
+                e2e_upd += p.cells * p.n_angles * p.nf * it
+        e2e_local = sum(e2e_t)
+        e2e_tmax, e2e_updall = reduce_max_sum(e2e_local, float(e2e_upd), dist)
+        e2e = {"value": e2e_updall / e2e_tmax, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # plain FP64 GPU path for the mixed-vs-FP64 solves/s comparison (2 solves)
+    fp64 = None
+    if not args.skip_fp64:
+        g64 = rt.Grid.from_problem(p, prec=rt.FP64)
+        g64.set_opacity_source(chi, eps, B, fw)
+        g64.ali_solve(tol=TOL, max_iter=2000)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        it64, _, _ = g64.ali_solve(tol=TOL, max_iter=2000)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t
+        fp64 = {"solves_per_s": 1.0 / t64, "iters": it64,
+                "updates_per_s": p.cells * p.n_angles * p.nf * it64 / t64}
+        g64.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = oracle_rate(p) if ws == 1 and not args.skip_cpu else None
+    per_launch_upd = p.cells * p.n_angles * p.nf
+    avg_launch_s = (sweep_ms / sweep_n) / 1e3 if sweep_n else float("nan")
+    achieved = FLOPS_PER_UPDATE * per_launch_upd / avg_launch_s / 1e12
+    clock_for_peak = 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_for_peak * 1e6 / 1e12
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": upd_all / t_max, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_dict(p, "flushed (256 MB written) before every timed step"),
+        "solves_per_s": ws * args.steps / t_max,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+        "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
+        "fp64_path": fp64,
+        "roofline": {"bound": "alu", "kernel": "sc_sweep_kernel<float>", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
+                     "flops_per_update": FLOPS_PER_UPDATE, "avg_launch_ms": avg_launch_s * 1e3,
+                     "launches": sweep_n},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s": wall1 - wall0,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """Short run for profilers: set the medium and do a few ALI iterations of the
+    same workload (no warm-up loop, no baselines)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1201_2222_gb300 import build, rt
+    build.build()
+    p = workload()
+    g = rt.Grid.from_problem(p, prec=rt.FP64 if args.fp64 else rt.MIXED)
+    g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+    it, resid, st = g.ali_solve(tol=TOL, max_iter=args.profile_iters, raise_on_fail=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": p.name, "iters": it, "resid": resid}), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU comparison solves")
+    ap.add_argument("--profile", action="store_true", help="one short solve for profilers")
+    ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

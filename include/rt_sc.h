@@ -3,13 +3,13 @@
  *
  * The library solves the time-independent, multi-frequency transfer equation
  *     n . grad I_nu = chi_nu (S_nu - I_nu),   S_nu = eps_nu B_nu + (1 - eps_nu) J_nu
- * (Davis, Stone & Jiang 2012, Eqs. 3-5) on a uniform 3D or 2D Cartesian grid with
+ * (Davis, Stone & Jiang 2012, Eqs. 8-9) on a uniform 3D or 2D Cartesian grid with
  *   - the short-characteristics formal solution with linear upwind-face
- *     interpolation and exponential segment weights (Sec. 3.3, Eq. 25),
- *   - the discrete moments J, H, K (Eqs. 22-24) and the diagonal Lambda*
+ *     interpolation and exponential segment weights (Sec. 3.3, Eq. 20),
+ *   - the discrete moments J, H, K (Eqs. 17-19) and the diagonal Lambda*
  *     (Sec. 3.4, Olson & Kunasz 1987),
- *   - Jacobi accelerated Lambda iteration (Sec. 3.4, Eq. 30) with the
- *     max |dS|/S convergence test (Eq. 31),
+ *   - Jacobi accelerated Lambda iteration (Sec. 3.4, Eq. 24) with the
+ *     max |dS|/S convergence test (Eq. 25),
  *   - the integral-form heating rate and the Eddington tensor K/J (Sec. 4).
  *
  * Conventions shared by every call:
@@ -73,7 +73,7 @@ typedef struct {
 } rt_grid_desc;
 
 typedef struct {
-  double tol;            /* delta_c of Eq. 31 (e.g. 1e-6) */
+  double tol;            /* delta_c of Eq. 25 (e.g. 1e-6) */
   int max_iter;          /* maximum formal solutions per solve */
   int check_every;       /* formal solutions enqueued between host checks; 0 = automatic */
   void *stream;          /* cudaStream_t to run on; NULL = the grid's own stream */
@@ -88,7 +88,7 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out);
 rt_status rt_destroy_grid(rt_grid g);
 
 /* Number of rays and the angle table: mu [n_angles][3] (direction cosines) and
- * w [n_angles] (weights, sum 1; Eq. 22 carries no 4 pi).  Either pointer may be
+ * w [n_angles] (weights, sum 1; Eq. 17 carries no 4 pi).  Either pointer may be
  * NULL.  Order: octant o = 0..7 with signs (-1 if o&1, -1 if o&2, -1 if o&4) for
  * (x, y, z), in 2D only the octants with mu_z > 0 (weights doubled); within an
  * octant level indices i outer, j inner, l = n_mu/2 + 2 - i - j. */
@@ -119,7 +119,7 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
  * the face is not RT_BC_FIXED. */
 rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I);
 
-/* One formal solution J = Lambda[S] (Sec. 3.4, Eq. 26) without an S update.
+/* One formal solution J = Lambda[S] (Sec. 3.4, Eq. 21) without an S update.
  * S: [nf][nz][ny][nx] or NULL to use the grid's current S; when S is given the
  * periodic ghosts are reset to the image cells' S (first-iteration semantics),
  * otherwise the lagged ghosts of the previous formal solution are used and
@@ -128,7 +128,7 @@ rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I);
 rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out,
                           int on_device, const rt_solve_opts *opts);
 
-/* Jacobi ALI to max|dS|/S <= opts->tol (Eqs. 30-31).  S_init [nf][nz][ny][nx]
+/* Jacobi ALI to max|dS|/S <= opts->tol (Eqs. 24-25).  S_init [nf][nz][ny][nx]
  * (device or host per on_device) or NULL to start from S = B.  Periodic ghosts
  * start as the image cells' S.  When every eps == 1 the stopping test uses the
  * change of J between consecutive formal solutions.  iters_out: formal
@@ -151,8 +151,10 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
 
 /* Device-time record of the latest rt_ali_solve / rt_formal_solve call, taken
  * with CUDA events on the launching stream when enabled.  sweep_ms: summed
- * duration of the formal-solution kernel launches; sweep_launches: how many;
- * total_ms: the whole solve; kernel_launches: all kernels the library launched. */
+ * duration of the formal-solution kernel launches that did work; sweep_launches:
+ * how many; total_ms: the whole solve; kernel_launches: all kernels this grid has
+ * launched since it was created (cumulative); updates: cell * ray * frequency
+ * updates of the latest call. */
 typedef struct {
   int iters;
   double resid;

@@ -2,15 +2,15 @@
 
 Follows Davis, Stone & Jiang (2012):
   * ``formal_solution``  - one short-characteristics formal solution J = Lambda[S]
-    (Sec. 3.3, Eq. 25 with linear interpolation), also returning the diagonal
-    Lambda* (Sec. 3.4, Olson & Kunasz 1987) and, on request, H and K (Eqs. 23-24).
+    (Sec. 3.3, Eq. 20 with linear interpolation), also returning the diagonal
+    Lambda* (Sec. 3.4, Olson & Kunasz 1987) and, on request, H and K (Eqs. 18-19).
     The sweep itself is the C function in ``sc_oracle.c``.
   * ``init_ghosts``      - first-iteration periodic ghost intensities: I = S of the
     periodic image cell (the paper lags incoming periodic/subdomain intensities
     by one iteration, Sec. 3; with no previous iteration the image S is used).
-  * ``ali_solve``        - Jacobi ALI (Eq. 30):
+  * ``ali_solve``        - Jacobi ALI (Eq. 24):
         dS = [(1 - eps) J + eps B - S] / [1 - (1 - eps) Lambda*],  S <- S + dS,
-    stopped when max |dS|/S <= delta_c (Eq. 31); when every eps = 1 the test uses
+    stopped when max |dS|/S <= delta_c (Eq. 25); when every eps = 1 the test uses
     the change of J between consecutive formal solutions (Sec. 3.4).  The
     iteration count is the number of formal solutions performed.
   * ``heating_rate``     - Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu) (Sec. 4, Q^int).
@@ -166,7 +166,7 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
 
 
 def max_relative_change(dS: np.ndarray, S: np.ndarray) -> float:
-    """max_i |dS_i|/|S_i| (Eq. 31); a cell with S_i = 0 counts 0 if dS_i = 0, else inf."""
+    """max_i |dS_i|/|S_i| (Eq. 25); a cell with S_i = 0 counts 0 if dS_i = 0, else inf."""
     a = np.abs(dS)
     s = np.abs(S)
     with np.errstate(divide="ignore", invalid="ignore"):
@@ -182,7 +182,7 @@ def heating_rate(chi, eps, J, B, freq_w):
 
 def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_init=None,
               I_fixed=None, nthreads=1, moments=True):
-    """Jacobi ALI to max|dS|/S <= tol (Eqs. 30-31), all frequencies per iteration.
+    """Jacobi ALI to max|dS|/S <= tol (Eqs. 24-25), all frequencies per iteration.
 
     chi, eps, B: [nf][nz][ny][nx].  I_fixed: None or a list (per frequency) of
     user boundary arrays.  Returns dict(S, J, lstar, H, K, f, Q, iters, resid,

@@ -20,7 +20,7 @@ Angle order (shared contract with the library, because user boundary arrays
 are indexed by angle): octant o = 0..7 with signs
 (sx, sy, sz) = (-1 if o & 1 else +1, -1 if o & 2 else +1, -1 if o & 4 else +1);
 inside an octant, i = 1..n_mu/2 outer, j inner, l = n_mu/2 + 2 - i - j.
-Weights sum to 1 over the sphere (Eq. 22 has no 4 pi).
+Weights sum to 1 over the sphere (Eq. 17 has no 4 pi).
 
 Parity: pinned by tests/test_oracle_quadrature.py (moment identities, the closed
 form of LQ4, published LQ6/LQ8 tables, exact integration of low-order

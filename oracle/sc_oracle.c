@@ -14,9 +14,9 @@
  *     interpolants of the four face vertices (Sec. 3.3, linear interpolation);
  *   - dtau = (chi- + chi0) s / 2;  E = exp(-dtau);  e0 = 1 - E;
  *     Psi0 = (dtau - e0)/dtau (a Taylor series below dtau = 1e-3); Psi- = e0 - Psi0;
- *     I0 = I- E + Psi- S- + Psi0 S0  (Eq. 25 with the linear form, Psi+ = 0);
- *   - J = sum_k w_k I_k (Eq. 22), Lambda*_ii = sum_k w_k Psi0_k (Sec. 3.4),
- *     H_i = sum_k w_k I_k mu_ik (Eq. 23), K_ij = sum_k w_k I_k mu_ik mu_jk (Eq. 24).
+ *     I0 = I- E + Psi- S- + Psi0 S0  (Eq. 20 with the linear form, Psi+ = 0);
+ *   - J = sum_k w_k I_k (Eq. 17), Lambda*_ii = sum_k w_k Psi0_k (Sec. 3.4),
+ *     H_i = sum_k w_k I_k mu_ik (Eq. 18), K_ij = sum_k w_k I_k mu_ik mu_jk (Eq. 19).
  *
  * Boundaries (Sec. 3.5): a vertex outside the domain is a ghost vertex.  chi and S
  * there are those of the periodic image (periodic axis) or of the adjacent

@@ -263,6 +263,7 @@ struct rt_grid_s {
   void *chiP[3] = {nullptr, nullptr, nullptr};
   void *SP[3] = {nullptr, nullptr, nullptr};
   void *G[2] = {nullptr, nullptr};
+  void *Gd[2] = {nullptr, nullptr};   // ghost increments (mixed-precision incremental solves)
   void *Ibc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *user_bc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void *Jpart = nullptr;
@@ -282,6 +283,8 @@ struct rt_grid_s {
   bool lte = false;
   int fs_total = 0;                // formal solutions since the ghosts were initialised
   bool last_fs_from_Sfs = false;   // the latest formal solution used Sfs (ALI) or S
+  bool last_incremental = false;   // the latest solve accumulated J from swept increments
+  bool sp_is_delta = false;        // the sweep copies of S hold the last increment
 
   bool timing = false;
   rt_stats stats{};
@@ -533,6 +536,9 @@ rtk::SweepArgs<T> sweep_args(rt_grid g) {
   }
   A.G[0] = (T *)g->G[0];
   A.G[1] = (T *)g->G[1];
+  A.Gd[0] = (T *)g->Gd[0];
+  A.Gd[1] = (T *)g->Gd[1];
+  A.incremental = 0;
   for (int f = 0; f < 6; ++f) A.Ibc[f] = (const T *)g->Ibc[f];
   A.ang = (const AngleParam<T> *)g->angp;
   A.grp = g->grp;
@@ -569,18 +575,26 @@ rt_status enqueue_sweep(rt_grid g, rtk::SweepArgs<T> &A, bool moments, cudaStrea
   return RT_OK;
 }
 
-rt_status collect_events(std::vector<EventPair> &ev, double *ms_out, int *n_out) {
+// Sums the first `first_n` recorded sweep durations (later ones were launches
+// enqueued after convergence that returned at once) and releases all events.
+rt_status collect_events(std::vector<EventPair> &ev, double *ms_out, int *n_out, size_t first_n) {
   double ms = 0.0;
-  for (auto &p : ev) {
-    float t = 0.0f;
-    CU(cudaEventElapsedTime(&t, p.a, p.b));
-    ms += t;
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+  int n = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t i = 0; i < ev.size(); ++i) {
+    if (i < first_n && err == cudaSuccess) {
+      float t = 0.0f;
+      err = cudaEventElapsedTime(&t, ev[i].a, ev[i].b);
+      ms += t;
+      ++n;
+    }
+    cudaEventDestroy(ev[i].a);
+    cudaEventDestroy(ev[i].b);
   }
-  *ms_out = ms;
-  *n_out = (int)ev.size();
   ev.clear();
+  CU(err);
+  *ms_out = ms;
+  *n_out = n;
   return RT_OK;
 }
 
@@ -591,7 +605,11 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   const int max_iter = opts && opts->max_iter > 0 ? opts->max_iter : 1000;
   CU(rtk::launch_state_op(g->st, 0, max_iter, tol, g->lte ? 1 : 0, s));
   g->launches++;
+  // The mixed path sweeps increments after the first formal solution so that
+  // float32 rounding scales with the update, not with S (J accumulated in FP64).
+  const int incremental = g->desc.prec == RT_PREC_MIXED ? 1 : 0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
+  A.incremental = incremental;
   rtk::AliArgs<T> L{};
   L.d = g->d;
   L.ngroups_per_f = (int)g->groups.size();
@@ -606,6 +624,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   for (int a = 0; a < 3; ++a) L.SP[a] = g->used_axis[a] ? (T *)g->SP[a] : nullptr;
   L.st = g->st;
   L.lte = g->lte ? 1 : 0;
+  L.incremental = incremental;
   std::vector<EventPair> ev;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (g->timing) {
@@ -639,7 +658,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     g->stats.total_ms = tt;
-    rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches);
+    rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches, (size_t)hs.iter);
     if (r != RT_OK) return r;
   }
   *iters = hs.iter;
@@ -647,6 +666,8 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   *converged = hs.converged != 0;
   g->fs_total = hs.fs_count;
   g->last_fs_from_Sfs = !g->lte;
+  g->last_incremental = incremental != 0;
+  g->sp_is_delta = incremental != 0;
   return RT_OK;
 }
 
@@ -662,12 +683,14 @@ rt_status formal_once(rt_grid g, cudaStream_t s) {
   g->launches += 2;
   if (g->timing) {
     CU(cudaStreamSynchronize(s));
-    r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches);
+    r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches, ev.size());
     if (r != RT_OK) return r;
     g->stats.total_ms = g->stats.sweep_ms;
   }
   g->fs_total += 1;
   g->last_fs_from_Sfs = false;
+  g->last_incremental = false;
+  g->sp_is_delta = false;
   return RT_OK;
 }
 
@@ -774,6 +797,10 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
   const size_t gbytes = (size_t)d.nf * g->na * d.gsize * ts;
   ALLOC(g->G[0], gbytes);
   ALLOC(g->G[1], gbytes);
+  if (D.prec == RT_PREC_MIXED) {
+    ALLOC(g->Gd[0], gbytes);
+    ALLOC(g->Gd[1], gbytes);
+  }
   for (int f = 0; f < 6; ++f) {
     if (d.periodic[f / 2]) continue;
     ALLOC(g->Ibc[f], (size_t)d.nf * g->na * d.face[f / 2] * ts);
@@ -784,6 +811,8 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
 #undef ALLOC
   if (cudaMemset(g->st, 0, sizeof(rtk::SolveState)) != cudaSuccess ||
       cudaMemset(g->G[0], 0, gbytes) != cudaSuccess || cudaMemset(g->G[1], 0, gbytes) != cudaSuccess ||
+      (g->Gd[0] && cudaMemset(g->Gd[0], 0, gbytes) != cudaSuccess) ||
+      (g->Gd[1] && cudaMemset(g->Gd[1], 0, gbytes) != cudaSuccess) ||
       cudaMemcpy(g->rays_d, g->rays.data(), g->na * sizeof(RayGeom), cudaMemcpyHostToDevice) != cudaSuccess)
     return cleanup(fail(RT_ERR_CUDA, "initialisation copy failed"));
   rt_status r = upload_plan_any(g);
@@ -799,6 +828,7 @@ rt_status rt_destroy_grid(rt_grid g) {
   if (g->own) cudaStreamSynchronize(g->own);
   void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
+                  g->Gd[0], g->Gd[1],
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
                   g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
                   g->Jpart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp};
@@ -913,11 +943,13 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
   }
   const size_t N = (size_t)N_of(g);
   rt_status r;
-  g->launches = 0;
   if (S) {
     if ((r = copy_in(g, g->S, S, N, on_device, s)) != RT_OK) return r;
     if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
     if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  } else if (g->sp_is_delta) {
+    // the sweep copies hold the last increment: restore the full S
+    if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
   }
   r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
   if (r != RT_OK) return r;
@@ -939,7 +971,6 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
   if (s != g->own) CU(cudaStreamSynchronize(g->own));
   const size_t N = (size_t)N_of(g);
   rt_status r;
-  g->launches = 0;
   if (S_init) {
     if ((r = copy_in(g, g->S, S_init, N, on_device, s)) != RT_OK) return r;
   } else {
@@ -985,8 +1016,14 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
     CU(rtk::launch_reduce_moments<float>(g->d, (int)g->groups.size(), (const float *)g->Jpart,
                                          (const float *)g->Mpart, dJ, dH, dK, dF, g->two_d, s));
   }
+  if (g->last_incremental) {
+    // J of the last formal solution as the solve accumulated it in FP64
+    CU(cudaMemcpyAsync(dJ, g->J, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   CU(rtk::launch_heating(g->d, g->fw, g->chi, g->eps, dJ, g->B, dQ, s));
+  g->launches += 2;   // moment reduction + heating rate
   if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  g->sp_is_delta = false;   // the sweep copies hold the full S again
   if (J && (r = copy_out(J, dJ, N, on_device, s)) != RT_OK) return r;
   if (H && (r = copy_out(H, dH, 3 * N, on_device, s)) != RT_OK) return r;
   if (K && (r = copy_out(K, dK, 6 * N, on_device, s)) != RT_OK) return r;
@@ -1015,6 +1052,7 @@ rt_status rt_enable_timing(rt_grid g, int enable) {
 rt_status rt_get_stats(rt_grid g, rt_stats *out) {
   if (!g || !out) return fail(RT_ERR_ARG, "NULL argument");
   *out = g->stats;
+  out->kernel_launches = g->launches;
   return RT_OK;
 }
 

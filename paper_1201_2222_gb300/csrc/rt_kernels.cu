@@ -1,7 +1,7 @@
 // CUDA kernels of the short-characteristics library (sm_103a).
 //
 //   sc_sweep_kernel   formal solution of one sweep group for one frequency (Sec. 3.3)
-//   ali_update_kernel Jacobi ALI update, FP64 (Sec. 3.4, Eq. 30) + max |dS|/S (Eq. 31)
+//   ali_update_kernel Jacobi ALI update, FP64 (Sec. 3.4, Eq. 24) + max |dS|/S (Eq. 25)
 //   lstar_kernel      diagonal Lambda* = sum_k w_k Psi0_k (Sec. 3.4)
 //   finish_kernel     convergence decision and ghost-parity advance (one thread)
 //   plus set-up kernels: validation, permuted sweep copies, ghost initialisation,
@@ -85,7 +85,8 @@ __device__ __forceinline__ long long face_cell(const Dims &d, int ax, const int 
 // out-of-range axis in the same order.
 template <typename T>
 __device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
-                                     int Nw, int f, int angle, const T *Gp, int u, int v, int w) {
+                                     int Nw, int f, int angle, const T *Gp, bool inc, int u, int v,
+                                     int w) {
   int crd[3];
   crd[cax[0]] = u;
   crd[cax[1]] = v;
@@ -102,6 +103,7 @@ __device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], in
 #pragma unroll
   for (int ax = 2; ax >= 0; --ax) {
     if (oor[ax] && !A.d.periodic[ax]) {
+      if (inc) return T(0);   // fixed inflow does not change between formal solutions
       const int face = 2 * ax + side[ax];
       const long long idx = ((long long)f * A.na + angle) * A.d.face[ax] + face_cell<T>(A.d, ax, m);
       return A.Ibc[face][RT_IDX(idx, (long long)A.d.nf * A.na * A.d.face[ax], 11)];
@@ -117,12 +119,28 @@ __device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], in
   return Gp[RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 12)];
 }
 
+// Outflow intensity onto a periodic face for the next formal solution.  Full
+// solutions store I; the first one of an incremental solve also stores its
+// change against the ghost it replaces; incremental ones store the change and
+// advance the full ghost by it.
+template <typename T>
+__device__ __forceinline__ void ghost_store(const T *Gp, T *Gn, T *Gdn, long long off, T I0, bool inc,
+                                            bool emit) {
+  if (inc) {
+    Gdn[off] = I0;
+    Gn[off] = Gp[off] + I0;
+  } else {
+    if (emit) Gdn[off] = I0 - Gp[off];
+    Gn[off] = I0;
+  }
+}
+
 // One sweep group (rays sharing the crossed-face axis a and sign(mu_a)) for one
 // frequency.  The plane normal to a is split into C strips of rows (v) over the C
 // CTAs of a cluster.  Every step computes one plane from the previous plane:
 //   I- , S-, chi- bilinear on the upwind face (weights wa..wd of the ray),
 //   dtau = (chi- + chi0) s/2,  I0 = S- + E (I- - S-) + Psi0 (S0 - S-),
-// which equals I- E + Psi- S- + Psi0 S0 with Psi- = 1 - E - Psi0 (Eq. 25, linear).
+// which equals I- E + Psi- S- + Psi0 S0 with Psi- = 1 - E - Psi0 (Eq. 20, linear).
 // The previous plane's intensities live in shared memory (double-buffered); a
 // strip's edge row comes from the neighbouring CTA's shared memory (DSMEM).
 // J partial of the group is the FP-T sum over its rays, written once per cell.
@@ -160,6 +178,13 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   const int prev = fs & 1;
   const T *Gp = A.G[prev];
   T *Gn = A.G[prev ^ 1];
+  // Incremental ALI solves: the first formal solution is a full one that also
+  // records its ghost increments; every later one sweeps dS with the ghost
+  // increments as inflow (zero at fixed faces) and keeps the full ghosts current.
+  const bool inc = A.incremental && A.st->iter > 0;
+  const bool emit = A.incremental && A.st->iter == 0;
+  const T *Gsrc = inc ? A.Gd[prev] : Gp;
+  T *Gdn = A.incremental ? A.Gd[prev ^ 1] : nullptr;
   const T *chiP = A.chiP[gp.axis] + (long long)f * cells;
   const T *SP = A.SP[gp.axis] + (long long)f * cells;
   T *Jout = A.Jpart + ((long long)gi * A.d.nf + f) * cells;
@@ -212,7 +237,7 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
             const int rowA = (a * Rmax + lv) * Nu;
             IA = prv[RT_IDX(rowA + u, smem_n, 5)];
             IB = ua_in ? prv[RT_IDX(rowA + ua, smem_n, 5)]
-                       : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, v, wp);
+                       : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, v, wp);
             if (vb_in) {
               const T *src = prv;
               int lvb = vb - v0;
@@ -225,16 +250,16 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
               const int rowC = (a * Rmax + lvb) * Nu;
               IC = src[RT_IDX(rowC + u, smem_n, 6)];
               ID = ua_in ? src[RT_IDX(rowC + ua, smem_n, 6)]
-                         : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+                         : ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, vb, wp);
             } else {
-              IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, vb, wp);
-              ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+              IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, u, vb, wp);
+              ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, vb, wp);
             }
           } else {
-            IA = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, v, wp);
-            IB = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, v, wp);
-            IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, u, vb, wp);
-            ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, ua, vb, wp);
+            IA = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, u, v, wp);
+            IB = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, v, wp);
+            IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, u, vb, wp);
+            ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, vb, wp);
           }
           const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
           const T Sm = p.wa * sA + p.wb * sB + p.wc * sC + p.wd * sD;
@@ -260,11 +285,15 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
           if (A.write_ghosts) {
             const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
             const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
-            if (perW && w == wlast) Gn[RT_IDX(gb + (long long)v * Nu + u, gn, 8)] = I0;
-            if (perU && u == (p.su > 0 ? Nu - 1 : 0))
-              Gn[RT_IDX(gb + plane + (long long)w * Nv + v, gn, 9)] = I0;
-            if (perV && v == (p.sv > 0 ? Nv - 1 : 0))
-              Gn[RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u, gn, 10)] = I0;
+            long long off = -1;
+            if (perW && w == wlast) off = gb + (long long)v * Nu + u;
+            if (off >= 0) ghost_store<T>(Gp, Gn, Gdn, RT_IDX(off, gn, 8), I0, inc, emit);
+            off = -1;
+            if (perU && u == (p.su > 0 ? Nu - 1 : 0)) off = gb + plane + (long long)w * Nv + v;
+            if (off >= 0) ghost_store<T>(Gp, Gn, Gdn, RT_IDX(off, gn, 9), I0, inc, emit);
+            off = -1;
+            if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) off = gb + plane + (long long)Nw * Nv + (long long)w * Nu + u;
+            if (off >= 0) ghost_store<T>(Gp, Gn, Gdn, RT_IDX(off, gn, 10), I0, inc, emit);
           }
         }
       }
@@ -314,7 +343,7 @@ __device__ __forceinline__ long long perm_index(const Dims &d, int a, long long 
   return ((long long)x * d.n[2] + z) * d.n[1] + y;                 // [x][z][y]
 }
 
-// Jacobi ALI (Eq. 30): dS = [(1-eps) J + eps B - S] / [1 - (1-eps) Lambda*], with
+// Jacobi ALI (Eq. 24): dS = [(1-eps) J + eps B - S] / [1 - (1-eps) Lambda*], with
 // the denominator formed as eps + (1-eps)(1 - Lambda*) from the separately summed
 // 1 - Lambda* (no cancellation in thick cells).  All of it in FP64.
 template <typename T>
@@ -323,18 +352,23 @@ __global__ void __launch_bounds__(256) ali_update_kernel(const AliArgs<T> A) {
   const long long cells = A.d.cells;
   const long long N = cells * A.d.nf;
   const bool first = A.st->iter == 0;
+  const bool inc = A.incremental && !first;
   double rmax = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const long long f = i / cells, c = i - f * cells;
-    double J = 0.0;
-    for (int p = 0; p < A.ngroups_per_f; ++p) J += (double)A.Jpart[((long long)p * A.d.nf + f) * cells + c];
-    A.J64[i] = J;
+    double dJ = 0.0;
+    for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[((long long)p * A.d.nf + f) * cells + c];
+    // incremental solves accumulate J in FP64 from the swept increments
+    const double J = inc ? A.J64[i] + dJ : dJ;
     double r;
     if (A.lte) {
-      const double Jp = A.Jprev[i];
-      r = first ? INFINITY : rel_change(J - Jp, J);
+      const double Jp = A.incremental ? A.J64[i] : A.Jprev[i];
+      r = first ? INFINITY : rel_change(inc ? dJ : J - Jp, J);
       A.Jprev[i] = J;
+      if (A.incremental)
+        for (int a = 0; a < 3; ++a)
+          if (A.SP[a]) A.SP[a][f * cells + perm_index(A.d, a, c)] = T(0);
     } else {
       const double S = A.S64[i], e = A.eps[i];
       const double dS = ((1.0 - e) * J + e * A.B[i] - S) / (e + (1.0 - e) * A.oml[i]);
@@ -342,10 +376,11 @@ __global__ void __launch_bounds__(256) ali_update_kernel(const AliArgs<T> A) {
       A.S64[i] = Sn;
       A.Sfs[i] = S;
       r = rel_change(dS, Sn);
-      const T Snt = (T)Sn;
+      const T Snt = (T)(A.incremental ? dS : Sn);
       for (int a = 0; a < 3; ++a)
         if (A.SP[a]) A.SP[a][f * cells + perm_index(A.d, a, c)] = Snt;
     }
+    A.J64[i] = J;
     rmax = fmax(rmax, r);
   }
   block_max_to(rmax, &A.st->resid_bits);

@@ -14,6 +14,7 @@ struct SweepArgs {
   const T *chiP[3];          // sweep-precision opacity, permuted per sweep axis, [nf][cells]
   const T *SP[3];            // sweep-precision source function, same layouts
   T *G[2];                   // lagged periodic ghosts [nf][na][gsize], selected by parity
+  T *Gd[2];                  // their increments between formal solutions (incremental solves)
   const T *Ibc[6];           // inflow intensity of non-periodic faces [nf][na][face cells]
   const AngleParam<T> *ang;  // rays in group order
   const GroupParam *grp;
@@ -25,6 +26,7 @@ struct SweepArgs {
   int write_ghosts;
   int skip_if_done;
   int cluster;               // CTAs per cluster = strips per plane
+  int incremental;           // ALI solve sweeping increments after its first formal solution
 };
 
 template <typename T>
@@ -37,6 +39,7 @@ struct AliArgs {
   T *SP[3];                  // permuted sweep copies of S to refresh (NULL = axis unused)
   SolveState *st;
   int lte;
+  int incremental;           // partials are increments of J; SP receives dS
 };
 
 template <typename T>

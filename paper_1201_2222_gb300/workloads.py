@@ -12,14 +12,14 @@ Workloads (sizes are the defaults; every builder also takes a smaller ``n`` so t
 same structure can be run at sizes a slow CPU reference finishes quickly):
 
 * ``stratified_atmosphere``: the paper's uniform-temperature non-LTE atmosphere
-  (Sec. 5.1, Eq. 43 and the 3D variant with periodic horizontal boundaries):
+  (Sec. 5.1, Eq. 30 and the 3D variant with periodic horizontal boundaries):
   plane-parallel exponential atmosphere whose vertical optical depth runs
   log-spaced from 1e-4 at the top to 1e3 at the bottom, constant epsilon, B = 1,
   vacuum at the top and I = B at the bottom.
 * ``turbulent_box``: a fully periodic box with a log-normal density drawn from a
   Gaussian random field with a k^(-11/3) spectrum, a log-normal temperature,
   absorption proportional to rho^2 T^-3.5 plus scattering proportional to rho,
-  B = T^4 (the kind of structure of the paper's shearing-box snapshot, Sec. 5.4).
+  B = T^4 (the kind of structure of the paper's shearing-box snapshot, Sec. 5.3).
 * ``multifrequency_atmosphere``: the stratified atmosphere with a horizontal
   temperature perturbation and free-free-like absorption over log-spaced
   frequency bins plus grey scattering (the multi-frequency spectra test, Sec. 5.1).

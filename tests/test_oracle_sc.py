@@ -279,7 +279,7 @@ def _eddington_error(nz, eps):
 
 def test_scattering_atmosphere_matches_eddington_solution():
     """Uniform-temperature non-LTE atmosphere (Sec. 5.1): with the two-stream set the
-    exact continuum answer is J = B (1 - exp(-sqrt(3 eps) tau)/(1 + sqrt(eps))) (Eq. 43),
+    exact continuum answer is J = B (1 - exp(-sqrt(3 eps) tau)/(1 + sqrt(eps))) (Eq. 30),
     so S = eps B + (1 - eps) J, S(0) = sqrt(eps) B and J -> B deep inside.  The
     discrete S must converge to it (better than first order in the zone size;
     the paper notes the largest errors sit at small optical depth)."""
@@ -309,9 +309,9 @@ def test_iterations_grow_as_eps_decreases():
 
 @pytest.mark.parametrize("N", [16, 32, 64])
 def test_linear_response_of_periodic_medium(N):
-    """Eq. 56: in a uniform medium, J responds to a sinusoidal B with
+    """Eq. 37: in a uniform medium, J responds to a sinusoidal B with
     J1/B1 = sum_k w_k chi^2/(chi^2 + k^2 mu_kx^2) for a discrete angle set (the
-    angle integral of Eq. 56 done with the quadrature).  SC on a periodic grid
+    angle integral of Eq. 37 done with the quadrature).  SC on a periodic grid
     must approach it as the grid is refined."""
     chi0, kw = 1.0, 1.0
     L = 2 * math.pi / kw
