@@ -307,7 +307,9 @@ def run_gpu(args):
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
         "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
         "fp64_path": fp64,
-        "roofline": {"bound": "alu", "kernel": "sc_sweep_kernel<float>", "achieved": achieved,
+        "sweep_plan": g.sweep_plan(),
+        "roofline": {"bound": "alu", "kernel": "sc_sweep_tiled_kernel<float>" if g.sweep_plan()["variant"] == 2 else "sc_sweep_kernel<float>",
+                     "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
                      "flops_per_update": FLOPS_PER_UPDATE, "avg_launch_ms": avg_launch_s * 1e3,

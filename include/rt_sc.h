@@ -167,9 +167,21 @@ typedef struct {
 rt_status rt_enable_timing(rt_grid g, int enable);
 rt_status rt_get_stats(rt_grid g, rt_stats *out);
 
-/* Tuning of the sweep launch (0 = automatic): angles per sweep group and CTAs per
- * thread-block cluster along the plane. */
-rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads);
+/* Tuning of the formal-solution launch (0 = automatic for each): rays per sweep
+ * group (1..8), CTAs per thread-block cluster = strips per plane (1..16),
+ * threads per CTA (multiple of 32, <= 512) and the kernel variant (1 = one cell
+ * per thread with direct loads, 2 = shared-memory staged planes with four cells
+ * per thread).  Automatic choice: variant 2 for RT_PREC_MIXED, 1 for FP64; rays
+ * per group and strips from the runtime's count of co-resident clusters.
+ * Results do not depend on the configuration beyond rounding order.
+ * Errors: RT_ERR_ARG for out-of-range values or no feasible configuration. */
+rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads,
+                              int variant);
+
+/* The sweep plan in use: plan[0] variant, [1] groups per frequency, [2] rays per
+ * group (max), [3] strips per plane (cluster size), [4] threads per CTA,
+ * [5] dynamic shared memory bytes per CTA. */
+rt_status rt_get_sweep_plan(rt_grid g, int *plan);
 
 /* Message describing the last error on this thread (never NULL). */
 const char *rt_last_error(void);

@@ -250,9 +250,9 @@ struct rt_grid_s {
   size_t tsize = 8;
 
   // sweep plan
-  int apg = 0, amax = 1, cluster = 1, threads = 256;
+  int apg = 0, amax = 1, cluster = 1, threads = 256, slots = 1, variant = 1;
   size_t smem = 0;
-  int req_apg = 0, req_cluster = 0, req_threads = 0;
+  int req_apg = 0, req_cluster = 0, req_threads = 0, req_variant = 0;
   std::vector<GroupParam> groups;
   std::vector<int> group_angles;   // angle index per AngleParam slot
 
@@ -336,46 +336,43 @@ void build_rays(rt_grid g) {
 
 // Largest dynamic shared memory a sweep CTA may use.
 constexpr size_t kSweepSmemBudget = 200 * 1024;
+constexpr int kSMs = 152;
 
-size_t sweep_smem(rt_grid g, int amax, int C) {
-  size_t s = 0;
+int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)); }
+
+// Shared memory and threads of one sweep CTA for `slots` rays and C strips.
+void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *threads) {
+  size_t sm = 0;
+  int th = 0;
   for (int a = 0; a < 3; ++a) {
     if (!g->used_axis[a]) continue;
     int cax[3];
     rtk::plane_axes(a, cax);
+    const int Nu = g->d.n[cax[0]];
     const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
-    s = std::max(s, (size_t)2 * amax * Rmax * g->d.n[cax[0]] * g->tsize);
+    if (variant == 2) {
+      const size_t W = (size_t)Nu + 2 + rtk::kSweepSeg;
+      sm = std::max(sm, (size_t)(2 * slots + 4) * (Rmax + 2) * W * g->tsize);
+      th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
+    } else {
+      sm = std::max(sm, (size_t)2 * slots * Rmax * Nu * g->tsize);
+      th = std::max(th, Rmax * Nu);
+    }
   }
-  return s;
+  *smem = sm;
+  *threads = std::max(32, std::min(512, ((th + 31) / 32) * 32));
 }
 
-int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)); }
-
-void plan_groups(rt_grid g) {
+// Split each (crossed axis, direction) class of rays into chunks of <= apg.
+void make_groups(rt_grid g, int apg, std::vector<GroupParam> &groups, std::vector<int> &gang, int *namax) {
   std::vector<int> per_key[6];
   for (int k = 0; k < g->na; ++k) {
     const RayGeom &r = g->rays[k];
     per_key[2 * r.axis + (r.sgn[r.axis] > 0 ? 0 : 1)].push_back(k);
   }
-  int nmax = 1;
-  for (auto &v : per_key) nmax = std::max(nmax, (int)v.size());
-  int minNv = 1 << 30;
-  for (int a = 0; a < 3; ++a) {
-    if (!g->used_axis[a]) continue;
-    int cax[3];
-    rtk::plane_axes(a, cax);
-    minNv = std::min(minNv, g->d.n[cax[1]]);
-  }
-  const int Cmax = std::min(16, minNv);
-  int apg = g->req_apg > 0 ? g->req_apg : 4;
-  apg = std::min(std::max(apg, 1), 8);
-  apg = std::min(apg, nmax);
-  // fewer rays per group when even the largest cluster cannot hold the planes
-  while (apg > 1 && sweep_smem(g, amax_for(apg), Cmax) > kSweepSmemBudget) apg = (apg + 1) / 2;
-  g->apg = apg;
-  g->amax = amax_for(apg);
-  g->groups.clear();
-  g->group_angles.clear();
+  groups.clear();
+  gang.clear();
+  *namax = 0;
   for (int key = 0; key < 6; ++key) {
     const auto &v = per_key[key];
     if (v.empty()) continue;
@@ -386,31 +383,92 @@ void plan_groups(rt_grid g) {
       GroupParam gp{};
       gp.axis = key / 2;
       gp.sa = (key % 2) ? -1 : 1;
-      gp.a0 = (int)g->group_angles.size();
+      gp.a0 = (int)gang.size();
       gp.na = sz;
-      for (int q = 0; q < sz; ++q) g->group_angles.push_back(v[pos + q]);
+      for (int q = 0; q < sz; ++q) gang.push_back(v[pos + q]);
       pos += sz;
-      g->groups.push_back(gp);
+      groups.push_back(gp);
+      *namax = std::max(*namax, sz);
     }
   }
-  // strips per plane: enough CTAs to cover the GPU twice, within the shared-memory budget
-  const long long inst = (long long)g->groups.size() * g->d.nf;
-  int C = g->req_cluster > 0 ? g->req_cluster : (int)std::max(1LL, (2 * 152 + inst - 1) / inst);
-  if (g->req_cluster <= 0) C = std::min(C, 8);
-  C = std::max(1, std::min(C, Cmax));
-  while (sweep_smem(g, g->amax, C) > kSweepSmemBudget && C < Cmax) ++C;
-  g->cluster = C;
-  g->smem = sweep_smem(g, g->amax, C);
-  size_t cells_strip = 0;
+}
+
+int resident_clusters(rt_grid g, int variant, int amax, int C, int threads, size_t smem) {
+  if (g->desc.prec == RT_PREC_FP64) return rtk::sweep_max_active_clusters<double>(variant == 2, amax, C, threads, smem);
+  return rtk::sweep_max_active_clusters<float>(variant == 2, amax, C, threads, smem);
+}
+
+// Choose rays per group and strips per plane: the estimated sweep time is
+// (waves of resident clusters) x (rays per group) x (cells per strip) x
+// (CTAs sharing an SM), from the runtime's count of co-resident clusters
+// (clusters cannot straddle a GPC, so this is not simply SMs / C).
+void plan_groups(rt_grid g) {
+  int minNv = 1 << 30;
   for (int a = 0; a < 3; ++a) {
     if (!g->used_axis[a]) continue;
     int cax[3];
     rtk::plane_axes(a, cax);
-    const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
-    cells_strip = std::max(cells_strip, (size_t)Rmax * g->d.n[cax[0]]);
+    minNv = std::min(minNv, g->d.n[cax[1]]);
   }
-  int th = g->req_threads > 0 ? g->req_threads : (int)std::min<size_t>(512, ((cells_strip + 31) / 32) * 32);
-  g->threads = std::max(32, std::min(512, th));
+  int variant = g->req_variant;
+  if (variant == 0) variant = g->desc.prec == RT_PREC_FP64 ? 1 : 2;
+  const int Cmax = std::min(16, minNv);
+  double best = 1e300;
+  int bapg = 1, bC = 1;
+  for (int apg = 1; apg <= 8; ++apg) {
+    if (g->req_apg > 0 && apg != g->req_apg) continue;
+    std::vector<GroupParam> gr;
+    std::vector<int> ga;
+    int namax = 0;
+    make_groups(g, apg, gr, ga, &namax);
+    const long long clusters = (long long)gr.size() * g->d.nf;
+    for (int C = 1; C <= Cmax; ++C) {
+      if (g->req_cluster > 0 && C != g->req_cluster) continue;
+      size_t smem;
+      int threads;
+      sweep_shape(g, variant, namax, C, &smem, &threads);
+      if (g->req_threads > 0) threads = g->req_threads;
+      if (smem > kSweepSmemBudget) continue;
+      int raw_threads = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (!g->used_axis[a]) continue;
+        int cax[3];
+        rtk::plane_axes(a, cax);
+        const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
+        const int Nu = g->d.n[cax[0]];
+        raw_threads = std::max(raw_threads, variant == 2 ? Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg) : Rmax * Nu);
+      }
+      int nres = resident_clusters(g, variant, amax_for(namax), C, threads, smem);
+      if (nres <= 0) nres = 1;   // unknown occupancy: assume one resident cluster
+      const double waves = std::ceil((double)clusters / nres);
+      const double share = std::max(1.0, (double)std::min<long long>(clusters, nres) * C / kSMs);
+      const double passes = std::ceil((double)raw_threads / threads);   // cells per thread per plane
+      double work = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        if (!g->used_axis[a]) continue;
+        int cax[3];
+        rtk::plane_axes(a, cax);
+        const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
+        work = std::max(work, (double)Rmax * g->d.n[cax[0]]);
+      }
+      // per-step cost: cells per strip, plus a fixed barrier/latency floor per step
+      const double est = waves * share * namax * (std::max(work, 64.0 * passes) + 2048.0);
+      if (est < best * 0.999) {
+        best = est;
+        bapg = apg;
+        bC = C;
+      }
+    }
+  }
+  int namax = 0;
+  make_groups(g, bapg, g->groups, g->group_angles, &namax);
+  g->variant = variant;
+  g->apg = bapg;
+  g->slots = namax;
+  g->amax = amax_for(namax);
+  g->cluster = bC;
+  sweep_shape(g, variant, namax, bC, &g->smem, &g->threads);
+  if (g->req_threads > 0) g->threads = g->req_threads;
 }
 
 template <typename T>
@@ -566,7 +624,11 @@ rt_status enqueue_sweep(rt_grid g, rtk::SweepArgs<T> &A, bool moments, cudaStrea
     CU(cudaEventCreate(&p.b));
     CU(cudaEventRecord(p.a, s));
   }
-  CU(rtk::launch_sweep<T>(A, g->amax, moments, g->threads, g->smem, s));
+  if (g->variant == 2) {
+    CU(rtk::launch_sweep_tiled<T>(A, g->amax, moments, g->threads, g->smem, s));
+  } else {
+    CU(rtk::launch_sweep<T>(A, g->amax, moments, g->threads, g->smem, s));
+  }
   g->launches++;
   if (ev) {
     CU(cudaEventRecord(p.b, s));
@@ -859,16 +921,18 @@ rt_status rt_get_angles(rt_grid g, double *mu, double *w) {
   return RT_OK;
 }
 
-rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads) {
+rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads, int variant) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   if (angles_per_group < 0 || angles_per_group > 8 || cluster_ctas < 0 || cluster_ctas > 16 ||
-      threads < 0 || threads > 512 || (threads % 32))
+      threads < 0 || threads > 512 || (threads % 32) || variant < 0 || variant > 2)
     return fail(RT_ERR_ARG, "bad sweep configuration");
   cudaStreamSynchronize(g->own);
   g->req_apg = angles_per_group;
   g->req_cluster = cluster_ctas;
   g->req_threads = threads;
+  g->req_variant = variant;
   plan_groups(g);
+  if (g->groups.empty()) return fail(RT_ERR_ARG, "no feasible sweep configuration");
   if (g->smem > 227 * 1024) return fail(RT_ERR_ARG, "sweep configuration needs %zu bytes of shared memory", g->smem);
   return upload_plan_any(g);
 }
@@ -1046,6 +1110,17 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
 rt_status rt_enable_timing(rt_grid g, int enable) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   g->timing = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_get_sweep_plan(rt_grid g, int *plan) {
+  if (!g || !plan) return fail(RT_ERR_ARG, "NULL argument");
+  plan[0] = g->variant;
+  plan[1] = (int)g->groups.size();
+  plan[2] = g->slots;
+  plan[3] = g->cluster;
+  plan[4] = g->threads;
+  plan[5] = (int)g->smem;
   return RT_OK;
 }
 

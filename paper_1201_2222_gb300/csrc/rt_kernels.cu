@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   const long long cells = A.d.cells;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Ibuf = reinterpret_cast<T *>(smem_raw);
-  const int bufstride = AMAX * Rmax * Nu;
+  const int bufstride = A.ray_slots * Rmax * Nu;   // one plane of every ray slot
 #ifdef RT_DEBUG_BOUNDS
   const long long smem_n = 2LL * bufstride;
 #endif
@@ -306,6 +306,263 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
         for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[q];
 #pragma unroll
         for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[q];
+      }
+    }
+    if (C > 1) cluster.sync();
+    else __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- tiled sweep
+// Same formal solution as sc_sweep_kernel, organised for throughput:
+//  * the upwind plane's intensities, opacity and source function are staged in
+//    shared memory with a one-cell halo (filled once per step from the
+//    neighbouring strips over DSMEM, or from the ghost rules), so the per-ray
+//    update reads shared memory only, without boundary tests;
+//  * chi and S of the current plane are staged too (they are the next step's
+//    upwind plane);
+//  * a thread computes SEG consecutive cells of one row, reusing the staged
+//    row values in registers, and each ray's signs (su, sv) are template
+//    parameters of the update so all register indexing is static.
+
+template <typename T, int SEG, bool MOM, int SU, int SV>
+__device__ __forceinline__ void seg_update(const AngleParam<T> &p, const T *__restrict__ Ip,
+                                           T *__restrict__ Ic, int row, int u0, int ncell, int W,
+                                           const T (&cm)[SEG + 2], const T (&c0)[SEG + 2],
+                                           const T (&cp)[SEG + 2], const T (&sm)[SEG + 2],
+                                           const T (&s0)[SEG + 2], const T (&sp)[SEG + 2],
+                                           const T (&chi0)[SEG], const T (&S0)[SEG], T (&out)[SEG]) {
+  // intensities of the upwind plane on rows v and v - SV, columns covering the segment
+  const int cb = u0 + (SU > 0 ? 0 : 1);
+  T Ia[SEG + 1], Iv[SEG + 1];
+#pragma unroll
+  for (int k = 0; k < SEG + 1; ++k) {
+    Ia[k] = Ip[row * W + cb + k];
+    Iv[k] = Ip[(row - SV) * W + cb + k];
+  }
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int kA = j + (SU > 0 ? 1 : 0), kB = j + (SU > 0 ? 0 : 1);
+    const int jA = j + 1, jB = j + 1 - SU;
+    const T chiC = SV > 0 ? cm[jA] : cp[jA], chiD = SV > 0 ? cm[jB] : cp[jB];
+    const T sC = SV > 0 ? sm[jA] : sp[jA], sD = SV > 0 ? sm[jB] : sp[jB];
+    const T chim = p.wa * c0[jA] + p.wb * c0[jB] + p.wc * chiC + p.wd * chiD;
+    const T Sm = p.wa * s0[jA] + p.wb * s0[jB] + p.wc * sC + p.wd * sD;
+    const T Im = p.wa * Ia[kA] + p.wb * Ia[kB] + p.wc * Iv[kA] + p.wd * Iv[kB];
+    const T dtau = (chim + chi0[j]) * p.hs;
+    T E, psi0, om;
+    seg_weights(dtau, E, psi0, om);
+    const T I0 = Sm + E * (Im - Sm) + psi0 * (S0[j] - Sm);
+    out[j] = I0;
+    if (j < ncell) Ic[row * W + u0 + j + 1] = I0;
+  }
+}
+
+template <typename T, int AMAX, bool MOM, int SEG>
+__global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> A) {
+  if (A.skip_if_done && A.st->done) return;
+  const int C = A.cluster;
+  const int rank = blockIdx.x % C;
+  const int inst = blockIdx.x / C;
+  const int gi = inst % A.ngroups;
+  const int f = inst / A.ngroups;
+  const GroupParam gp = A.grp[gi];
+  int cax[3];
+  plane_axes(gp.axis, cax);
+  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
+  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int v0 = (int)(((long long)rank * Nv) / C);
+  const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
+  const int R = v1 - v0;
+  const int Rmax = (Nv + C - 1) / C;
+  const int W = Nu + 2 + SEG;          // staged row: halo, Nu cells, halo, padding
+  const int RX = Rmax + 2;
+  const int pb = RX * W;               // one staged plane
+  const int ib = A.ray_slots * pb;     // one plane of every ray of the group
+  const long long plane = (long long)Nu * Nv;
+  const long long cells = A.d.cells;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ib = reinterpret_cast<T *>(smem_raw);   // [2][AMAX][RX][W]
+  T *Cb = Ib + 2 * ib;                       // [2][RX][W]
+  T *Sb = Cb + 2 * pb;                       // [2][RX][W]
+#ifdef RT_DEBUG_BOUNDS
+  const long long smem_n = 2LL * ib + 4LL * pb;
+#endif
+  __shared__ AngleParam<T> P[AMAX];
+  if (threadIdx.x < gp.na) P[threadIdx.x] = A.ang[gp.a0 + threadIdx.x];
+  __syncthreads();
+
+  const int fs = A.st->fs_count + A.parity_offset;
+  const int prev = fs & 1;
+  const T *Gp = A.G[prev];
+  T *Gn = A.G[prev ^ 1];
+  const bool inc = A.incremental && A.st->iter > 0;
+  const bool emit = A.incremental && A.st->iter == 0;
+  const T *Gsrc = inc ? A.Gd[prev] : Gp;
+  T *Gdn = A.incremental ? A.Gd[prev ^ 1] : nullptr;
+  const T *chiP = A.chiP[gp.axis] + (long long)f * cells;
+  const T *SP = A.SP[gp.axis] + (long long)f * cells;
+  T *Jout = A.Jpart + ((long long)gi * A.d.nf + f) * cells;
+  const int sa = gp.sa;
+  const int wlast = sa > 0 ? Nw - 1 : 0;
+  const int na = gp.na;
+  const int nseg = (Nu + SEG - 1) / SEG;
+  const int ext = (R + 2) * (Nu + 2);
+  cg::cluster_group cluster = cg::this_cluster();
+
+  auto stage_fields = [&](int wsrc, T *Cd, T *Sd) {
+    for (int idx = threadIdx.x; idx < ext; idx += blockDim.x) {
+      const int row = idx / (Nu + 2), col = idx - row * (Nu + 2);
+      int uu = col - 1, vv = v0 - 1 + row;
+      uu = uu < 0 ? (perU ? uu + Nu : 0) : (uu >= Nu ? (perU ? uu - Nu : Nu - 1) : uu);
+      vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
+      const long long o = (long long)wsrc * plane + (long long)vv * Nu + uu;
+      Cd[RT_IDX(row * W + col, pb, 20)] = chiP[RT_IDX(o, cells, 21)];
+      Sd[RT_IDX(row * W + col, pb, 20)] = SP[RT_IDX(o, cells, 21)];
+    }
+  };
+
+  for (int t = 0; t < Nw; ++t) {
+    const int w = sa > 0 ? t : Nw - 1 - t;
+    const int wp = w - sa;
+    const bool wp_in = t > 0;
+    T *Icur = Ib + (t & 1) * ib;
+    T *Iprv = Ib + ((t + 1) & 1) * ib;
+    T *Ccur = Cb + (t & 1) * pb, *Cprv = Cb + ((t + 1) & 1) * pb;
+    T *Scur = Sb + (t & 1) * pb, *Sprv = Sb + ((t + 1) & 1) * pb;
+
+    // 1. chi, S of this plane (and of the upwind ghost plane on the first step)
+    stage_fields(w, Ccur, Scur);
+    if (!wp_in) stage_fields(perW ? (wp < 0 ? wp + Nw : wp - Nw) : w, Cprv, Sprv);
+    // 2. intensities of the upwind plane outside this strip
+    if (!wp_in) {
+      for (int idx = threadIdx.x; idx < na * ext; idx += blockDim.x) {
+        const int a = idx / ext, r2 = idx - a * ext;
+        const int row = r2 / (Nu + 2), col = r2 - row * (Nu + 2);
+        Iprv[RT_IDX(a * pb + row * W + col, 2LL * ib, 22)] =
+            ghost_I<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, col - 1, v0 - 1 + row, wp);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < na * 2 * Nu; idx += blockDim.x) {
+        const int a = idx / (2 * Nu), r2 = idx - a * 2 * Nu;
+        const int side = r2 / Nu, u = r2 - side * Nu;
+        const int vv = side ? v1 : v0 - 1;
+        const int row = side ? R + 1 : 0;
+        T val;
+        if (vv >= 0 && vv < Nv) {
+          const int rr = side ? rank + 1 : rank - 1;
+          const int rv0 = (int)(((long long)rr * Nv) / C);
+          const T *src = cluster.map_shared_rank(Iprv, rr);
+          val = src[RT_IDX(a * pb + (vv - rv0 + 1) * W + u + 1, 2LL * ib, 23)];
+        } else {
+          val = ghost_I<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, u, vv, wp);
+        }
+        Iprv[RT_IDX(a * pb + row * W + u + 1, 2LL * ib, 24)] = val;
+      }
+      for (int idx = threadIdx.x; idx < na * 2 * (R + 2); idx += blockDim.x) {
+        const int a = idx / (2 * (R + 2)), r2 = idx - a * 2 * (R + 2);
+        const int side = r2 / (R + 2), row = r2 - side * (R + 2);
+        Iprv[RT_IDX(a * pb + row * W + (side ? Nu + 1 : 0), 2LL * ib, 25)] =
+            ghost_I<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, side ? Nu : -1, v0 - 1 + row, wp);
+      }
+    }
+    __syncthreads();
+
+    // 3. the strip's cells, SEG per thread
+    for (int sidx = threadIdx.x; sidx < R * nseg; sidx += blockDim.x) {
+      const int lv = sidx / nseg, seg = sidx - lv * nseg;
+      const int u0 = seg * SEG, v = v0 + lv, row = lv + 1;
+      const int ncell = min(SEG, Nu - u0);
+      T cm[SEG + 2], c0[SEG + 2], cp[SEG + 2], sm[SEG + 2], s0[SEG + 2], sp[SEG + 2];
+#pragma unroll
+      for (int j = 0; j < SEG + 2; ++j) {
+        cm[j] = Cprv[(row - 1) * W + u0 + j];
+        c0[j] = Cprv[row * W + u0 + j];
+        cp[j] = Cprv[(row + 1) * W + u0 + j];
+        sm[j] = Sprv[(row - 1) * W + u0 + j];
+        s0[j] = Sprv[row * W + u0 + j];
+        sp[j] = Sprv[(row + 1) * W + u0 + j];
+      }
+      T chi0[SEG], S0[SEG], Jacc[SEG];
+      T Hm[MOM ? SEG : 1][3], Km[MOM ? SEG : 1][6];
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        chi0[j] = Ccur[row * W + u0 + j + 1];
+        S0[j] = Scur[row * W + u0 + j + 1];
+        Jacc[j] = T(0);
+        if (MOM) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) Hm[MOM ? j : 0][q] = T(0);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Km[MOM ? j : 0][q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a) {
+        if (a < na) {
+          const AngleParam<T> &p = P[a];
+          const T *Ip = Iprv + a * pb;
+          T *Ic = Icur + a * pb;
+          T I0[SEG];
+          const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
+          if (key == 3) seg_update<T, SEG, MOM, 1, 1>(p, Ip, Ic, row, u0, ncell, W, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else if (key == 2) seg_update<T, SEG, MOM, -1, 1>(p, Ip, Ic, row, u0, ncell, W, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else if (key == 1) seg_update<T, SEG, MOM, 1, -1>(p, Ip, Ic, row, u0, ncell, W, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else seg_update<T, SEG, MOM, -1, -1>(p, Ip, Ic, row, u0, ncell, W, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+#pragma unroll
+          for (int j = 0; j < SEG; ++j) {
+            const T wI = p.wq * I0[j];
+            Jacc[j] += wI;
+            if (MOM) {
+              Hm[MOM ? j : 0][0] += wI * p.mu[0];
+              Hm[MOM ? j : 0][1] += wI * p.mu[1];
+              Hm[MOM ? j : 0][2] += wI * p.mu[2];
+              Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+              Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+              Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+              Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+              Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+              Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
+            }
+          }
+          if (A.write_ghosts) {
+            const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+            const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+#pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+              if (j < ncell) {
+                const int u = u0 + j;
+                if (perW && w == wlast)
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u, gn, 26), I0[j], inc, emit);
+                if (perU && u == (p.su > 0 ? Nu - 1 : 0))
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 27), I0[j], inc, emit);
+                if (perV && v == (p.sv > 0 ? Nv - 1 : 0))
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u, gn, 28),
+                                 I0[j], inc, emit);
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        if (j < ncell) {
+          int crd[3];
+          crd[cax[0]] = u0 + j;
+          crd[cax[1]] = v;
+          crd[cax[2]] = w;
+          const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+          Jout[RT_IDX(canon, cells, 29)] = Jacc[j];
+          if (MOM) {
+            T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
+            const long long qs = (long long)A.d.nf * cells;
+            const long long o = (long long)f * cells + canon;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[MOM ? j : 0][q];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[MOM ? j : 0][q];
+          }
+        }
       }
     }
     if (C > 1) cluster.sync();
@@ -644,6 +901,48 @@ static cudaError_t launch_sweep_t(const SweepArgs<T> &A, int threads, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
+template <typename T, int AMAX, bool MOM>
+static cudaError_t launch_tiled_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
+  auto kern = sc_sweep_tiled_kernel<T, AMAX, MOM, kSweepSeg>;
+  static size_t set_smem = 0;
+  static bool nonportable = false;
+  if (smem > set_smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_smem = smem;
+  }
+  if (A.cluster > 8 && !nonportable) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    nonportable = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)A.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = A.cluster > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, A);
+}
+
+template <typename T>
+cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                               cudaStream_t s) {
+  switch (amax) {
+    case 1: return moments ? launch_tiled_t<T, 1, true>(A, threads, smem, s) : launch_tiled_t<T, 1, false>(A, threads, smem, s);
+    case 2: return moments ? launch_tiled_t<T, 2, true>(A, threads, smem, s) : launch_tiled_t<T, 2, false>(A, threads, smem, s);
+    case 4: return moments ? launch_tiled_t<T, 4, true>(A, threads, smem, s) : launch_tiled_t<T, 4, false>(A, threads, smem, s);
+    case 8: return moments ? launch_tiled_t<T, 8, true>(A, threads, smem, s) : launch_tiled_t<T, 8, false>(A, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                          cudaStream_t s) {
@@ -653,6 +952,43 @@ cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int thre
     case 4: return moments ? launch_sweep_t<T, 4, true>(A, threads, smem, s) : launch_sweep_t<T, 4, false>(A, threads, smem, s);
     case 8: return moments ? launch_sweep_t<T, 8, true>(A, threads, smem, s) : launch_sweep_t<T, 8, false>(A, threads, smem, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int AMAX>
+static int max_active_t(int tiled, int cluster, int threads, size_t smem) {
+  const void *kern = tiled ? (const void *)sc_sweep_tiled_kernel<T, AMAX, false, kSweepSeg>
+                           : (const void *)sc_sweep_kernel<T, AMAX, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  if (cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cluster, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return n;
+}
+
+template <typename T>
+int sweep_max_active_clusters(int tiled, int amax, int cluster, int threads, size_t smem) {
+  switch (amax) {
+    case 1: return max_active_t<T, 1>(tiled, cluster, threads, smem);
+    case 2: return max_active_t<T, 2>(tiled, cluster, threads, smem);
+    case 4: return max_active_t<T, 4>(tiled, cluster, threads, smem);
+    case 8: return max_active_t<T, 8>(tiled, cluster, threads, smem);
+    default: return -1;
   }
 }
 
@@ -729,6 +1065,8 @@ cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, c
 
 #define RT_INSTANTIATE(T)                                                                          \
   template cudaError_t launch_sweep<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template cudaError_t launch_sweep_tiled<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template int sweep_max_active_clusters<T>(int, int, int, int, size_t);                          \
   template cudaError_t launch_ali<T>(const AliArgs<T> &, cudaStream_t);                             \
   template cudaError_t launch_lstar<T>(const Dims &, const double *, const RayGeom *, int, double *, \
                                        double *, cudaStream_t);                                     \

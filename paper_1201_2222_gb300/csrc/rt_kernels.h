@@ -27,6 +27,7 @@ struct SweepArgs {
   int skip_if_done;
   int cluster;               // CTAs per cluster = strips per plane
   int incremental;           // ALI solve sweeping increments after its first formal solution
+  int ray_slots;             // shared-memory planes per ray slot (>= rays of any group)
 };
 
 template <typename T>
@@ -45,6 +46,14 @@ struct AliArgs {
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                          cudaStream_t s);
+// cells per thread of the tiled sweep
+constexpr int kSweepSeg = 4;
+// clusters of one sweep configuration that can be resident at once (-1 on error)
+template <typename T>
+int sweep_max_active_clusters(int tiled, int amax, int cluster, int threads, size_t smem);
+template <typename T>
+cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s);
 cudaError_t launch_finish(SolveState *st, cudaStream_t s);

@@ -68,7 +68,8 @@ _SIGS = {
     "rt_get_S": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts)]),
     "rt_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(rt_stats)]),
-    "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "rt_get_sweep_plan": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "rt_angle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rt_last_error": (ctypes.c_char_p, []),
 }
@@ -204,8 +205,13 @@ class Grid:
         _check(load().rt_get_angles(self._h, mu.ctypes.data, w.ctypes.data))
         return mu, w
 
-    def set_sweep_config(self, angles_per_group=0, cluster_ctas=0, threads=0):
-        _check(load().rt_set_sweep_config(self._h, angles_per_group, cluster_ctas, threads))
+    def set_sweep_config(self, angles_per_group=0, cluster_ctas=0, threads=0, variant=0):
+        _check(load().rt_set_sweep_config(self._h, angles_per_group, cluster_ctas, threads, variant))
+
+    def sweep_plan(self):
+        v = (ctypes.c_int * 6)()
+        _check(load().rt_get_sweep_plan(self._h, v))
+        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem"), list(v)))
 
     def set_opacity_source(self, chi, eps, B, freq_w=None):
         pc, dc, kc = self._in(chi)

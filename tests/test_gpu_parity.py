@@ -1,10 +1,14 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
 
 Tolerances: the FP64 path must match the oracle to 1e-5 relative (it agrees to
-round-off in practice, so the tests use 1e-10); the mixed path (float32 sweeps,
-FP64 ALI) to 1e-3 relative in J, S and the heating rate, with the heating rate
-gated as |dQ| <= 1e-3 |Q| + 1e-6 4 pi chi_abs B where J ~ B makes Q cancel; the
-ALI iteration count must agree within one iteration.
+round-off in practice, so the tests use 1e-8..1e-10).  The mixed path (float32
+sweeps, FP64 ALI) must match to 1e-3 relative in J and S, with a floor of 1e-5
+of the frequency bin's largest value (float32 rounding in a sweep is relative to
+the largest intensity in the stencil, so cells 1e6 dimmer than their neighbours
+carry absolute, not relative, float32 errors), and in the heating rate to
+|dQ| <= 1e-3 |Q| + 1e-4 * 4 pi chi_abs B (Q = 4 pi chi_abs (J - B) cancels where
+J ~ B; a fixed float32 error in J is amplified by about 1/eps in the diffusion
+regime).  The ALI iteration count must agree within one iteration.
 """
 import math
 
@@ -44,6 +48,14 @@ def rel(a, b):
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
 
 
+def mixed_ok(x, ref, rtol=1e-3, floor=1e-5):
+    """|x - ref| <= rtol |ref| + floor * (largest |ref| of the frequency bin)."""
+    x = np.asarray(x)
+    ref = np.asarray(ref)
+    binmax = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1).reshape((-1,) + (1,) * (ref.ndim - 1))
+    return bool(np.all(np.abs(x - ref) <= rtol * np.abs(ref) + floor * binmax))
+
+
 # ------------------------------------------------------------- formal solution
 
 FS_CASES = [
@@ -57,19 +69,20 @@ FS_CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", range(len(FS_CASES)))
-def test_formal_solution_and_lambda_star(rt, prec, case):
+def test_formal_solution_and_lambda_star(rt, prec, case, variant):
     nx, ny, nz, n_mu, lo, hi, cfg = FS_CASES[case]
     p = W.random_box(nx, ny, nz, seed=100 + case, n_mu=n_mu, bc_lo=lo, bc_hi=hi)
-    g = make(rt, p, prec, **cfg)
+    g = make(rt, p, prec, variant=variant, **cfg)
     og = O.Grid.from_problem(p)
     rng = np.random.default_rng(case)
     S = rng.uniform(0.3, 2.0, p.chi.shape)
     J, L = g.formal_solve(S, want_lstar=True)
     G = O.init_ghosts(og, S[0])
     ref = O.formal_solution(og, p.chi[0], S[0], p.B[0], G_prev=G)
-    assert rel(J[0], ref["J"]) < TOL[prec]
+    assert rel(J[0], ref["J"]) < (TOL[prec] if prec == "fp64" else 1e-5)
     assert rel(L[0], ref["lstar"]) < (1e-10 if prec == "fp64" else 1e-5)
     # lagged periodic ghosts: further formal solutions from the previous ones
     G = ref["G_next"]
@@ -77,7 +90,7 @@ def test_formal_solution_and_lambda_star(rt, prec, case):
         J = g.formal_solve(None)
         ref = O.formal_solution(og, p.chi[0], S[0], p.B[0], G_prev=G)
         G = ref["G_next"]
-        assert rel(J[0], ref["J"]) < TOL[prec]
+        assert rel(J[0], ref["J"]) < (TOL[prec] if prec == "fp64" else 1e-5)
 
 
 def test_fixed_boundary_searchlight(rt):
@@ -92,8 +105,8 @@ def test_fixed_boundary_searchlight(rt):
     faces = [np.zeros(og.na * og.face[f // 2]) for f in range(6)]
     faces[4] = I.reshape(-1)
     Ifix = np.concatenate(faces)
-    for prec in ("fp64", "mixed"):
-        g = make(rt, p, prec)
+    for prec, variant in (("fp64", 1), ("fp64", 2), ("mixed", 1), ("mixed", 2)):
+        g = make(rt, p, prec, variant=variant)
         g.set_boundary_intensity(4, I)
         G = O.init_ghosts(og, p.B[0])
         for it in range(3):
@@ -121,17 +134,22 @@ def _compare_solve(rt, p, prec, tol=None, cfg=None, max_iter=3000):
         assert rel(m["J"], ref["J"]) < 1e-8
     else:
         # both stop within delta_c of the same fixed point
-        assert rel(S, ref["S"]) < t
-        assert rel(m["J"], ref["J"]) < t
+        assert mixed_ok(S, ref["S"]), rel(S, ref["S"])
+        assert mixed_ok(m["J"], ref["J"]), rel(m["J"], ref["J"])
     H = m["H"]
     for q in range(3):
         scale = np.abs(ref["J"]).max()
         assert np.abs(H[:, q] - ref["H"][:, q]).max() < t * scale
-    assert rel(m["K"][:, 0] + m["K"][:, 1] + m["K"][:, 2], ref["K"][:, 0] + ref["K"][:, 1] + ref["K"][:, 2]) < max(t, 1e-8)
+    trK = m["K"][:, 0] + m["K"][:, 1] + m["K"][:, 2]
+    trKr = ref["K"][:, 0] + ref["K"][:, 1] + ref["K"][:, 2]
+    assert (rel(trK, trKr) < 1e-8) if prec == "fp64" else mixed_ok(trK, trKr)
     np.testing.assert_allclose(m["f"][:, 0] + m["f"][:, 1] + m["f"][:, 2], 1.0, rtol=1e-5 if prec == "mixed" else 1e-12)
-    floor = 1e-6 * 4 * math.pi * np.sum(p.freq_w[:, None, None, None] * p.eps * p.chi * p.B, axis=0)
+    emission = 4 * math.pi * np.sum(p.freq_w[:, None, None, None] * p.eps * p.chi * p.B, axis=0)
     dQ = np.abs(m["Q"] - ref["Q"])
-    assert np.all(dQ <= max(t, 1e-8) * np.abs(ref["Q"]) + floor + 1e-300)
+    if prec == "fp64":
+        assert np.all(dQ <= 1e-8 * np.abs(ref["Q"]) + 1e-10 * emission + 1e-300)
+    else:
+        assert np.all(dQ <= 1e-3 * np.abs(ref["Q"]) + 1e-4 * emission + 1e-300)
     return iters, ref["iters"]
 
 
@@ -161,6 +179,32 @@ def test_multifrequency_small(rt, prec):
 def test_random_media_every_boundary(rt, prec):
     p = W.random_box(7, 9, 6, seed=5, n_mu=6, nf=2, bc_lo=(T, P, V), bc_hi=(V, P, T))
     _compare_solve(rt, p, prec, tol=1e-8)
+
+
+def test_mixed_converges_past_float32_floor(rt):
+    """Sweeping increments lets the mixed path reach delta_c far below
+    float32 resolution / eps (a full-S float32 sweep stalls near 1e-5 here)."""
+    p = W.stratified_atmosphere(24, eps=1e-3, nxy=8)
+    og, ref = O.solve_problem(p, tol=1e-9, max_iter=20000)
+    g = make(rt, p, "mixed")
+    iters, resid, st = g.ali_solve(tol=1e-9, max_iter=20000)
+    assert st == rt.RT_OK and resid <= 1e-9
+    assert abs(iters - ref["iters"]) <= 1, (iters, ref["iters"])
+    assert mixed_ok(g.get_S(), ref["S"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kernel_variants_agree(rt, prec):
+    p = W.turbulent_box(32, n_mu=6)
+    out = []
+    for variant in (1, 2):
+        g = make(rt, p, prec, variant=variant)
+        plan = g.sweep_plan()
+        assert plan["variant"] == variant and plan["threads"] <= 512
+        it, _, _ = g.ali_solve(tol=1e-7)
+        out.append((it, g.get_S()))
+    assert abs(out[0][0] - out[1][0]) <= 1
+    assert rel(out[0][1], out[1][1]) < (1e-10 if prec == "fp64" else 1e-4)
 
 
 def test_lte_uses_change_of_J(rt):
