@@ -583,6 +583,14 @@ rt_status fill_bc_any(rt_grid g, int face, cudaStream_t s) {
   return g->desc.prec == RT_PREC_FP64 ? fill_bc<double>(g, face, s) : fill_bc<float>(g, face, s);
 }
 
+// Error word written by the bounds-checked debug build's kernels.
+rt_status check_device_error(rt_grid g) {
+  rtk::SolveState hs{};
+  CU(cudaMemcpy(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost));
+  if (hs.err) return fail(RT_ERR_CUDA, "device bounds check failed (code %d, index %d)", hs.err, hs.err_info);
+  return RT_OK;
+}
+
 template <typename T>
 rtk::SweepArgs<T> sweep_args(rt_grid g) {
   rtk::SweepArgs<T> A{};
@@ -597,6 +605,7 @@ rtk::SweepArgs<T> sweep_args(rt_grid g) {
   A.Gd[0] = (T *)g->Gd[0];
   A.Gd[1] = (T *)g->Gd[1];
   A.incremental = 0;
+  A.ray_slots = g->slots;
   for (int f = 0; f < 6; ++f) A.Ibc[f] = (const T *)g->Ibc[f];
   A.ang = (const AngleParam<T> *)g->angp;
   A.grp = g->grp;
@@ -1019,7 +1028,10 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
   if (r != RT_OK) return r;
   if (J_out && (r = copy_out(J_out, g->J, N, on_device, s)) != RT_OK) return r;
   if (lstar_out && (r = copy_out(lstar_out, g->lstar, N, on_device, s)) != RT_OK) return r;
-  if (!on_device || !opts || !opts->stream) CU(cudaStreamSynchronize(s));
+  if (!on_device || !opts || !opts->stream) {
+    CU(cudaStreamSynchronize(s));
+    if ((r = check_device_error(g)) != RT_OK) return r;
+  }
   g->stats.iters = 1;
   g->stats.updates = (long long)g->d.cells * g->na * g->d.nf;
   g->stats.kernel_launches = g->launches;
@@ -1094,7 +1106,7 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
   if (f && (r = copy_out(f, dF, 6 * N, on_device, s)) != RT_OK) return r;
   if (Q && (r = copy_out(Q, dQ, (size_t)g->d.cells, on_device, s)) != RT_OK) return r;
   CU(cudaStreamSynchronize(s));
-  return RT_OK;
+  return check_device_error(g);
 }
 
 rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts) {

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
+  if (gp.na > A.ray_slots) {   // plan inconsistent with the shared-memory layout: refuse to run
+    if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
+    return;
+  }
   int cax[3];
   plane_axes(gp.axis, cax);
   const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
@@ -367,6 +371,10 @@ __global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> 
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
+  if (gp.na > A.ray_slots) {   // plan inconsistent with the shared-memory layout: refuse to run
+    if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
+    return;
+  }
   int cax[3];
   plane_axes(gp.axis, cax);
   const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
@@ -874,17 +882,12 @@ static int grid_for(long long n, int threads) {
 template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = sc_sweep_kernel<T, AMAX, MOM>;
-  static size_t set_smem = 0;
-  static bool nonportable = false;
-  if (smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // set on every launch: occupancy queries for other plans change these attributes
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (A.cluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    set_smem = smem;
-  }
-  if (A.cluster > 8 && !nonportable) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    nonportable = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
@@ -904,17 +907,12 @@ static cudaError_t launch_sweep_t(const SweepArgs<T> &A, int threads, size_t sme
 template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_tiled_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = sc_sweep_tiled_kernel<T, AMAX, MOM, kSweepSeg>;
-  static size_t set_smem = 0;
-  static bool nonportable = false;
-  if (smem > set_smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // set on every launch: occupancy queries for other plans change these attributes
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (A.cluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    set_smem = smem;
-  }
-  if (A.cluster > 8 && !nonportable) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    nonportable = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
