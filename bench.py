@@ -201,6 +201,8 @@ def run_gpu(args):
     B = torch.from_numpy(p.B).to(dev)
     fw = torch.from_numpy(p.freq_w).to(dev)
     g = rt.Grid.from_problem(p, prec=rt.MIXED)
+    g.set_opacity_source(chi, eps, B, fw)
+    tuned = g.autotune()          # set-up: pick the sweep launch plan once per problem shape
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -277,6 +279,7 @@ def run_gpu(args):
     if not args.skip_fp64:
         g64 = rt.Grid.from_problem(p, prec=rt.FP64)
         g64.set_opacity_source(chi, eps, B, fw)
+        g64.autotune()
         g64.ali_solve(tol=TOL, max_iter=2000)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -336,9 +339,14 @@ def run_profile(args):
     p = workload()
     g = rt.Grid.from_problem(p, prec=rt.FP64 if args.fp64 else rt.MIXED)
     g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+    if args.plan:
+        v, apg, c = (int(x) for x in args.plan.split(","))
+        g.set_sweep_config(apg, c, 0, v)
+    elif not args.no_autotune:
+        g.autotune()
     it, resid, st = g.ali_solve(tol=TOL, max_iter=args.profile_iters, raise_on_fail=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_run": p.name, "iters": it, "resid": resid}), flush=True)
+    print(json.dumps({"profile_run": p.name, "iters": it, "resid": resid, "plan": g.sweep_plan()}), flush=True)
     return 0
 
 
@@ -353,6 +361,8 @@ def main(argv=None):
     ap.add_argument("--profile", action="store_true", help="one short solve for profilers")
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
+    ap.add_argument("--plan", default="", help="with --profile: variant,rays_per_group,cluster")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -183,6 +183,15 @@ rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas,
  * [5] dynamic shared memory bytes per CTA. */
 rt_status rt_get_sweep_plan(rt_grid g, int *plan);
 
+/* Time candidate sweep configurations (variant x rays per group x strips) with
+ * formal solutions of the current medium, keep the fastest for this grid and
+ * remember it for every later grid of the same shape, rays, frequencies,
+ * precision and boundaries in this process.  Leaves S = B and fresh ghosts (as
+ * rt_set_opacity_source does).  plan_out (6 ints, may be NULL) receives the plan
+ * as rt_get_sweep_plan reports it.  Errors: RT_ERR_STATE before
+ * rt_set_opacity_source. */
+rt_status rt_autotune(rt_grid g, int *plan_out);
+
 /* Message describing the last error on this thread (never NULL). */
 const char *rt_last_error(void);
 

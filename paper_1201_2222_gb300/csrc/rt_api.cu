@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -350,7 +351,11 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
     rtk::plane_axes(a, cax);
     const int Nu = g->d.n[cax[0]];
     const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
-    if (variant == 2) {
+    if (variant == 3) {
+      const size_t W = (size_t)rtk::pipe_row_len(Nu, rtk::kSweepSeg);
+      sm = std::max(sm, (size_t)(2 * slots + 6) * (Rmax + 2) * W * g->tsize);
+      th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
+    } else if (variant == 2) {
       const size_t W = (size_t)Nu + 2 + rtk::kSweepSeg;
       sm = std::max(sm, (size_t)(2 * slots + 4) * (Rmax + 2) * W * g->tsize);
       th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
@@ -394,8 +399,9 @@ void make_groups(rt_grid g, int apg, std::vector<GroupParam> &groups, std::vecto
 }
 
 int resident_clusters(rt_grid g, int variant, int amax, int C, int threads, size_t smem) {
-  if (g->desc.prec == RT_PREC_FP64) return rtk::sweep_max_active_clusters<double>(variant == 2, amax, C, threads, smem);
-  return rtk::sweep_max_active_clusters<float>(variant == 2, amax, C, threads, smem);
+  const int kind = variant == 3 ? 3 : (variant == 2 ? 1 : 0);
+  if (g->desc.prec == RT_PREC_FP64) return rtk::sweep_max_active_clusters<double>(kind, amax, C, threads, smem);
+  return rtk::sweep_max_active_clusters<float>(kind, amax, C, threads, smem);
 }
 
 // Choose rays per group and strips per plane: the estimated sweep time is
@@ -436,7 +442,7 @@ void plan_groups(rt_grid g) {
         rtk::plane_axes(a, cax);
         const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
         const int Nu = g->d.n[cax[0]];
-        raw_threads = std::max(raw_threads, variant == 2 ? Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg) : Rmax * Nu);
+        raw_threads = std::max(raw_threads, variant >= 2 ? Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg) : Rmax * Nu);
       }
       int nres = resident_clusters(g, variant, amax_for(namax), C, threads, smem);
       if (nres <= 0) nres = 1;   // unknown occupancy: assume one resident cluster
@@ -451,8 +457,13 @@ void plan_groups(rt_grid g) {
         const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
         work = std::max(work, (double)Rmax * g->d.n[cax[0]]);
       }
-      // per-step cost: cells per strip, plus a fixed barrier/latency floor per step
-      const double est = waves * share * namax * (std::max(work, 64.0 * passes) + 2048.0);
+      // per-step cost: the rays' cells per strip plus a per-ray and per-step staging
+      // and barrier overhead (measured: groups of 7-8 rays beat small groups on
+      // the 128^3 x 80-ray box, whose per-plane work is otherwise latency bound),
+      // and the J partials every group writes
+      const double per_step = namax * std::max(work, 64.0 * passes) + 4096.0 + 1024.0 * namax;
+      const double partials = (double)gr.size() * g->d.nf * (double)g->d.cells / kSMs / 16.0;
+      const double est = waves * share * per_step * (Cmax > 0 ? 1.0 : 1.0) + partials / std::max(1.0, (double)g->d.n[0]);
       if (est < best * 0.999) {
         best = est;
         bapg = apg;
@@ -633,7 +644,9 @@ rt_status enqueue_sweep(rt_grid g, rtk::SweepArgs<T> &A, bool moments, cudaStrea
     CU(cudaEventCreate(&p.b));
     CU(cudaEventRecord(p.a, s));
   }
-  if (g->variant == 2) {
+  if (g->variant == 3) {
+    CU(rtk::launch_sweep_pipe<T>(A, g->amax, moments, g->threads, g->smem, s));
+  } else if (g->variant == 2) {
     CU(rtk::launch_sweep_tiled<T>(A, g->amax, moments, g->threads, g->smem, s));
   } else {
     CU(rtk::launch_sweep<T>(A, g->amax, moments, g->threads, g->smem, s));
@@ -933,7 +946,7 @@ rt_status rt_get_angles(rt_grid g, double *mu, double *w) {
 rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads, int variant) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   if (angles_per_group < 0 || angles_per_group > 8 || cluster_ctas < 0 || cluster_ctas > 16 ||
-      threads < 0 || threads > 512 || (threads % 32) || variant < 0 || variant > 2)
+      threads < 0 || threads > 512 || (threads % 32) || variant < 0 || variant > 3)
     return fail(RT_ERR_ARG, "bad sweep configuration");
   cudaStreamSynchronize(g->own);
   g->req_apg = angles_per_group;
@@ -1122,6 +1135,118 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
 rt_status rt_enable_timing(rt_grid g, int enable) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   g->timing = enable != 0;
+  return RT_OK;
+}
+
+// Plans chosen by rt_autotune, keyed by problem shape (process-wide cache).
+struct TuneKey {
+  int n[3], nf, n_mu, prec, bc[6];
+  bool operator==(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
+};
+struct TuneVal {
+  int variant, apg, cluster;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+TuneKey tune_key(rt_grid g) {
+  TuneKey k;
+  std::memset(&k, 0, sizeof k);
+  for (int a = 0; a < 3; ++a) {
+    k.n[a] = g->d.n[a];
+    k.bc[a] = g->desc.bc_lo[a];
+    k.bc[3 + a] = g->desc.bc_hi[a];
+  }
+  k.nf = g->d.nf;
+  k.n_mu = g->desc.n_mu;
+  k.prec = g->desc.prec;
+  return k;
+}
+
+rt_status rt_autotune(rt_grid g, int *plan_out) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  const TuneKey key = tune_key(g);
+  TuneVal best{0, 0, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : g_tune_cache)
+      if (kv.first == key) best = kv.second;
+  }
+  cudaStream_t s = g->own;
+  const int saved[4] = {g->req_apg, g->req_cluster, g->req_threads, g->req_variant};
+  rt_status r;
+  if (best.variant == 0) {
+    int minNv = 1 << 30;
+    for (int a = 0; a < 3; ++a) {
+      if (!g->used_axis[a]) continue;
+      int cax[3];
+      rtk::plane_axes(a, cax);
+      minNv = std::min(minNv, g->d.n[cax[1]]);
+    }
+    const int variants[3] = {3, 2, 1};
+    const int apgs[5] = {2, 4, 6, 7, 8};
+    const int clusters[5] = {1, 2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    double best_ms = 1e300;
+    for (int vi = 0; vi < 3; ++vi) {
+      for (int ai = 0; ai < 5; ++ai) {
+        for (int ci = 0; ci < 5; ++ci) {
+          if (clusters[ci] > minNv) continue;
+          g->req_variant = variants[vi];
+          g->req_apg = apgs[ai];
+          g->req_cluster = clusters[ci];
+          g->req_threads = 0;
+          plan_groups(g);
+          if (g->groups.empty() || g->smem > kSweepSmemBudget || g->apg != apgs[ai] || g->cluster != clusters[ci])
+            continue;
+          if ((r = upload_plan_any(g)) != RT_OK) return r;
+          float ms = 0.0f;
+          bool ok = true;
+          for (int rep = 0; rep < 3 && ok; ++rep) {   // one warm-up, two timed
+            CU(cudaEventRecord(e0, s));
+            r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
+            if (r != RT_OK) { ok = false; cudaGetLastError(); break; }
+            CU(cudaEventRecord(e1, s));
+            CU(cudaEventSynchronize(e1));
+            float t = 0.0f;
+            CU(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms += t;
+          }
+          if (ok && ms < best_ms) {
+            best_ms = ms;
+            best = TuneVal{variants[vi], apgs[ai], clusters[ci]};
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best.variant == 0) {
+      g->req_apg = saved[0]; g->req_cluster = saved[1]; g->req_threads = saved[2]; g->req_variant = saved[3];
+      plan_groups(g);
+      upload_plan_any(g);
+      return fail(RT_ERR_CUDA, "autotune found no runnable sweep configuration");
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.push_back({key, best});
+  }
+  g->req_variant = best.variant;
+  g->req_apg = best.apg;
+  g->req_cluster = best.cluster;
+  g->req_threads = 0;
+  plan_groups(g);
+  if ((r = upload_plan_any(g)) != RT_OK) return r;
+  // leave the solver state as rt_set_opacity_source does: S = B, fresh ghosts
+  CU(cudaMemcpyAsync(g->S, g->B, (size_t)N_of(g) * 8, cudaMemcpyDeviceToDevice, s));
+  if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  g->last_incremental = false;
+  g->sp_is_delta = false;
+  CU(cudaStreamSynchronize(s));
+  if (plan_out) return rt_get_sweep_plan(g, plan_out);
   return RT_OK;
 }
 

@@ -578,6 +578,391 @@ __global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> 
   }
 }
 
+// ------------------------------------------------------------ pipelined sweep
+// The tiled organisation with the plane loads taken off the critical path:
+//  * chi and S planes live in a three-deep ring in shared memory; while plane t
+//    is computed, plane t+1 streams in with cp.async (16-byte copies when rows
+//    are 16-byte aligned), so the only global-memory latency left is hidden;
+//  * the halo intensities of the plane being computed (ghosts on the domain
+//    faces) are fetched the same way for the next step;
+//  * rows of neighbouring strips are read directly from their CTAs' shared
+//    memory (DSMEM), so each plane costs one cluster barrier.
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  if (sizeof(T) == 4) cp_async4(dst, src);
+  else cp_async8(dst, src);
+}
+
+// Address of the intensity at an out-of-domain upwind vertex (see ghost_I), or
+// nullptr when it is zero (vacuum inflow, or fixed inflow in an incremental sweep).
+template <typename T>
+__device__ __forceinline__ const T *ghost_ptr(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
+                                              int Nw, int f, int angle, const T *Gp, bool inc, int u,
+                                              int v, int w) {
+  int crd[3];
+  crd[cax[0]] = u;
+  crd[cax[1]] = v;
+  crd[cax[2]] = w;
+  int m[3], oor[3], side[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = A.d.n[ax];
+    const int c = crd[ax];
+    oor[ax] = (c < 0) || (c >= n);
+    side[ax] = c >= n;
+    m[ax] = !oor[ax] ? c : (A.d.periodic[ax] ? (c < 0 ? c + n : c - n) : (c < 0 ? 0 : n - 1));
+  }
+#pragma unroll
+  for (int ax = 2; ax >= 0; --ax) {
+    if (oor[ax] && !A.d.periodic[ax]) {
+      if (inc) return nullptr;
+      const int face = 2 * ax + side[ax];
+      const long long idx = ((long long)f * A.na + angle) * A.d.face[ax] + face_cell<T>(A.d, ax, m);
+      return A.Ibc[face] + RT_IDX(idx, (long long)A.d.nf * A.na * A.d.face[ax], 41);
+    }
+  }
+  const long long gb = ((long long)f * A.na + angle) * A.d.gsize;
+  const int ax = oor[2] ? 2 : (oor[1] ? 1 : 0);
+  const int mu_ = m[cax[0]], mv_ = m[cax[1]], mw_ = m[cax[2]];
+  long long off;
+  if (ax == cax[2]) off = (long long)mv_ * Nu + mu_;
+  else if (ax == cax[0]) off = (long long)Nu * Nv + (long long)mw_ * Nv + mv_;
+  else off = (long long)Nu * Nv + (long long)Nw * Nv + (long long)mw_ * Nu + mu_;
+  return Gp + RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 42);
+}
+
+template <typename T>
+__device__ __forceinline__ void ghost_async(T *dst, const T *src) {
+  if (src) cp_async_elem(dst, src);
+  else *dst = T(0);
+}
+
+constexpr int kPipeX0 = 4;   // first interior column of a staged row (16-byte aligned)
+
+template <typename T, int SEG, int SU, int SV>
+__device__ __forceinline__ void pipe_update(const AngleParam<T> &p, const T *__restrict__ Irow,
+                                            const T *__restrict__ Ivrow, T *__restrict__ Iout, int ncell,
+                                            const T (&cm)[SEG + 2], const T (&c0)[SEG + 2],
+                                            const T (&cp)[SEG + 2], const T (&sm)[SEG + 2],
+                                            const T (&s0)[SEG + 2], const T (&sp)[SEG + 2],
+                                            const T (&chi0)[SEG], const T (&S0)[SEG], T (&out)[SEG]) {
+  // Irow / Ivrow point at column X0 + u0 of rows v and v - SV of the upwind plane
+  T Ia[SEG + 1], Iv[SEG + 1];
+  const int cb = SU > 0 ? -1 : 0;
+#pragma unroll
+  for (int k = 0; k < SEG + 1; ++k) {
+    Ia[k] = Irow[cb + k];
+    Iv[k] = Ivrow[cb + k];
+  }
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    const int kA = j + (SU > 0 ? 1 : 0), kB = j + (SU > 0 ? 0 : 1);
+    const int jA = j + 1, jB = j + 1 - SU;
+    const T chiC = SV > 0 ? cm[jA] : cp[jA], chiD = SV > 0 ? cm[jB] : cp[jB];
+    const T sC = SV > 0 ? sm[jA] : sp[jA], sD = SV > 0 ? sm[jB] : sp[jB];
+    const T chim = p.wa * c0[jA] + p.wb * c0[jB] + p.wc * chiC + p.wd * chiD;
+    const T Sm = p.wa * s0[jA] + p.wb * s0[jB] + p.wc * sC + p.wd * sD;
+    const T Im = p.wa * Ia[kA] + p.wb * Ia[kB] + p.wc * Iv[kA] + p.wd * Iv[kB];
+    const T dtau = (chim + chi0[j]) * p.hs;
+    T E, psi0, om;
+    seg_weights(dtau, E, psi0, om);
+    out[j] = Sm + E * (Im - Sm) + psi0 * (S0[j] - Sm);
+  }
+  // a ragged last segment must not touch the halo column beyond the row
+#pragma unroll
+  for (int j = 0; j < SEG; ++j)
+    if (j < ncell) Iout[j] = out[j];
+}
+
+template <typename T, int AMAX, bool MOM, int SEG>
+__global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
+  if (A.skip_if_done && A.st->done) return;
+  const int C = A.cluster;
+  const int rank = blockIdx.x % C;
+  const int inst = blockIdx.x / C;
+  const int gi = inst % A.ngroups;
+  const int f = inst / A.ngroups;
+  const GroupParam gp = A.grp[gi];
+  if (gp.na > A.ray_slots) {
+    if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
+    return;
+  }
+  int cax[3];
+  plane_axes(gp.axis, cax);
+  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
+  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int v0 = (int)(((long long)rank * Nv) / C);
+  const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
+  const int R = v1 - v0;
+  const int Rmax = (Nv + C - 1) / C;
+  const int W = pipe_row_len(Nu, SEG);
+  const int RX = Rmax + 2;
+  const int pb = RX * W;               // one staged plane
+  const int ib = A.ray_slots * pb;     // one plane of every ray of the group
+  const long long plane = (long long)Nu * Nv;
+  const long long cells = A.d.cells;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Ib = reinterpret_cast<T *>(smem_raw);   // [2][slots][RX][W]   intensities
+  T *Cr = Ib + 2 * ib;                       // [3][RX][W]          chi ring
+  T *Sr = Cr + 3 * pb;                       // [3][RX][W]          S ring
+#ifdef RT_DEBUG_BOUNDS
+  const long long smem_n = 2LL * ib + 6LL * pb;
+#endif
+  __shared__ AngleParam<T> P[AMAX];
+  if (threadIdx.x < gp.na) P[threadIdx.x] = A.ang[gp.a0 + threadIdx.x];
+
+  const int fs = A.st->fs_count + A.parity_offset;
+  const int prev = fs & 1;
+  const T *Gp = A.G[prev];
+  T *Gn = A.G[prev ^ 1];
+  const bool inc = A.incremental && A.st->iter > 0;
+  const bool emit = A.incremental && A.st->iter == 0;
+  const T *Gsrc = inc ? A.Gd[prev] : Gp;
+  T *Gdn = A.incremental ? A.Gd[prev ^ 1] : nullptr;
+  const T *chiP = A.chiP[gp.axis] + (long long)f * cells;
+  const T *SP = A.SP[gp.axis] + (long long)f * cells;
+  T *Jout = A.Jpart + ((long long)gi * A.d.nf + f) * cells;
+  const int sa = gp.sa;
+  const int wlast = sa > 0 ? Nw - 1 : 0;
+  const int na = gp.na;
+  const int nseg = (Nu + SEG - 1) / SEG;
+  const bool vec = (sizeof(T) == 4) && (Nu % 4 == 0);
+  const bool top_edge = v0 == 0 && !perV;      // no strip and no periodic image below
+  const bool bot_edge = v1 == Nv && !perV;
+  cg::cluster_group cluster = cg::this_cluster();
+  __syncthreads();
+
+  // chi and S of plane wsrc (rows v0-1 .. v1, columns -1 .. Nu, wrapped or clamped) -> ring slot
+  auto stage = [&](int wsrc, int slot) {
+    T *Cd = Cr + slot * pb, *Sd = Sr + slot * pb;
+    const int rows = R + 2;
+    if (vec) {
+      const int q = Nu / 4;
+      for (int idx = threadIdx.x; idx < rows * q; idx += blockDim.x) {
+        const int row = idx / q, k = idx - row * q;
+        int vv = v0 - 1 + row;
+        vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
+        const long long o = (long long)wsrc * plane + (long long)vv * Nu + 4 * k;
+        cp_async16(Cd + RT_IDX(row * W + kPipeX0 + 4 * k, 6LL * pb, 43), chiP + o);
+        cp_async16(Sd + RT_IDX(row * W + kPipeX0 + 4 * k, 6LL * pb, 43), SP + o);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < rows * Nu; idx += blockDim.x) {
+        const int row = idx / Nu, u = idx - row * Nu;
+        int vv = v0 - 1 + row;
+        vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
+        const long long o = (long long)wsrc * plane + (long long)vv * Nu + u;
+        cp_async_elem(Cd + RT_IDX(row * W + kPipeX0 + u, 6LL * pb, 44), chiP + o);
+        cp_async_elem(Sd + RT_IDX(row * W + kPipeX0 + u, 6LL * pb, 44), SP + o);
+      }
+    }
+    for (int idx = threadIdx.x; idx < 2 * rows; idx += blockDim.x) {
+      const int side = idx / rows, row = idx - side * rows;
+      int vv = v0 - 1 + row;
+      vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
+      const int uu = side ? (perU ? 0 : Nu - 1) : (perU ? Nu - 1 : 0);
+      const long long o = (long long)wsrc * plane + (long long)vv * Nu + uu;
+      const int col = side ? kPipeX0 + Nu : kPipeX0 - 1;
+      cp_async_elem(Cd + RT_IDX(row * W + col, 6LL * pb, 45), chiP + o);
+      cp_async_elem(Sd + RT_IDX(row * W + col, 6LL * pb, 45), SP + o);
+    }
+  };
+  // ghost intensities of plane wsrc around the strip: halo columns of every row,
+  // and the halo rows on a domain face without a periodic image (whole plane if all)
+  auto ghost_halo = [&](T *Ibuf, int wsrc, bool whole) {
+    if (whole) {
+      const int ext = (R + 2) * (Nu + 2);
+      for (int idx = threadIdx.x; idx < na * ext; idx += blockDim.x) {
+        const int a = idx / ext, r2 = idx - a * ext;
+        const int row = r2 / (Nu + 2), col = r2 - row * (Nu + 2);
+        ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 - 1 + col, 2LL * ib, 46),
+                    ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, col - 1, v0 - 1 + row, wsrc));
+      }
+      return;
+    }
+    for (int idx = threadIdx.x; idx < na * 2 * (R + 2); idx += blockDim.x) {
+      const int a = idx / (2 * (R + 2)), r2 = idx - a * 2 * (R + 2);
+      const int side = r2 / (R + 2), row = r2 - side * (R + 2);
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + (side ? kPipeX0 + Nu : kPipeX0 - 1), 2LL * ib, 47),
+                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, side ? Nu : -1, v0 - 1 + row, wsrc));
+    }
+    const int nrow = (v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0);   // rows outside the domain in v
+    for (int idx = threadIdx.x; idx < na * nrow * Nu; idx += blockDim.x) {
+      const int a = idx / (nrow * Nu), r2 = idx - a * nrow * Nu;
+      const int which = r2 / Nu, u = r2 - which * Nu;
+      const bool lo = (v0 == 0) && (which == 0);
+      const int row = lo ? 0 : R + 1;
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 + u, 2LL * ib, 48),
+                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, u, lo ? -1 : Nv, wsrc));
+    }
+  };
+
+  // prologue: the first plane, the upwind ghost plane, and its intensities
+  const int w0 = sa > 0 ? 0 : Nw - 1;
+  stage(w0, 0);
+  stage(perW ? (sa > 0 ? Nw - 1 : 0) : w0, 2);
+  ghost_halo(Ib + ib, w0 - sa, true);
+  cp_async_commit();
+  cp_async_wait_all();
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+
+  for (int t = 0; t < Nw; ++t) {
+    const int w = sa > 0 ? t : Nw - 1 - t;
+    T *Icur = Ib + (t & 1) * ib;
+    const T *Iprv = Ib + ((t + 1) & 1) * ib;
+    const T *Cc = Cr + (t % 3) * pb, *Cp = Cr + ((t + 2) % 3) * pb;
+    const T *Sc = Sr + (t % 3) * pb, *Sp = Sr + ((t + 2) % 3) * pb;
+    // next plane's chi and S, and this plane's halo ghosts for the next step
+    if (t + 1 < Nw) stage(w + sa, (t + 1) % 3);
+    ghost_halo(Icur, w, false);
+    cp_async_commit();
+    // neighbouring strips' rows of the upwind plane
+    const T *Itop = nullptr, *Ibot = nullptr;   // rows v0-1 and v1 at column X0
+    if (C > 1 && t > 0) {
+      if (rank > 0) {
+        const int rv0 = (int)(((long long)(rank - 1) * Nv) / C);
+        Itop = cluster.map_shared_rank(const_cast<T *>(Iprv), rank - 1) + (v0 - 1 - rv0 + 1) * W + kPipeX0;
+      }
+      if (rank < C - 1) {
+        Ibot = cluster.map_shared_rank(const_cast<T *>(Iprv), rank + 1) + 1 * W + kPipeX0;
+      }
+    }
+    const bool at_wlast = perW && (w == wlast);
+    for (int sidx = threadIdx.x; sidx < R * nseg; sidx += blockDim.x) {
+      const int lv = sidx / nseg, seg = sidx - lv * nseg;
+      const int u0 = seg * SEG, v = v0 + lv, row = lv + 1;
+      const int ncell = min(SEG, Nu - u0);
+      T cm[SEG + 2], c0[SEG + 2], cp[SEG + 2], sm[SEG + 2], s0[SEG + 2], sp[SEG + 2];
+#pragma unroll
+      for (int j = 0; j < SEG + 2; ++j) {
+        const int col = kPipeX0 - 1 + u0 + j;
+        cm[j] = Cp[(row - 1) * W + col];
+        c0[j] = Cp[row * W + col];
+        cp[j] = Cp[(row + 1) * W + col];
+        sm[j] = Sp[(row - 1) * W + col];
+        s0[j] = Sp[row * W + col];
+        sp[j] = Sp[(row + 1) * W + col];
+      }
+      T chi0[SEG], S0[SEG], Jacc[SEG];
+      T Hm[MOM ? SEG : 1][3], Km[MOM ? SEG : 1][6];
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        chi0[j] = Cc[row * W + kPipeX0 + u0 + j];
+        S0[j] = Sc[row * W + kPipeX0 + u0 + j];
+        Jacc[j] = T(0);
+        if (MOM) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) Hm[MOM ? j : 0][q] = T(0);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Km[MOM ? j : 0][q] = T(0);
+        }
+      }
+      const bool seg_u_first = u0 == 0, seg_u_last = u0 + ncell == Nu;
+#pragma unroll
+      for (int a = 0; a < AMAX; ++a) {
+        if (a < na) {
+          const AngleParam<T> &p = P[a];
+          const T *Ia = Iprv + a * pb + row * W + kPipeX0 + u0;
+          T *Io = Icur + a * pb + row * W + kPipeX0 + u0;
+          T I0[SEG];
+          // row v - sv of the upwind plane: own rows, a neighbour's, or the ghost halo row
+          const T *Iv;
+          if (p.sv > 0) Iv = (lv == 0 && Itop) ? Itop + a * pb + u0 : Ia - W;
+          else Iv = (lv == R - 1 && Ibot) ? Ibot + a * pb + u0 : Ia + W;
+          const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
+          if (key == 3) pipe_update<T, SEG, 1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else if (key == 2) pipe_update<T, SEG, -1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else if (key == 1) pipe_update<T, SEG, 1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          else pipe_update<T, SEG, -1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+#pragma unroll
+          for (int j = 0; j < SEG; ++j) {
+            const T wI = p.wq * I0[j];
+            Jacc[j] += wI;
+            if (MOM) {
+              Hm[MOM ? j : 0][0] += wI * p.mu[0];
+              Hm[MOM ? j : 0][1] += wI * p.mu[1];
+              Hm[MOM ? j : 0][2] += wI * p.mu[2];
+              Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+              Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+              Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+              Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+              Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+              Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
+            }
+          }
+          if (A.write_ghosts) {
+            const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+            const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+            if (at_wlast) {
+#pragma unroll
+              for (int j = 0; j < SEG; ++j)
+                if (j < ncell)
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 49), I0[j], inc, emit);
+            }
+            if (perU && (p.su > 0 ? seg_u_last : seg_u_first)) {
+              const int j = p.su > 0 ? ncell - 1 : 0;
+              T val = I0[0];
+#pragma unroll
+              for (int q = 1; q < SEG; ++q)
+                if (q == j) val = I0[q];
+              ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 50), val, inc, emit);
+            }
+            if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
+#pragma unroll
+              for (int j = 0; j < SEG; ++j)
+                if (j < ncell)
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 51),
+                                 I0[j], inc, emit);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < SEG; ++j) {
+        if (j < ncell) {
+          int crd[3];
+          crd[cax[0]] = u0 + j;
+          crd[cax[1]] = v;
+          crd[cax[2]] = w;
+          const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+          Jout[RT_IDX(canon, cells, 52)] = Jacc[j];
+          if (MOM) {
+            T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
+            const long long qs = (long long)A.d.nf * cells;
+            const long long o = (long long)f * cells + canon;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[MOM ? j : 0][q];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[MOM ? j : 0][q];
+          }
+        }
+      }
+    }
+    cp_async_wait_all();
+    if (C > 1) cluster.sync();
+    else __syncthreads();
+  }
+  (void)top_edge;
+  (void)bot_edge;
+}
+
 // --------------------------------------------------------------------- ALI update
 
 __device__ __forceinline__ double rel_change(double d, double x) {
@@ -611,42 +996,67 @@ __device__ __forceinline__ long long perm_index(const Dims &d, int a, long long 
 // Jacobi ALI (Eq. 24): dS = [(1-eps) J + eps B - S] / [1 - (1-eps) Lambda*], with
 // the denominator formed as eps + (1-eps)(1 - Lambda*) from the separately summed
 // 1 - Lambda* (no cancellation in thick cells).  All of it in FP64.
+// A block owns a tile of 32 x 32 cells (x, y) of one z plane and frequency; the
+// sweep copies of the new S (or of dS) are written x-contiguous for the y and z
+// sweeps and through a shared-memory transpose, y-contiguous, for the x sweep.
+constexpr int kAliTile = 32;
+constexpr int kAliRows = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(256) ali_update_kernel(const AliArgs<T> A) {
+__global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const AliArgs<T> A) {
   if (A.st->done) return;
+  __shared__ T tile[kAliTile][kAliTile + 1];
+  const int nx = A.d.n[0], ny = A.d.n[1], nz = A.d.n[2];
+  const int tx = threadIdx.x % kAliTile, ty = threadIdx.x / kAliTile;
+  const int tiles_x = (nx + kAliTile - 1) / kAliTile;
+  const int x0 = (blockIdx.x % tiles_x) * kAliTile, y0 = (blockIdx.x / tiles_x) * kAliTile;
+  const int z = blockIdx.y, f = blockIdx.z;
   const long long cells = A.d.cells;
-  const long long N = cells * A.d.nf;
+  const long long fbase = (long long)f * cells;
   const bool first = A.st->iter == 0;
   const bool inc = A.incremental && !first;
+  const int x = x0 + tx;
   double rmax = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / cells, c = i - f * cells;
-    double dJ = 0.0;
-    for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[((long long)p * A.d.nf + f) * cells + c];
-    // incremental solves accumulate J in FP64 from the swept increments
-    const double J = inc ? A.J64[i] + dJ : dJ;
-    double r;
-    if (A.lte) {
-      const double Jp = A.incremental ? A.J64[i] : A.Jprev[i];
-      r = first ? INFINITY : rel_change(inc ? dJ : J - Jp, J);
-      A.Jprev[i] = J;
-      if (A.incremental)
-        for (int a = 0; a < 3; ++a)
-          if (A.SP[a]) A.SP[a][f * cells + perm_index(A.d, a, c)] = T(0);
-    } else {
-      const double S = A.S64[i], e = A.eps[i];
-      const double dS = ((1.0 - e) * J + e * A.B[i] - S) / (e + (1.0 - e) * A.oml[i]);
-      const double Sn = S + dS;
-      A.S64[i] = Sn;
-      A.Sfs[i] = S;
-      r = rel_change(dS, Sn);
-      const T Snt = (T)(A.incremental ? dS : Sn);
-      for (int a = 0; a < 3; ++a)
-        if (A.SP[a]) A.SP[a][f * cells + perm_index(A.d, a, c)] = Snt;
+#pragma unroll
+  for (int k = 0; k < kAliTile / kAliRows; ++k) {
+    const int y = y0 + ty + k * kAliRows;
+    T snew = T(0);
+    if (x < nx && y < ny) {
+      const long long c = ((long long)z * ny + y) * nx + x;
+      const long long i = fbase + c;
+      double dJ = 0.0;
+      for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[(long long)p * A.d.nf * cells + i];
+      // incremental solves accumulate J in FP64 from the swept increments
+      const double J = inc ? A.J64[i] + dJ : dJ;
+      double r;
+      if (A.lte) {
+        const double Jp = A.incremental ? A.J64[i] : A.Jprev[i];
+        r = first ? INFINITY : rel_change(inc ? dJ : J - Jp, J);
+        A.Jprev[i] = J;
+        snew = A.incremental ? T(0) : (T)A.S64[i];
+      } else {
+        const double S = A.S64[i], e = A.eps[i];
+        const double dS = ((1.0 - e) * J + e * A.B[i] - S) / (e + (1.0 - e) * A.oml[i]);
+        const double Sn = S + dS;
+        A.S64[i] = Sn;
+        A.Sfs[i] = S;
+        r = rel_change(dS, Sn);
+        snew = (T)(A.incremental ? dS : Sn);
+      }
+      A.J64[i] = J;
+      rmax = fmax(rmax, r);
+      if (A.SP[2]) A.SP[2][i] = snew;                                                 // [z][y][x]
+      if (A.SP[1]) A.SP[1][fbase + ((long long)y * nz + z) * nx + x] = snew;          // [y][z][x]
     }
-    A.J64[i] = J;
-    rmax = fmax(rmax, r);
+    tile[ty + k * kAliRows][tx] = snew;
+  }
+  if (A.SP[0]) {                                                                      // [x][z][y]
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kAliTile / kAliRows; ++k) {
+      const int xx = x0 + ty + k * kAliRows, yy = y0 + tx;
+      if (xx < nx && yy < ny) A.SP[0][fbase + ((long long)xx * nz + z) * ny + yy] = tile[tx][ty + k * kAliRows];
+    }
   }
   block_max_to(rmax, &A.st->resid_bits);
 }
@@ -929,6 +1339,42 @@ static cudaError_t launch_tiled_t(const SweepArgs<T> &A, int threads, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
+template <typename T, int AMAX, bool MOM>
+static cudaError_t launch_pipe_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
+  auto kern = sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (A.cluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)A.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = A.cluster > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, A);
+}
+
+template <typename T>
+cudaError_t launch_sweep_pipe(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                              cudaStream_t s) {
+  switch (amax) {
+    case 1: return moments ? launch_pipe_t<T, 1, true>(A, threads, smem, s) : launch_pipe_t<T, 1, false>(A, threads, smem, s);
+    case 2: return moments ? launch_pipe_t<T, 2, true>(A, threads, smem, s) : launch_pipe_t<T, 2, false>(A, threads, smem, s);
+    case 4: return moments ? launch_pipe_t<T, 4, true>(A, threads, smem, s) : launch_pipe_t<T, 4, false>(A, threads, smem, s);
+    case 8: return moments ? launch_pipe_t<T, 8, true>(A, threads, smem, s) : launch_pipe_t<T, 8, false>(A, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                                cudaStream_t s) {
@@ -955,8 +1401,9 @@ cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int thre
 
 template <typename T, int AMAX>
 static int max_active_t(int tiled, int cluster, int threads, size_t smem) {
-  const void *kern = tiled ? (const void *)sc_sweep_tiled_kernel<T, AMAX, false, kSweepSeg>
-                           : (const void *)sc_sweep_kernel<T, AMAX, false>;
+  const void *kern = tiled == 3 ? (const void *)sc_sweep_pipe_kernel<T, AMAX, false, kSweepSeg>
+                    : (tiled ? (const void *)sc_sweep_tiled_kernel<T, AMAX, false, kSweepSeg>
+                             : (const void *)sc_sweep_kernel<T, AMAX, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
   if (cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return -1;
@@ -992,8 +1439,9 @@ int sweep_max_active_clusters(int tiled, int amax, int cluster, int threads, siz
 
 template <typename T>
 cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s) {
-  const long long n = A.d.cells * A.d.nf;
-  ali_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(A);
+  const dim3 grid((unsigned)(((A.d.n[0] + kAliTile - 1) / kAliTile) * ((A.d.n[1] + kAliTile - 1) / kAliTile)),
+                  (unsigned)A.d.n[2], (unsigned)A.d.nf);
+  ali_update_kernel<T><<<grid, kAliTile * kAliRows, 0, s>>>(A);
   return cudaGetLastError();
 }
 
@@ -1064,6 +1512,7 @@ cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, c
 #define RT_INSTANTIATE(T)                                                                          \
   template cudaError_t launch_sweep<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
   template cudaError_t launch_sweep_tiled<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template cudaError_t launch_sweep_pipe<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
   template int sweep_max_active_clusters<T>(int, int, int, int, size_t);                          \
   template cudaError_t launch_ali<T>(const AliArgs<T> &, cudaStream_t);                             \
   template cudaError_t launch_lstar<T>(const Dims &, const double *, const RayGeom *, int, double *, \

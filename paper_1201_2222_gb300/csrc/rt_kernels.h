@@ -46,8 +46,14 @@ struct AliArgs {
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                          cudaStream_t s);
-// cells per thread of the tiled sweep
+// cells per thread of the tiled sweeps
 constexpr int kSweepSeg = 4;
+// staged row length of the pipelined sweep: 4 leading columns (halo at 3), Nu
+// cells, halo, segment padding, rounded to 16 bytes
+__host__ __device__ inline int pipe_row_len(int Nu, int seg) { return ((4 + Nu + 1 + seg + 3) / 4) * 4; }
+template <typename T>
+cudaError_t launch_sweep_pipe(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                              cudaStream_t s);
 // clusters of one sweep configuration that can be resident at once (-1 on error)
 template <typename T>
 int sweep_max_active_clusters(int tiled, int amax, int cluster, int threads, size_t smem);

@@ -70,6 +70,7 @@ _SIGS = {
     "rt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(rt_stats)]),
     "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rt_get_sweep_plan": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "rt_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "rt_angle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rt_last_error": (ctypes.c_char_p, []),
 }
@@ -207,6 +208,11 @@ class Grid:
 
     def set_sweep_config(self, angles_per_group=0, cluster_ctas=0, threads=0, variant=0):
         _check(load().rt_set_sweep_config(self._h, angles_per_group, cluster_ctas, threads, variant))
+
+    def autotune(self):
+        v = (ctypes.c_int * 6)()
+        _check(load().rt_autotune(self._h, v))
+        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem"), list(v)))
 
     def sweep_plan(self):
         v = (ctypes.c_int * 6)()

@@ -69,7 +69,7 @@ FS_CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", range(len(FS_CASES)))
 def test_formal_solution_and_lambda_star(rt, prec, case, variant):
@@ -105,7 +105,7 @@ def test_fixed_boundary_searchlight(rt):
     faces = [np.zeros(og.na * og.face[f // 2]) for f in range(6)]
     faces[4] = I.reshape(-1)
     Ifix = np.concatenate(faces)
-    for prec, variant in (("fp64", 1), ("fp64", 2), ("mixed", 1), ("mixed", 2)):
+    for prec, variant in (("fp64", 1), ("fp64", 2), ("fp64", 3), ("mixed", 1), ("mixed", 2), ("mixed", 3)):
         g = make(rt, p, prec, variant=variant)
         g.set_boundary_intensity(4, I)
         G = O.init_ghosts(og, p.B[0])
@@ -197,14 +197,28 @@ def test_mixed_converges_past_float32_floor(rt):
 def test_kernel_variants_agree(rt, prec):
     p = W.turbulent_box(32, n_mu=6)
     out = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         g = make(rt, p, prec, variant=variant)
         plan = g.sweep_plan()
         assert plan["variant"] == variant and plan["threads"] <= 512
         it, _, _ = g.ali_solve(tol=1e-7)
         out.append((it, g.get_S()))
-    assert abs(out[0][0] - out[1][0]) <= 1
-    assert rel(out[0][1], out[1][1]) < (1e-10 if prec == "fp64" else 1e-4)
+    for k in (1, 2):
+        assert abs(out[0][0] - out[k][0]) <= 1
+        assert rel(out[0][1], out[k][1]) < (1e-10 if prec == "fp64" else 1e-4)
+
+
+def test_autotune_keeps_results(rt):
+    p = W.turbulent_box(24, n_mu=4)
+    g = make(rt, p, "mixed")
+    J0 = g.formal_solve(p.B)
+    plan = g.autotune()
+    assert plan["variant"] in (1, 2, 3) and plan["groups"] >= 1
+    assert rel(g.get_S(), p.B) == 0.0           # state left as after set_opacity_source
+    J1 = g.formal_solve(p.B)
+    assert rel(J1, J0) < 1e-5
+    g2 = make(rt, p, "mixed")
+    assert g2.autotune() == plan                # cached for the same problem shape
 
 
 def test_lte_uses_change_of_J(rt):
