@@ -59,7 +59,12 @@ typedef enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_THERMAL = 2, RT_BC_FI
  *   MIXED: the sweep (interpolation, segment weights, intensities, the per-sweep
  *          angle sums) in float32 with a Taylor form of the segment weights for
  *          small optical depth; J summed across sweeps, Lambda*, the ALI update,
- *          its denominator and the convergence test in double precision. */
+ *          its denominator and the convergence test in double precision.  After
+ *          the first formal solution of a solve the sweeps carry only the change
+ *          of S (float32 rounding then scales with the update).  Frequency bins
+ *          where scattering makes the problem ill-conditioned for float32 (unit
+ *          roundoff / the smallest eps of optically thick cells > 1e-4) are swept
+ *          in FP64 instead. */
 typedef enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 } rt_precision;
 
 typedef struct {
@@ -178,16 +183,18 @@ rt_status rt_get_stats(rt_grid g, rt_stats *out);
 rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads,
                               int variant);
 
-/* The sweep plan in use: plan[0] variant, [1] groups per frequency, [2] rays per
- * group (max), [3] strips per plane (cluster size), [4] threads per CTA,
- * [5] dynamic shared memory bytes per CTA. */
+/* The sweep plan in use (7 ints): plan[0] variant, [1] groups per frequency,
+ * [2] rays per group (max), [3] strips per plane (cluster size), [4] threads per
+ * CTA, [5] dynamic shared memory bytes per CTA, [6] frequency bins a mixed grid
+ * sweeps in FP64 because the float32 error bound (unit roundoff / the smallest
+ * eps of optically thick cells) exceeds 1e-4 there. */
 rt_status rt_get_sweep_plan(rt_grid g, int *plan);
 
 /* Time candidate sweep configurations (variant x rays per group x strips) with
  * formal solutions of the current medium, keep the fastest for this grid and
  * remember it for every later grid of the same shape, rays, frequencies,
  * precision and boundaries in this process.  Leaves S = B and fresh ghosts (as
- * rt_set_opacity_source does).  plan_out (6 ints, may be NULL) receives the plan
+ * rt_set_opacity_source does).  plan_out (7 ints, may be NULL) receives the plan
  * as rt_get_sweep_plan reports it.  Errors: RT_ERR_STATE before
  * rt_set_opacity_source. */
 rt_status rt_autotune(rt_grid g, int *plan_out);

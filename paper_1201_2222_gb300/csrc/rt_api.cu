@@ -290,6 +290,17 @@ struct rt_grid_s {
   bool timing = false;
   rt_stats stats{};
   long long launches = 0;
+
+  // Mixed grids: frequency bins whose float32 error bound (unit roundoff over the
+  // smallest eps of optically thick cells) exceeds prec_limit are solved by an
+  // internal FP64 grid and masked out of this grid's ALI update.
+  rt_grid sub64 = nullptr;
+  std::vector<int> bins64;
+  unsigned char *fmask = nullptr;
+  unsigned long long *epsmin = nullptr;
+  double *tmp2 = nullptr;
+  size_t tmp2_n = 0;
+  double prec_limit = 1e-4;
 };
 
 namespace {
@@ -709,6 +720,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   L.st = g->st;
   L.lte = g->lte ? 1 : 0;
   L.incremental = incremental;
+  L.fmask = g->fmask;
   std::vector<EventPair> ev;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (g->timing) {
@@ -792,6 +804,95 @@ rt_status moments_sweep(rt_grid g, cudaStream_t s) {
   A.write_ghosts = 0;
   A.skip_if_done = 0;
   return enqueue_sweep<T>(g, A, true, s, nullptr);
+}
+
+rt_status ensure_tmp2(rt_grid g, size_t n) {
+  if (n <= g->tmp2_n) return RT_OK;
+  if (g->tmp2) cudaFree(g->tmp2);
+  g->tmp2 = nullptr;
+  g->tmp2_n = 0;
+  CU(cudaMalloc((void **)&g->tmp2, n * sizeof(double)));
+  g->tmp2_n = n;
+  return RT_OK;
+}
+
+// copy frequency bins `bins` of a [nf][block] array into a packed [bins][block] array
+// (gather) or back (scatter)
+rt_status move_bins(const std::vector<int> &bins, double *packed, double *full, size_t block, bool gather,
+                    cudaMemcpyKind kind, cudaStream_t s) {
+  for (size_t k = 0; k < bins.size(); ++k) {
+    double *a = packed + k * block, *b = full + (size_t)bins[k] * block;
+    CU(cudaMemcpyAsync(gather ? a : b, gather ? b : a, block * sizeof(double), kind, s));
+  }
+  return RT_OK;
+}
+
+// Inflow intensities of fixed faces, restricted to the FP64 bins.
+rt_status sync_sub_bc(rt_grid g, int face) {
+  rt_grid h = g->sub64;
+  if (!h || !g->user_bc[face]) return RT_OK;
+  const size_t block = (size_t)g->na * g->d.face[face / 2];
+  if (!h->user_bc[face]) CU(cudaMalloc((void **)&h->user_bc[face], g->bins64.size() * block * 8));
+  rt_status r = move_bins(g->bins64, h->user_bc[face], g->user_bc[face], block, true, cudaMemcpyDeviceToDevice, g->own);
+  if (r != RT_OK) return r;
+  CU(cudaStreamSynchronize(g->own));
+  return fill_bc_any(h, face, h->own);
+}
+
+// Decide which bins of a mixed grid need FP64 sweeps and (re)build the FP64 grid.
+rt_status plan_precision(rt_grid g) {
+  const int nf = g->d.nf;
+  cudaStream_t s = g->own;
+  if (!g->epsmin) CU(cudaMalloc((void **)&g->epsmin, nf * sizeof(unsigned long long)));
+  std::vector<unsigned long long> init(nf, (unsigned long long)0x3FF0000000000000ULL);   // 1.0
+  CU(cudaMemcpyAsync(g->epsmin, init.data(), nf * 8, cudaMemcpyHostToDevice, s));
+  CU(rtk::launch_eps_thick_min(g->d, g->eps, g->oml, g->epsmin, s));
+  g->launches++;
+  std::vector<unsigned long long> bits(nf);
+  CU(cudaMemcpyAsync(bits.data(), g->epsmin, nf * 8, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  std::vector<int> ill;
+  const double u32 = 5.96e-8;   // float32 unit roundoff
+  for (int f = 0; f < nf; ++f) {
+    double e;
+    std::memcpy(&e, &bits[f], 8);
+    if (u32 / e > g->prec_limit) ill.push_back(f);
+  }
+  if (ill.empty()) {
+    if (g->sub64) rt_destroy_grid(g->sub64);
+    g->sub64 = nullptr;
+    g->bins64.clear();
+    if (g->fmask) cudaFree(g->fmask);
+    g->fmask = nullptr;
+    return RT_OK;
+  }
+  if (!g->sub64 || g->bins64 != ill) {
+    if (g->sub64) rt_destroy_grid(g->sub64);
+    g->sub64 = nullptr;
+    rt_grid_desc d = g->desc;
+    d.prec = RT_PREC_FP64;
+    d.nfreq = (int)ill.size();
+    rt_status r = rt_create_grid(&d, &g->sub64);
+    if (r != RT_OK) return r;
+    g->bins64 = ill;
+  }
+  const size_t C = (size_t)g->d.cells, m = ill.size();
+  rt_status r = ensure_tmp(g, 3 * m * C + m);
+  if (r != RT_OK) return r;
+  double *tc = g->tmp, *te = tc + m * C, *tb = te + m * C, *tw = tb + m * C;
+  if ((r = move_bins(ill, tc, g->chi, C, true, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+  if ((r = move_bins(ill, te, g->eps, C, true, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+  if ((r = move_bins(ill, tb, g->B, C, true, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+  if ((r = move_bins(ill, tw, g->fw, 1, true, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+  CU(cudaStreamSynchronize(s));
+  if ((r = rt_set_opacity_source(g->sub64, tc, te, tb, tw, 1)) != RT_OK) return r;
+  for (int face = 0; face < 6; ++face)
+    if ((r = sync_sub_bc(g, face)) != RT_OK) return r;
+  std::vector<unsigned char> mask(nf, 0);
+  for (int f : ill) mask[f] = 1;
+  if (!g->fmask) CU(cudaMalloc((void **)&g->fmask, nf));
+  CU(cudaMemcpy(g->fmask, mask.data(), nf, cudaMemcpyHostToDevice));
+  return RT_OK;
 }
 
 }  // namespace
@@ -910,6 +1011,10 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
 rt_status rt_destroy_grid(rt_grid g) {
   if (!g) return RT_OK;
   if (g->own) cudaStreamSynchronize(g->own);
+  if (g->sub64) rt_destroy_grid(g->sub64);
+  if (g->fmask) cudaFree(g->fmask);
+  if (g->epsmin) cudaFree(g->epsmin);
+  if (g->tmp2) cudaFree(g->tmp2);
   void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
                   g->Gd[0], g->Gd[1],
@@ -998,6 +1103,7 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
   if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
   for (int f = 0; f < 6; ++f)
     if ((r = fill_bc_any(g, f, s)) != RT_OK) return r;
+  if (g->desc.prec == RT_PREC_MIXED && (r = plan_precision(g)) != RT_OK) return r;
   g->have_medium = true;
   return RT_OK;
 }
@@ -1016,7 +1122,7 @@ rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I) {
   rt_status r = fill_bc_any(g, face, g->own);
   if (r != RT_OK) return r;
   CU(cudaStreamSynchronize(g->own));
-  return RT_OK;
+  return sync_sub_bc(g, face);
 }
 
 rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out, int on_device,
@@ -1039,6 +1145,23 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
   }
   r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
   if (r != RT_OK) return r;
+  if (g->sub64) {   // FP64 bins: their formal solution replaces the float32 one
+    const size_t C = (size_t)g->d.cells, m = g->bins64.size();
+    if ((r = ensure_tmp2(g, 2 * m * C)) != RT_OK) return r;
+    double *tj = g->tmp2, *tl = tj + m * C;
+    const double *Ssub = nullptr;
+    if (S) {
+      if ((r = move_bins(g->bins64, tj, g->S, C, true, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+      Ssub = tj;
+    }
+    CU(cudaStreamSynchronize(s));
+    rt_solve_opts o2{};
+    o2.stream = (void *)s;
+    if ((r = rt_formal_solve(g->sub64, Ssub, tj, tl, 1, &o2)) != RT_OK) return r;
+    CU(cudaStreamSynchronize(s));
+    if ((r = move_bins(g->bins64, tj, g->J, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, tl, g->lstar, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+  }
   if (J_out && (r = copy_out(J_out, g->J, N, on_device, s)) != RT_OK) return r;
   if (lstar_out && (r = copy_out(lstar_out, g->lstar, N, on_device, s)) != RT_OK) return r;
   if (!on_device || !opts || !opts->stream) {
@@ -1073,6 +1196,32 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
   r = g->desc.prec == RT_PREC_FP64 ? ali_loop<double>(g, opts, s, &iters, &resid, &conv)
                                    : ali_loop<float>(g, opts, s, &iters, &resid, &conv);
   if (r != RT_OK) return r;
+  if (g->sub64) {   // FP64 bins, then their S, J and last-formal-solution S merged back
+    const size_t C = (size_t)g->d.cells, m = g->bins64.size();
+    if ((r = ensure_tmp2(g, m * C)) != RT_OK) return r;
+    const double *Ssub = nullptr;
+    if (S_init) {
+      if ((r = move_bins(g->bins64, g->tmp2, const_cast<double *>(S_init), C, true,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s)) != RT_OK)
+        return r;
+      Ssub = g->tmp2;
+    }
+    CU(cudaStreamSynchronize(s));
+    rt_solve_opts o2 = opts ? *opts : rt_solve_opts{1e-6, 1000, 0, nullptr};
+    o2.stream = (void *)s;
+    int it2 = 0;
+    double res2 = 0.0;
+    r = rt_ali_solve(g->sub64, Ssub, 1, &o2, &it2, &res2);
+    if (r != RT_OK && r != RT_ERR_NOT_CONVERGED) return r;
+    if (r == RT_ERR_NOT_CONVERGED) conv = false;
+    iters = std::max(iters, it2);
+    resid = std::max(resid, res2);
+    if ((r = move_bins(g->bins64, g->sub64->S, g->S, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, g->sub64->J, g->J, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, g->sub64->Sfs, g->Sfs, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    CU(cudaStreamSynchronize(s));
+    g->stats.sweep_ms += g->sub64->stats.sweep_ms;
+  }
   if (iters_out) *iters_out = iters;
   if (resid_out) *resid_out = resid;
   g->stats.iters = iters;
@@ -1108,6 +1257,19 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
   if (g->last_incremental) {
     // J of the last formal solution as the solve accumulated it in FP64
     CU(cudaMemcpyAsync(dJ, g->J, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  if (g->sub64) {   // the FP64 bins' moments replace the float32 ones
+    const size_t C = (size_t)g->d.cells, m = g->bins64.size();
+    if ((r = ensure_tmp2(g, 16 * m * C + C)) != RT_OK) return r;
+    double *sJ = g->tmp2, *sH = sJ + m * C, *sK = sH + 3 * m * C, *sF = sK + 6 * m * C, *sQ = sF + 6 * m * C;
+    CU(cudaStreamSynchronize(s));
+    rt_solve_opts o2{};
+    o2.stream = (void *)s;
+    if ((r = rt_moments(g->sub64, sJ, sH, sK, sF, sQ, 1, &o2)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, sJ, dJ, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, sH, dH, 3 * C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, sK, dK, 6 * C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
+    if ((r = move_bins(g->bins64, sF, dF, 6 * C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
   }
   CU(rtk::launch_heating(g->d, g->fw, g->chi, g->eps, dJ, g->B, dQ, s));
   g->launches += 2;   // moment reduction + heating rate
@@ -1258,6 +1420,7 @@ rt_status rt_get_sweep_plan(rt_grid g, int *plan) {
   plan[3] = g->cluster;
   plan[4] = g->threads;
   plan[5] = (int)g->smem;
+  plan[6] = (int)g->bins64.size();
   return RT_OK;
 }
 

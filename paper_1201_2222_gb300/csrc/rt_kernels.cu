@@ -1017,6 +1017,10 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
   const bool inc = A.incremental && !first;
   const int x = x0 + tx;
   double rmax = 0.0;
+  if (A.fmask && A.fmask[f]) {   // this frequency is solved by another grid
+    block_max_to(0.0, &A.st->resid_bits);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < kAliTile / kAliRows; ++k) {
     const int y = y0 + ty + k * kAliRows;
@@ -1266,6 +1270,15 @@ __global__ void reduce_moments_kernel(Dims d, int ngroups, const T *Jpart, const
   }
 }
 
+__global__ void eps_thick_min_kernel(Dims d, const double *eps, const double *oml,
+                                     unsigned long long *out) {
+  const long long N = d.cells * d.nf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (oml[i] < 0.5) atomicMin(&out[i / d.cells], (unsigned long long)__double_as_longlong(eps[i]));
+  }
+}
+
 // Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)  (integral form, Sec. 4).
 __global__ void heating_kernel(Dims d, const double *fw, const double *chi, const double *eps,
                                const double *J, const double *B, double *Q) {
@@ -1500,6 +1513,12 @@ cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, co
                                   double *J, double *H, double *K, double *F, int two_d,
                                   cudaStream_t s) {
   reduce_moments_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, ngroups, Jpart, Mpart, J, H, K, F, two_d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double *oml,
+                                 unsigned long long *out, cudaStream_t s) {
+  eps_thick_min_kernel<<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, eps, oml, out);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ struct AliArgs {
   SolveState *st;
   int lte;
   int incremental;           // partials are increments of J; SP receives dS
+  const unsigned char *fmask; // frequencies solved elsewhere (skipped; NULL = none)
 };
 
 template <typename T>
@@ -83,6 +84,10 @@ template <typename T>
 cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, const T *Mpart,
                                   double *J, double *H, double *K, double *F, int two_d,
                                   cudaStream_t s);
+// per frequency: the smallest eps among optically thick cells (1 - Lambda* < 1/2),
+// as the bits of a non-negative double (atomicMin); cells with none leave 1.0
+cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double *oml,
+                                 unsigned long long *out, cudaStream_t s);
 cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, const double *eps,
                            const double *J, const double *B, double *Q, cudaStream_t s);
 

@@ -210,14 +210,16 @@ class Grid:
         _check(load().rt_set_sweep_config(self._h, angles_per_group, cluster_ctas, threads, variant))
 
     def autotune(self):
-        v = (ctypes.c_int * 6)()
+        v = (ctypes.c_int * 7)()
         _check(load().rt_autotune(self._h, v))
-        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem"), list(v)))
+        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem", "fp64_bins"),
+                        list(v)))
 
     def sweep_plan(self):
-        v = (ctypes.c_int * 6)()
+        v = (ctypes.c_int * 7)()
         _check(load().rt_get_sweep_plan(self._h, v))
-        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem"), list(v)))
+        return dict(zip(("variant", "groups", "rays_per_group", "cluster", "threads", "smem", "fp64_bins"),
+                        list(v)))
 
     def set_opacity_source(self, chi, eps, B, freq_w=None):
         pc, dc, kc = self._in(chi)

@@ -170,8 +170,14 @@ def test_turbulent_box_small(rt, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_multifrequency_small(rt, prec):
-    """Frequency-dependent absorption over 8 bins at 16^3 (all bins in one launch)."""
+    """Frequency-dependent absorption over 8 bins at 16^3 (all bins in one launch).
+    The high-frequency bins scatter almost purely (eps ~ 1e-6 in thick layers), so a
+    mixed grid must sweep those in FP64 (float32 error ~ unit roundoff / eps)."""
     p = W.multifrequency_atmosphere(16, nf=8)
+    if prec == "mixed":
+        g = make(rt, p, prec)
+        plan = g.sweep_plan()
+        assert 0 < plan["fp64_bins"] < p.nf, plan
     _compare_solve(rt, p, prec)
 
 
