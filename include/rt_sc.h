@@ -199,6 +199,33 @@ rt_status rt_get_sweep_plan(rt_grid g, int *plan);
  * rt_set_opacity_source. */
 rt_status rt_autotune(rt_grid g, int *plan_out);
 
+/* One formal solution that allocates nothing on the device.
+ *
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * call cudaMalloc, for example a host framework that has already reserved the
+ * device memory for its own pool, or a time-critical loop that must not take
+ * the device-wide synchronisation an allocation can imply.  It computes what
+ * rt_create_grid + rt_set_opacity_source + rt_formal_solve(S) would (J = Lambda[S]
+ * with first-iteration periodic ghosts, the default sweep plan, no FP64 bin
+ * split), taking all working memory (sweep copies, ghosts, partial sums,
+ * tables, control block) from one static device array of
+ * RT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  The caller passes device pointers: chi, S, B
+ * [nf][nz][ny][nx] (read; not validated) and J_out [nf][nz][ny][nx] (written),
+ * and a cudaStream_t (NULL = the legacy default stream); the call synchronises
+ * that stream before it returns.
+ *   - Problems whose working memory exceeds the array return RT_ERR_ARG before
+ *     any device work; so do fixed-intensity faces.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (device current): make that first call before any
+ *     stream capture.
+ *   - Every call shares the array and it keeps the previous call's contents
+ *     (only its control block is cleared): calls that overlap on the GPU, from
+ *     several streams or threads, race and must be serialised by the caller. */
+#define RT_NOALLOC_SCRATCH_BYTES (64ULL << 20)
+rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const double *chi, const double *S,
+                                  const double *B, double *J_out, void *stream);
+
 /* Message describing the last error on this thread (never NULL). */
 const char *rt_last_error(void);
 

@@ -1432,3 +1432,166 @@ rt_status rt_get_stats(rt_grid g, rt_stats *out) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------- allocation-free formal solution
+// Working memory for rt_formal_solve_noalloc: one array in this library's device
+// image.  Every GPU that loads the library holds it until the process exits;
+// every call uses it, so calls that overlap on the GPU race.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};   // device address of g_noalloc_scratch per device ordinal
+
+// Looked up once per device, with that device current (host code cannot use the
+// array's name as a device address).
+rt_status noalloc_base(char **out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(RT_ERR_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(RT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (char *)g_noalloc_addr[dev];
+  return RT_OK;
+}
+
+// Carves 256-byte aligned pieces off the scratch array (or measures, with base NULL).
+struct ScratchCarver {
+  char *base;
+  size_t off = 0;
+  void *take(size_t bytes) {
+    const size_t a = (off + 255) & ~(size_t)255;
+    off = a + bytes;
+    return base ? base + a : nullptr;
+  }
+};
+
+template <typename T>
+rt_status noalloc_run(rt_grid_s &g, const double *chi, const double *S, const double *B, double *J,
+                      cudaStream_t s) {
+  // the same per-ray constants as a grid's sweep plan
+  std::vector<AngleParam<T>> ap(g.group_angles.size());
+  for (size_t gi = 0; gi < g.groups.size(); ++gi) {
+    const GroupParam &gp = g.groups[gi];
+    int cax[3];
+    rtk::plane_axes(gp.axis, cax);
+    for (int q = 0; q < gp.na; ++q) {
+      const int k = g.group_angles[gp.a0 + q];
+      const RayGeom &r = g.rays[k];
+      const double fu = r.frac[cax[0]], fv = r.frac[cax[1]];
+      AngleParam<T> p{};
+      p.wq = (T)r.w;
+      p.hs = (T)(0.5 * r.s);
+      p.wa = (T)((1.0 - fu) * (1.0 - fv));
+      p.wb = (T)(fu * (1.0 - fv));
+      p.wc = (T)((1.0 - fu) * fv);
+      p.wd = (T)(fu * fv);
+      for (int a = 0; a < 3; ++a) p.mu[a] = (T)g.mu[3 * k + a];
+      p.su = r.sgn[cax[0]];
+      p.sv = r.sgn[cax[1]];
+      p.angle = k;
+      ap[gp.a0 + q] = p;
+    }
+  }
+  const size_t N = (size_t)g.d.cells * g.d.nf;
+  const size_t gbytes = (size_t)g.d.nf * g.na * g.d.gsize * sizeof(T);
+  auto layout = [&](ScratchCarver &c) {
+    g.st = (rtk::SolveState *)c.take(sizeof(rtk::SolveState));
+    g.angp = c.take(std::max<size_t>(1, ap.size()) * sizeof(AngleParam<T>));
+    g.grp = (GroupParam *)c.take(std::max<size_t>(1, g.groups.size()) * sizeof(GroupParam));
+    g.rays_d = (RayGeom *)c.take((size_t)g.na * sizeof(RayGeom));
+    for (int a = 0; a < 3; ++a) {
+      g.chiP[a] = g.used_axis[a] ? c.take(N * sizeof(T)) : nullptr;
+      g.SP[a] = g.used_axis[a] ? c.take(N * sizeof(T)) : nullptr;
+    }
+    g.G[0] = c.take(gbytes);
+    g.G[1] = c.take(gbytes);
+    for (int f = 0; f < 6; ++f)
+      g.Ibc[f] = g.d.periodic[f / 2] ? nullptr : c.take((size_t)g.d.nf * g.na * g.d.face[f / 2] * sizeof(T));
+    g.Jpart = c.take(g.groups.size() * N * sizeof(T));
+  };
+  ScratchCarver measure{nullptr};
+  layout(measure);
+  if (measure.off > RT_NOALLOC_SCRATCH_BYTES)
+    return fail(RT_ERR_ARG, "rt_formal_solve_noalloc: this problem needs %zu bytes of scratch, more than the %llu available",
+                measure.off, (unsigned long long)RT_NOALLOC_SCRATCH_BYTES);
+  if (!chi || !S || !B || !J) return fail(RT_ERR_ARG, "rt_formal_solve_noalloc: NULL array");
+  char *base = nullptr;
+  rt_status r = noalloc_base(&base);
+  if (r != RT_OK) return r;
+  ScratchCarver carve{base};
+  layout(carve);
+  g.jpart_groups = g.groups.size();
+  g.chi = const_cast<double *>(chi);
+  g.B = const_cast<double *>(B);
+  g.J = J;
+  // the array keeps the previous call's contents: only the control block must start at zero
+  CU(cudaMemsetAsync(g.st, 0, sizeof(rtk::SolveState), s));
+  CU(cudaMemcpyAsync(g.angp, ap.data(), ap.size() * sizeof(AngleParam<T>), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(g.grp, g.groups.data(), g.groups.size() * sizeof(GroupParam), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(g.rays_d, g.rays.data(), g.na * sizeof(RayGeom), cudaMemcpyHostToDevice, s));
+  if ((r = permute_into<T>(&g, chi, g.chiP, s)) != RT_OK) return r;
+  if ((r = permute_into<T>(&g, S, g.SP, s)) != RT_OK) return r;
+  if ((r = init_ghosts<T>(&g, S, s)) != RT_OK) return r;
+  for (int f = 0; f < 6; ++f)
+    if ((r = fill_bc<T>(&g, f, s)) != RT_OK) return r;
+  if ((r = formal_once<T>(&g, s)) != RT_OK) return r;
+  CU(cudaStreamSynchronize(s));   // also keeps the host tables alive until copied
+  return check_device_error(&g);
+}
+
+}  // namespace
+
+extern "C" rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const double *chi, const double *S,
+                                             const double *B, double *J_out, void *stream) {
+  if (!desc) return fail(RT_ERR_ARG, "rt_formal_solve_noalloc: NULL descriptor");
+  const rt_grid_desc &D = *desc;
+  if (D.nx < 1 || D.ny < 1 || D.nz < 1 || D.nfreq < 1) return fail(RT_ERR_ARG, "grid sizes and nfreq must be >= 1");
+  if (!(D.dx > 0) || !(D.dy > 0) || (D.nz > 1 && !(D.dz > 0))) return fail(RT_ERR_ARG, "cell spacings must be > 0");
+  if (D.prec != RT_PREC_FP64 && D.prec != RT_PREC_MIXED) return fail(RT_ERR_ARG, "bad precision");
+  for (int a = 0; a < 3; ++a) {
+    if (D.bc_lo[a] < 0 || D.bc_lo[a] > 2 || D.bc_hi[a] < 0 || D.bc_hi[a] > 2)
+      return fail(RT_ERR_ARG, "rt_formal_solve_noalloc supports periodic, vacuum and thermal faces only");
+    if ((a < 2 || D.nz > 1) && (D.bc_lo[a] == RT_BC_PERIODIC) != (D.bc_hi[a] == RT_BC_PERIODIC))
+      return fail(RT_ERR_ARG, "axis %d: a periodic axis must be periodic on both faces", a);
+  }
+  // the size limit is checked before any pointer is touched
+  rt_grid_s g;
+  g.desc = D;
+  g.two_d = D.nz == 1;
+  if (g.two_d) {
+    g.desc.bc_lo[2] = g.desc.bc_hi[2] = RT_BC_PERIODIC;
+    g.desc.dz = 1.0;
+  }
+  if (!level_symmetric(D.n_mu, g.two_d, g.mu, g.wq))
+    return fail(RT_ERR_ARG, "n_mu must be 2, 4, 6, 8, 10 or 12 (got %d)", D.n_mu);
+  g.na = (int)g.wq.size();
+  g.tsize = D.prec == RT_PREC_FP64 ? 8 : 4;
+  g.d.n[0] = D.nx;
+  g.d.n[1] = D.ny;
+  g.d.n[2] = D.nz;
+  g.d.nf = D.nfreq;
+  g.d.cells = (long long)D.nx * D.ny * D.nz;
+  for (int a = 0; a < 3; ++a) {
+    g.d.bc_lo[a] = g.desc.bc_lo[a];
+    g.d.bc_hi[a] = g.desc.bc_hi[a];
+    g.d.periodic[a] = g.desc.bc_lo[a] == RT_BC_PERIODIC;
+  }
+  g.d.face[0] = (long long)D.nz * D.ny;
+  g.d.face[1] = (long long)D.nz * D.nx;
+  g.d.face[2] = (long long)D.ny * D.nx;
+  g.d.gsize = g.d.face[0] + g.d.face[1] + g.d.face[2];
+  build_rays(&g);
+  plan_groups(&g);
+  cudaStream_t s = (cudaStream_t)stream;
+  return D.prec == RT_PREC_FP64 ? noalloc_run<double>(g, chi, S, B, J_out, s)
+                                : noalloc_run<float>(g, chi, S, B, J_out, s);
+}
+

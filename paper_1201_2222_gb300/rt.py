@@ -72,6 +72,7 @@ _SIGS = {
     "rt_get_sweep_plan": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "rt_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "rt_angle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "rt_formal_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(rt_grid_desc), _VP, _VP, _VP, _VP, _VP]),
     "rt_last_error": (ctypes.c_char_p, []),
 }
 
@@ -123,6 +124,27 @@ def angle_table(n_mu, two_d=False):
     w = np.empty(n)
     lib.rt_angle_table(n_mu, 1 if two_d else 0, mu.ctypes.data, w.ctypes.data)
     return mu, w
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def formal_solve_noalloc(nx, ny, nz, chi, S, B, J_out, n_mu=4, nfreq=1,
+                         bc_lo=(PERIODIC, PERIODIC, THERMAL), bc_hi=(PERIODIC, PERIODIC, VACUUM),
+                         dx=1.0, dy=1.0, dz=1.0, prec=MIXED):
+    """J = Lambda[S] with no device allocation (see rt_formal_solve_noalloc).
+
+    chi, S, B, J_out: CUDA float64 torch tensors [nf][nz][ny][nx]; runs on torch's
+    current stream."""
+    lib = load()
+    if isinstance(prec, str):
+        prec = {"fp64": FP64, "mixed": MIXED}[prec.lower()]
+    d = rt_grid_desc(nx, ny, nz, dx, dy, dz, n_mu, nfreq, (ctypes.c_int * 3)(*bc_lo),
+                     (ctypes.c_int * 3)(*bc_hi), prec)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    stream = _torch().cuda.current_stream().cuda_stream
+    _check(lib.rt_formal_solve_noalloc(ctypes.byref(d), ptr(chi), ptr(S), ptr(B), ptr(J_out), stream))
+    return J_out
 
 
 class Grid:
