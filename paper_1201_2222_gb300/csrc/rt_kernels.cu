@@ -690,7 +690,40 @@ __device__ __forceinline__ void pipe_update(const AngleParam<T> &p, const T *__r
     if (j < ncell) Iout[j] = out[j];
 }
 
-template <typename T, int AMAX, bool MOM, int SEG>
+// One staged row around a 4-cell segment, (u0-1 .. u0+4), without bank conflicts:
+// one aligned 128-bit load per lane, neighbours by warp shuffle from the adjacent
+// lanes (same row, adjacent segment) or, at row ends, by a scalar load.
+__device__ __forceinline__ void vec_row(const float *rowp, bool haveL, bool haveR, float (&o)[6]) {
+  const float4 q = *reinterpret_cast<const float4 *>(rowp);
+  float l = __shfl_up_sync(0xffffffffu, q.w, 1);
+  float r = __shfl_down_sync(0xffffffffu, q.x, 1);
+  if (!haveL) l = rowp[-1];
+  if (!haveR) r = rowp[4];
+  o[0] = l; o[1] = q.x; o[2] = q.y; o[3] = q.z; o[4] = q.w; o[5] = r;
+}
+
+template <int SU, int SV>
+__device__ __forceinline__ void vec_update(const AngleParam<float> &p, const float (&Ir)[6], const float (&Iw)[6],
+                                           const float (&cm)[6], const float (&c0)[6], const float (&cp)[6],
+                                           const float (&sm)[6], const float (&s0)[6], const float (&sp)[6],
+                                           const float (&chi0)[4], const float (&S0)[4], float (&out)[4]) {
+  // Ir, Iw: rows v and v - SV of the upwind plane, columns u0-1 .. u0+4
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int jA = j + 1, jB = j + 1 - SU;
+    const float chiC = SV > 0 ? cm[jA] : cp[jA], chiD = SV > 0 ? cm[jB] : cp[jB];
+    const float sC = SV > 0 ? sm[jA] : sp[jA], sD = SV > 0 ? sm[jB] : sp[jB];
+    const float chim = p.wa * c0[jA] + p.wb * c0[jB] + p.wc * chiC + p.wd * chiD;
+    const float Sm = p.wa * s0[jA] + p.wb * s0[jB] + p.wc * sC + p.wd * sD;
+    const float Im = p.wa * Ir[jA] + p.wb * Ir[jB] + p.wc * Iw[jA] + p.wd * Iw[jB];
+    const float dtau = (chim + chi0[j]) * p.hs;
+    float E, psi0, om;
+    seg_weights(dtau, E, psi0, om);
+    out[j] = Sm + E * (Im - Sm) + psi0 * (S0[j] - Sm);
+  }
+}
+
+template <typename T, int AMAX, bool MOM, int SEG, bool VEC>
 __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;
@@ -845,112 +878,235 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
       }
     }
     const bool at_wlast = perW && (w == wlast);
-    for (int sidx = threadIdx.x; sidx < R * nseg; sidx += blockDim.x) {
-      const int lv = sidx / nseg, seg = sidx - lv * nseg;
-      const int u0 = seg * SEG, v = v0 + lv, row = lv + 1;
-      const int ncell = min(SEG, Nu - u0);
-      T cm[SEG + 2], c0[SEG + 2], cp[SEG + 2], sm[SEG + 2], s0[SEG + 2], sp[SEG + 2];
-#pragma unroll
-      for (int j = 0; j < SEG + 2; ++j) {
-        const int col = kPipeX0 - 1 + u0 + j;
-        cm[j] = Cp[(row - 1) * W + col];
-        c0[j] = Cp[row * W + col];
-        cp[j] = Cp[(row + 1) * W + col];
-        sm[j] = Sp[(row - 1) * W + col];
-        s0[j] = Sp[row * W + col];
-        sp[j] = Sp[(row + 1) * W + col];
-      }
-      T chi0[SEG], S0[SEG], Jacc[SEG];
-      T Hm[MOM ? SEG : 1][3], Km[MOM ? SEG : 1][6];
-#pragma unroll
-      for (int j = 0; j < SEG; ++j) {
-        chi0[j] = Cc[row * W + kPipeX0 + u0 + j];
-        S0[j] = Sc[row * W + kPipeX0 + u0 + j];
-        Jacc[j] = T(0);
+    if constexpr (VEC) {
+      // float32 rows whose length is a multiple of 4: one segment per lane, a
+      // warp-uniform trip count so every shuffle has the whole warp
+      const int ntask = R * nseg;
+      const int lane = threadIdx.x & 31;
+      const int ustride = cax[0] == 0 ? 1 : A.d.n[0];   // canonical stride along u
+      for (int base = threadIdx.x - lane; base < ntask; base += blockDim.x) {
+        const int sidx = base + lane;
+        const bool active = sidx < ntask;
+        const int sc = active ? sidx : ntask - 1;
+        const int lv = sc / nseg, seg = sc - lv * nseg;
+        const int u0 = seg * 4, v = v0 + lv, row = lv + 1;
+        const bool haveL = active && seg > 0 && lane > 0;
+        const bool haveR = active && seg < nseg - 1 && lane < 31 && sidx + 1 < ntask;
+        float cm[6], c0[6], cp[6], sm[6], s0[6], sp[6];
+        const float *Cpr = reinterpret_cast<const float *>(Cp) + row * W + kPipeX0 + u0;
+        const float *Spr = reinterpret_cast<const float *>(Sp) + row * W + kPipeX0 + u0;
+        vec_row(Cpr - W, haveL, haveR, cm);
+        vec_row(Cpr, haveL, haveR, c0);
+        vec_row(Cpr + W, haveL, haveR, cp);
+        vec_row(Spr - W, haveL, haveR, sm);
+        vec_row(Spr, haveL, haveR, s0);
+        vec_row(Spr + W, haveL, haveR, sp);
+        const float4 q0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(Cc) + row * W + kPipeX0 + u0);
+        const float4 r0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(Sc) + row * W + kPipeX0 + u0);
+        const float chi0[4] = {q0.x, q0.y, q0.z, q0.w};
+        const float S0[4] = {r0.x, r0.y, r0.z, r0.w};
+        float Jacc[4] = {0.f, 0.f, 0.f, 0.f};
+        float Hm[MOM ? 4 : 1][3], Km[MOM ? 4 : 1][6];
         if (MOM) {
 #pragma unroll
-          for (int q = 0; q < 3; ++q) Hm[MOM ? j : 0][q] = T(0);
+          for (int j = 0; j < (MOM ? 4 : 1); ++j) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) Km[MOM ? j : 0][q] = T(0);
-        }
-      }
-      const bool seg_u_first = u0 == 0, seg_u_last = u0 + ncell == Nu;
+            for (int q = 0; q < 3; ++q) Hm[j][q] = 0.f;
 #pragma unroll
-      for (int a = 0; a < AMAX; ++a) {
-        if (a < na) {
-          const AngleParam<T> &p = P[a];
-          const T *Ia = Iprv + a * pb + row * W + kPipeX0 + u0;
-          T *Io = Icur + a * pb + row * W + kPipeX0 + u0;
-          T I0[SEG];
-          // row v - sv of the upwind plane: own rows, a neighbour's, or the ghost halo row
-          const T *Iv;
-          if (p.sv > 0) Iv = (lv == 0 && Itop) ? Itop + a * pb + u0 : Ia - W;
-          else Iv = (lv == R - 1 && Ibot) ? Ibot + a * pb + u0 : Ia + W;
-          const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
-          if (key == 3) pipe_update<T, SEG, 1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-          else if (key == 2) pipe_update<T, SEG, -1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-          else if (key == 1) pipe_update<T, SEG, 1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-          else pipe_update<T, SEG, -1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-#pragma unroll
-          for (int j = 0; j < SEG; ++j) {
-            const T wI = p.wq * I0[j];
-            Jacc[j] += wI;
-            if (MOM) {
-              Hm[MOM ? j : 0][0] += wI * p.mu[0];
-              Hm[MOM ? j : 0][1] += wI * p.mu[1];
-              Hm[MOM ? j : 0][2] += wI * p.mu[2];
-              Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
-              Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
-              Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
-              Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
-              Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
-              Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
-            }
-          }
-          if (A.write_ghosts) {
-            const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
-            const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
-            if (at_wlast) {
-#pragma unroll
-              for (int j = 0; j < SEG; ++j)
-                if (j < ncell)
-                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 49), I0[j], inc, emit);
-            }
-            if (perU && (p.su > 0 ? seg_u_last : seg_u_first)) {
-              const int j = p.su > 0 ? ncell - 1 : 0;
-              T val = I0[0];
-#pragma unroll
-              for (int q = 1; q < SEG; ++q)
-                if (q == j) val = I0[q];
-              ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 50), val, inc, emit);
-            }
-            if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
-#pragma unroll
-              for (int j = 0; j < SEG; ++j)
-                if (j < ncell)
-                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 51),
-                                 I0[j], inc, emit);
-            }
+            for (int q = 0; q < 6; ++q) Km[j][q] = 0.f;
           }
         }
-      }
+        const bool seg_u_first = u0 == 0, seg_u_last = u0 + 4 >= Nu;
 #pragma unroll
-      for (int j = 0; j < SEG; ++j) {
-        if (j < ncell) {
+        for (int a = 0; a < AMAX; ++a) {
+          if (a < na) {
+            const AngleParam<float> &p = reinterpret_cast<const AngleParam<float> &>(P[a]);
+            const float *Ia = reinterpret_cast<const float *>(Iprv) + a * pb + row * W + kPipeX0 + u0;
+            const float *Iv;
+            if (p.sv > 0) Iv = (lv == 0 && Itop) ? reinterpret_cast<const float *>(Itop) + a * pb + u0 : Ia - W;
+            else Iv = (lv == R - 1 && Ibot) ? reinterpret_cast<const float *>(Ibot) + a * pb + u0 : Ia + W;
+            float Ir[6], Iw[6], I0[4];
+            vec_row(Ia, haveL, haveR, Ir);
+            vec_row(Iv, haveL, haveR, Iw);
+            const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
+            if (key == 3) vec_update<1, 1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else if (key == 2) vec_update<-1, 1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else if (key == 1) vec_update<1, -1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else vec_update<-1, -1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            if (active)
+              *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Icur) + a * pb + row * W + kPipeX0 + u0) =
+                  make_float4(I0[0], I0[1], I0[2], I0[3]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float wI = p.wq * I0[j];
+              Jacc[j] += wI;
+              if (MOM) {
+                Hm[MOM ? j : 0][0] += wI * p.mu[0];
+                Hm[MOM ? j : 0][1] += wI * p.mu[1];
+                Hm[MOM ? j : 0][2] += wI * p.mu[2];
+                Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+                Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+                Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+                Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+                Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+                Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
+              }
+            }
+            if (A.write_ghosts && active) {
+              const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+              const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+              if (at_wlast) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 53), (T)I0[j], inc, emit);
+              }
+              if (perU && (p.su > 0 ? seg_u_last : seg_u_first))
+                ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 54),
+                               (T)(p.su > 0 ? I0[3] : I0[0]), inc, emit);
+              if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 55),
+                                 (T)I0[j], inc, emit);
+              }
+            }
+          }
+        }
+        if (active) {
           int crd[3];
-          crd[cax[0]] = u0 + j;
+          crd[cax[0]] = u0;
           crd[cax[1]] = v;
           crd[cax[2]] = w;
           const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
-          Jout[RT_IDX(canon, cells, 52)] = Jacc[j];
+          float *Jf = reinterpret_cast<float *>(Jout);
+          if (ustride == 1) {
+            *reinterpret_cast<float4 *>(Jf + RT_IDX(canon, cells, 56)) = make_float4(Jacc[0], Jacc[1], Jacc[2], Jacc[3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Jf[RT_IDX(canon + (long long)j * ustride, cells, 57)] = Jacc[j];
+          }
           if (MOM) {
             T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
             const long long qs = (long long)A.d.nf * cells;
-            const long long o = (long long)f * cells + canon;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[MOM ? j : 0][q];
+            for (int j = 0; j < 4; ++j) {
+              const long long o = (long long)f * cells + canon + (long long)j * ustride;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[MOM ? j : 0][q];
+              for (int q = 0; q < 3; ++q) M[q * qs + o] = (T)Hm[MOM ? j : 0][q];
+#pragma unroll
+              for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = (T)Km[MOM ? j : 0][q];
+            }
+          }
+        }
+      }
+    } else {
+      for (int sidx = threadIdx.x; sidx < R * nseg; sidx += blockDim.x) {
+        const int lv = sidx / nseg, seg = sidx - lv * nseg;
+        const int u0 = seg * SEG, v = v0 + lv, row = lv + 1;
+        const int ncell = min(SEG, Nu - u0);
+        T cm[SEG + 2], c0[SEG + 2], cp[SEG + 2], sm[SEG + 2], s0[SEG + 2], sp[SEG + 2];
+  #pragma unroll
+        for (int j = 0; j < SEG + 2; ++j) {
+          const int col = kPipeX0 - 1 + u0 + j;
+          cm[j] = Cp[(row - 1) * W + col];
+          c0[j] = Cp[row * W + col];
+          cp[j] = Cp[(row + 1) * W + col];
+          sm[j] = Sp[(row - 1) * W + col];
+          s0[j] = Sp[row * W + col];
+          sp[j] = Sp[(row + 1) * W + col];
+        }
+        T chi0[SEG], S0[SEG], Jacc[SEG];
+        T Hm[MOM ? SEG : 1][3], Km[MOM ? SEG : 1][6];
+  #pragma unroll
+        for (int j = 0; j < SEG; ++j) {
+          chi0[j] = Cc[row * W + kPipeX0 + u0 + j];
+          S0[j] = Sc[row * W + kPipeX0 + u0 + j];
+          Jacc[j] = T(0);
+          if (MOM) {
+  #pragma unroll
+            for (int q = 0; q < 3; ++q) Hm[MOM ? j : 0][q] = T(0);
+  #pragma unroll
+            for (int q = 0; q < 6; ++q) Km[MOM ? j : 0][q] = T(0);
+          }
+        }
+        const bool seg_u_first = u0 == 0, seg_u_last = u0 + ncell == Nu;
+  #pragma unroll
+        for (int a = 0; a < AMAX; ++a) {
+          if (a < na) {
+            const AngleParam<T> &p = P[a];
+            const T *Ia = Iprv + a * pb + row * W + kPipeX0 + u0;
+            T *Io = Icur + a * pb + row * W + kPipeX0 + u0;
+            T I0[SEG];
+            // row v - sv of the upwind plane: own rows, a neighbour's, or the ghost halo row
+            const T *Iv;
+            if (p.sv > 0) Iv = (lv == 0 && Itop) ? Itop + a * pb + u0 : Ia - W;
+            else Iv = (lv == R - 1 && Ibot) ? Ibot + a * pb + u0 : Ia + W;
+            const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
+            if (key == 3) pipe_update<T, SEG, 1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else if (key == 2) pipe_update<T, SEG, -1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else if (key == 1) pipe_update<T, SEG, 1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            else pipe_update<T, SEG, -1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+  #pragma unroll
+            for (int j = 0; j < SEG; ++j) {
+              const T wI = p.wq * I0[j];
+              Jacc[j] += wI;
+              if (MOM) {
+                Hm[MOM ? j : 0][0] += wI * p.mu[0];
+                Hm[MOM ? j : 0][1] += wI * p.mu[1];
+                Hm[MOM ? j : 0][2] += wI * p.mu[2];
+                Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+                Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+                Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+                Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+                Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+                Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
+              }
+            }
+            if (A.write_ghosts) {
+              const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+              const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+              if (at_wlast) {
+  #pragma unroll
+                for (int j = 0; j < SEG; ++j)
+                  if (j < ncell)
+                    ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 49), I0[j], inc, emit);
+              }
+              if (perU && (p.su > 0 ? seg_u_last : seg_u_first)) {
+                const int j = p.su > 0 ? ncell - 1 : 0;
+                T val = I0[0];
+  #pragma unroll
+                for (int q = 1; q < SEG; ++q)
+                  if (q == j) val = I0[q];
+                ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 50), val, inc, emit);
+              }
+              if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
+  #pragma unroll
+                for (int j = 0; j < SEG; ++j)
+                  if (j < ncell)
+                    ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 51),
+                                   I0[j], inc, emit);
+              }
+            }
+          }
+        }
+  #pragma unroll
+        for (int j = 0; j < SEG; ++j) {
+          if (j < ncell) {
+            int crd[3];
+            crd[cax[0]] = u0 + j;
+            crd[cax[1]] = v;
+            crd[cax[2]] = w;
+            const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+            Jout[RT_IDX(canon, cells, 52)] = Jacc[j];
+            if (MOM) {
+              T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
+              const long long qs = (long long)A.d.nf * cells;
+              const long long o = (long long)f * cells + canon;
+  #pragma unroll
+              for (int q = 0; q < 3; ++q) M[q * qs + o] = Hm[MOM ? j : 0][q];
+  #pragma unroll
+              for (int q = 0; q < 6; ++q) M[(3 + q) * qs + o] = Km[MOM ? j : 0][q];
+            }
           }
         }
       }
@@ -1352,9 +1508,17 @@ static cudaError_t launch_tiled_t(const SweepArgs<T> &A, int threads, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
+template <typename T>
+static bool pipe_vec_ok(const Dims &d) {
+  if (sizeof(T) != 4) return false;
+  // rows of every sweep axis (u = y for x sweeps, x otherwise) hold a multiple of 4 cells
+  return d.n[0] % 4 == 0 && d.n[1] % 4 == 0;
+}
+
 template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_pipe_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
-  auto kern = sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg>;
+  auto kern = pipe_vec_ok<T>(A.d) ? sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg, (sizeof(T) == 4)>
+                                  : sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (A.cluster > 8) {
@@ -1414,7 +1578,7 @@ cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int thre
 
 template <typename T, int AMAX>
 static int max_active_t(int tiled, int cluster, int threads, size_t smem) {
-  const void *kern = tiled == 3 ? (const void *)sc_sweep_pipe_kernel<T, AMAX, false, kSweepSeg>
+  const void *kern = tiled == 3 ? (const void *)sc_sweep_pipe_kernel<T, AMAX, false, kSweepSeg, false>
                     : (tiled ? (const void *)sc_sweep_tiled_kernel<T, AMAX, false, kSweepSeg>
                              : (const void *)sc_sweep_kernel<T, AMAX, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
