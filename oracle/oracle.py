@@ -14,6 +14,10 @@ Follows Davis, Stone & Jiang (2012):
     the change of J between consecutive formal solutions (Sec. 3.4).  The
     iteration count is the number of formal solutions performed.
   * ``heating_rate``     - Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu) (Sec. 4, Q^int).
+  * ``heating_rate_dif`` - Q^dif = -4 pi sum_nu w_nu div H_nu (Sec. 4), div H by
+    centred differences of the cell-centred H (one-sided at non-periodic faces).
+  * ``heating_rate_switch`` - per cell and frequency Q^int where chi dx <= 1,
+    else Q^dif (the switch of Sec. 4).
 
 Parity: pinned by tests/test_oracle_*.py.
 """
@@ -178,6 +182,62 @@ def heating_rate(chi, eps, J, B, freq_w):
     """Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)  (integral form, Sec. 4)."""
     fw = np.asarray(freq_w, dtype=np.float64).reshape((-1,) + (1,) * (np.ndim(J) - 1))
     return 4.0 * math.pi * np.sum(fw * eps * chi * (J - B), axis=0)
+
+
+def _derivative(F, axis, h, periodic):
+    """dF/dx along one array axis of cell-centred values: centred differences
+    (F[i+1] - F[i-1]) / 2h, wrapped on a periodic axis; at the first and last
+    cell of a non-periodic axis the one-sided difference; zero on an axis of one
+    cell."""
+    n = F.shape[axis]
+    if n == 1:
+        return np.zeros_like(F)
+    if periodic:
+        return (np.roll(F, -1, axis=axis) - np.roll(F, 1, axis=axis)) / (2.0 * h)
+    F = np.moveaxis(F, axis, 0)
+    out = np.empty_like(F)
+    out[1:-1] = (F[2:] - F[:-2]) / (2.0 * h)
+    out[0] = (F[1] - F[0]) / h
+    out[-1] = (F[-1] - F[-2]) / h
+    return np.moveaxis(out, 0, axis)
+
+
+def divergence(grid: Grid, H):
+    """div H per cell for H [..., 3, nz, ny, nx] (components x, y, z)."""
+    H = np.asarray(H, dtype=np.float64)
+    hx, hy, hz = grid.d
+    per = [grid.bc_lo[a] == PERIODIC for a in range(3)]
+    return (_derivative(H[..., 0, :, :, :], -1, hx, per[0])
+            + _derivative(H[..., 1, :, :, :], -2, hy, per[1])
+            + _derivative(H[..., 2, :, :, :], -3, hz, per[2]))
+
+
+def heating_rate_dif(grid: Grid, H, freq_w):
+    """Q^dif = -4 pi sum_nu w_nu div H_nu (differential form, Sec. 4)."""
+    divH = divergence(grid, np.asarray(H, dtype=np.float64).reshape((-1, 3) + grid.shape))
+    fw = np.asarray(freq_w, dtype=np.float64).reshape((-1, 1, 1, 1))
+    return -4.0 * math.pi * np.sum(fw * divH, axis=0)
+
+
+def cell_width(grid: Grid):
+    """Width of a cell in the heating-rate switch: the largest spacing along the
+    axes that have more than one cell."""
+    return max(grid.d[a] for a in range(3) if grid.n[a] > 1) if max(grid.n) > 1 else grid.d[0]
+
+
+def heating_rate_switch(grid: Grid, chi, eps, J, B, H, freq_w):
+    """Q per cell and frequency: the integral form where chi_nu dx <= 1, else the
+    differential form (Sec. 4), summed over frequency with the weights w_nu."""
+    chi = np.asarray(chi, dtype=np.float64).reshape((-1,) + grid.shape)
+    eps = np.asarray(eps, dtype=np.float64).reshape(chi.shape)
+    J = np.asarray(J, dtype=np.float64).reshape(chi.shape)
+    B = np.asarray(B, dtype=np.float64).reshape(chi.shape)
+    divH = divergence(grid, np.asarray(H, dtype=np.float64).reshape((-1, 3) + grid.shape))
+    q_int = eps * chi * (J - B)
+    q_dif = -divH
+    q = np.where(chi * cell_width(grid) <= 1.0, q_int, q_dif)
+    fw = np.asarray(freq_w, dtype=np.float64).reshape((-1, 1, 1, 1))
+    return 4.0 * math.pi * np.sum(fw * q, axis=0)
 
 
 def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_init=None,
