@@ -43,6 +43,10 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
+# sweep kernel of each planner variant (simple, tiled, pipelined)
+SWEEP_KERNEL_NAMES = {1: "sc_sweep_kernel<float>", 2: "sc_sweep_tiled_kernel<float>",
+                      3: "sc_sweep_pipe_kernel<float>"}
+
 def workload():
     from paper_1201_2222_gb300 import workloads as W
     return W.turbulent_box(N_BOX, n_mu=N_MU, tol=TOL)
@@ -133,7 +137,7 @@ class ClockSampler:
 
 # -------------------------------------------------------------- CPU baseline
 
-def oracle_rate(p, min_seconds=10.0, max_runs=3):
+def oracle_rate(p, min_seconds=10.0, max_runs=40):
     """The FP64 CPU oracle's formal-solution rate on this workload (all host cores)."""
     from oracle import oracle as O
     og = O.Grid.from_problem(p)
@@ -202,7 +206,11 @@ def run_gpu(args):
     fw = torch.from_numpy(p.freq_w).to(dev)
     g = rt.Grid.from_problem(p, prec=rt.MIXED)
     g.set_opacity_source(chi, eps, B, fw)
-    tuned = g.autotune()          # set-up: pick the sweep launch plan once per problem shape
+    if args.plan:                 # a given sweep plan (e.g. to list one run's launches)
+        v, apg, c = (int(x) for x in args.plan.split(","))
+        g.set_sweep_config(apg, c, 0, v)
+    else:                         # set-up: pick the sweep launch plan once per problem shape
+        g.autotune()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -311,7 +319,7 @@ def run_gpu(args):
         "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
         "fp64_path": fp64,
         "sweep_plan": g.sweep_plan(),
-        "roofline": {"bound": "alu", "kernel": "sc_sweep_tiled_kernel<float>" if g.sweep_plan()["variant"] == 2 else "sc_sweep_kernel<float>",
+        "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[g.sweep_plan()["variant"]],
                      "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
@@ -362,7 +370,7 @@ def main(argv=None):
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
-    ap.add_argument("--plan", default="", help="with --profile: variant,rays_per_group,cluster")
+    ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster instead of autotuning")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

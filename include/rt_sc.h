@@ -144,12 +144,28 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
 
 /* Outputs of the last formal solution of the latest solve (Sec. 4): J [nf][cells],
  * H [nf][3][cells], K [nf][6][cells] (xx, yy, zz, xy, xz, yz), the variable
- * Eddington tensor f = K/J [nf][6][cells], and the heating rate
- * Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu) [cells].  Any pointer may be NULL.
+ * Eddington tensor f = K/J [nf][6][cells], and the heating rate Q [cells] in the
+ * form chosen by rt_set_heating_form (default: the integral form
+ * Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)).  Any pointer may be NULL.
  * Recomputes that formal solution with moment accumulation.
  * Errors: RT_ERR_STATE if no formal solution has run. */
 rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, double *Q,
                      int on_device, const rt_solve_opts *opts);
+
+/* Form of the heating rate Q returned by rt_moments (Sec. 4).
+ *   RT_HEAT_INTEGRAL:     Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu), chi_abs = eps chi.
+ *   RT_HEAT_DIFFERENTIAL: Q = -4 pi sum_nu w_nu div H_nu, div H from centred
+ *                         differences of the cell-centred H (wrapped on periodic
+ *                         axes, one-sided at the first and last cell of a bounded
+ *                         axis, zero along an axis of one cell).
+ *   RT_HEAT_SWITCH:       per cell and frequency, the integral form where
+ *                         chi_nu dx <= 1 and the differential form elsewhere, dx
+ *                         the largest cell spacing along axes of more than one cell
+ *                         (the paper's switch; the integral form loses accuracy in
+ *                         optically thick cells, where J ~ B).
+ * Errors: RT_ERR_ARG for another value. */
+typedef enum { RT_HEAT_INTEGRAL = 0, RT_HEAT_DIFFERENTIAL = 1, RT_HEAT_SWITCH = 2 } rt_heating_form;
+rt_status rt_set_heating_form(rt_grid g, int form);
 
 /* Current source function S [nf][nz][ny][nx]. */
 rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts);
@@ -174,10 +190,13 @@ rt_status rt_get_stats(rt_grid g, rt_stats *out);
 
 /* Tuning of the formal-solution launch (0 = automatic for each): rays per sweep
  * group (1..8), CTAs per thread-block cluster = strips per plane (1..16),
- * threads per CTA (multiple of 32, <= 512) and the kernel variant (1 = one cell
- * per thread with direct loads, 2 = shared-memory staged planes with four cells
- * per thread).  Automatic choice: variant 2 for RT_PREC_MIXED, 1 for FP64; rays
- * per group and strips from the runtime's count of co-resident clusters.
+ * threads per CTA (multiple of 32, <= 512; FP64 grids use at most 256 for
+ * variants 2 and 3) and the kernel variant (1 = one cell per thread with direct
+ * loads, 2 = shared-memory staged planes with four cells per thread,
+ * 3 = pipelined: chi and S staged one plane ahead by asynchronous copies, strip
+ * edges exchanged through distributed shared memory).  Automatic choice:
+ * variant 3 for RT_PREC_MIXED, 1 for FP64; rays per group and strips from the
+ * runtime's count of co-resident clusters (rt_autotune measures instead).
  * Results do not depend on the configuration beyond rounding order.
  * Errors: RT_ERR_ARG for out-of-range values or no feasible configuration. */
 rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas, int threads,

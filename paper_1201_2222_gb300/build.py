@@ -53,7 +53,10 @@ def build(debug: bool = False, force: bool = False, verbose: bool = False) -> st
     nvcc = _nvcc()
     bdir = os.path.join(HERE, "_build", "debug" if debug else "release")
     os.makedirs(bdir, exist_ok=True)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # -ftz=true: float32 subnormals flush to zero, so the sweep's fast exp and
+    # reciprocal are single special-function instructions (FP64 is unaffected)
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+                     "-I", CSRC]
     if debug:
         common.append("-DRT_DEBUG_BOUNDS")
     procs = []

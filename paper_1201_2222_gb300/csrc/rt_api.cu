@@ -260,7 +260,7 @@ struct rt_grid_s {
   // device buffers
   double *chi = nullptr, *eps = nullptr, *B = nullptr, *fw = nullptr;
   double *S = nullptr, *Sfs = nullptr, *J = nullptr, *Jprev = nullptr;
-  double *lstar = nullptr, *oml = nullptr;
+  double *lstar = nullptr, *oml = nullptr, *iden = nullptr;
   void *chiP[3] = {nullptr, nullptr, nullptr};
   void *SP[3] = {nullptr, nullptr, nullptr};
   void *G[2] = {nullptr, nullptr};
@@ -301,6 +301,7 @@ struct rt_grid_s {
   double *tmp2 = nullptr;
   size_t tmp2_n = 0;
   double prec_limit = 1e-4;
+  int heat_form = RT_HEAT_INTEGRAL;   // form of Q returned by rt_moments (Sec. 4)
 };
 
 namespace {
@@ -352,6 +353,12 @@ constexpr int kSMs = 152;
 
 int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)); }
 
+// Largest CTA of a sweep variant in the grid's precision.
+int sweep_thread_cap(rt_grid g, int variant) {
+  if (variant == 1) return 512;
+  return g->desc.prec == RT_PREC_FP64 ? rtk::sweep_max_threads<double>() : rtk::sweep_max_threads<float>();
+}
+
 // Shared memory and threads of one sweep CTA for `slots` rays and C strips.
 void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *threads) {
   size_t sm = 0;
@@ -376,7 +383,7 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
     }
   }
   *smem = sm;
-  *threads = std::max(32, std::min(512, ((th + 31) / 32) * 32));
+  *threads = std::max(32, std::min(sweep_thread_cap(g, variant), ((th + 31) / 32) * 32));
 }
 
 // Split each (crossed axis, direction) class of rays into chunks of <= apg.
@@ -390,8 +397,17 @@ void make_groups(rt_grid g, int apg, std::vector<GroupParam> &groups, std::vecto
   gang.clear();
   *namax = 0;
   for (int key = 0; key < 6; ++key) {
-    const auto &v = per_key[key];
+    auto &v = per_key[key];
     if (v.empty()) continue;
+    // order by the signs of mu along the plane axes, so that each group holds
+    // runs of rays sharing one interpolation stencil
+    int cax[3];
+    rtk::plane_axes(key / 2, cax);
+    auto skey = [&](int k) {
+      const RayGeom &r = g->rays[k];
+      return (r.sgn[cax[0]] > 0 ? 1 : 0) + (r.sgn[cax[1]] > 0 ? 2 : 0);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return skey(x) < skey(y); });
     const int nchunk = ((int)v.size() + apg - 1) / apg;
     size_t pos = 0;
     for (int c = 0; c < nchunk; ++c) {
@@ -402,6 +418,11 @@ void make_groups(rt_grid g, int apg, std::vector<GroupParam> &groups, std::vecto
       gp.a0 = (int)gang.size();
       gp.na = sz;
       for (int q = 0; q < sz; ++q) gang.push_back(v[pos + q]);
+      for (int k = 0; k <= 4; ++k) {   // first ray with stencil key >= k
+        int q = 0;
+        while (q < sz && skey(v[pos + q]) < k) ++q;
+        gp.kb[k] = q;
+      }
       pos += sz;
       groups.push_back(gp);
       *namax = std::max(*namax, sz);
@@ -428,7 +449,7 @@ void plan_groups(rt_grid g) {
     minNv = std::min(minNv, g->d.n[cax[1]]);
   }
   int variant = g->req_variant;
-  if (variant == 0) variant = g->desc.prec == RT_PREC_FP64 ? 1 : 2;
+  if (variant == 0) variant = g->desc.prec == RT_PREC_FP64 ? 1 : 3;
   const int Cmax = std::min(16, minNv);
   double best = 1e300;
   int bapg = 1, bC = 1;
@@ -444,7 +465,7 @@ void plan_groups(rt_grid g) {
       size_t smem;
       int threads;
       sweep_shape(g, variant, namax, C, &smem, &threads);
-      if (g->req_threads > 0) threads = g->req_threads;
+      if (g->req_threads > 0) threads = std::min(g->req_threads, sweep_thread_cap(g, variant));
       if (smem > kSweepSmemBudget) continue;
       int raw_threads = 0;
       for (int a = 0; a < 3; ++a) {
@@ -490,7 +511,7 @@ void plan_groups(rt_grid g) {
   g->amax = amax_for(namax);
   g->cluster = bC;
   sweep_shape(g, variant, namax, bC, &g->smem, &g->threads);
-  if (g->req_threads > 0) g->threads = g->req_threads;
+  if (g->req_threads > 0) g->threads = std::min(g->req_threads, sweep_thread_cap(g, variant));
 }
 
 template <typename T>
@@ -711,7 +732,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   L.Jpart = (const T *)g->Jpart;
   L.eps = g->eps;
   L.B = g->B;
-  L.oml = g->oml;
+  L.iden = g->iden;
   L.S64 = g->S;
   L.Sfs = g->Sfs;
   L.J64 = g->J;
@@ -974,6 +995,7 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
   ALLOC(g->Jprev, N * 8);
   ALLOC(g->lstar, N * 8);
   ALLOC(g->oml, N * 8);
+  ALLOC(g->iden, N * 8);
   for (int a = 0; a < 3; ++a) {
     if (!g->used_axis[a]) continue;
     ALLOC(g->chiP[a], N * ts);
@@ -1015,7 +1037,7 @@ rt_status rt_destroy_grid(rt_grid g) {
   if (g->fmask) cudaFree(g->fmask);
   if (g->epsmin) cudaFree(g->epsmin);
   if (g->tmp2) cudaFree(g->tmp2);
-  void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml,
+  void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml, g->iden,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
                   g->Gd[0], g->Gd[1],
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
@@ -1097,7 +1119,8 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
   } else {
     CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
   }
-  g->launches++;
+  CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
+  g->launches += 2;
   CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
   if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
   if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
@@ -1271,7 +1294,8 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
     if ((r = move_bins(g->bins64, sK, dK, 6 * C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
     if ((r = move_bins(g->bins64, sF, dF, 6 * C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
   }
-  CU(rtk::launch_heating(g->d, g->fw, g->chi, g->eps, dJ, g->B, dQ, s));
+  const double h[3] = {g->desc.dx, g->desc.dy, g->desc.dz};
+  CU(rtk::launch_heating(g->d, g->fw, g->chi, g->eps, dJ, g->B, dH, h, g->heat_form, dQ, s));
   g->launches += 2;   // moment reduction + heating rate
   if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
   g->sp_is_delta = false;   // the sweep copies hold the full S again
@@ -1291,6 +1315,14 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
   rt_status r = copy_out(S, g->S, (size_t)N_of(g), on_device, s);
   if (r != RT_OK) return r;
   CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_set_heating_form(rt_grid g, int form) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (form != RT_HEAT_INTEGRAL && form != RT_HEAT_DIFFERENTIAL && form != RT_HEAT_SWITCH)
+    return fail(RT_ERR_ARG, "unknown heating form %d", form);
+  g->heat_form = form;
   return RT_OK;
 }
 
@@ -1347,15 +1379,15 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
       minNv = std::min(minNv, g->d.n[cax[1]]);
     }
     const int variants[3] = {3, 2, 1};
-    const int apgs[5] = {2, 4, 6, 7, 8};
-    const int clusters[5] = {1, 2, 4, 8, 16};
+    const int apgs[7] = {2, 3, 4, 5, 6, 7, 8};
+    const int clusters[9] = {1, 2, 4, 6, 8, 9, 10, 12, 16};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best_ms = 1e300;
     for (int vi = 0; vi < 3; ++vi) {
-      for (int ai = 0; ai < 5; ++ai) {
-        for (int ci = 0; ci < 5; ++ci) {
+      for (int ai = 0; ai < 7; ++ai) {
+        for (int ci = 0; ci < 9; ++ci) {
           if (clusters[ci] > minNv) continue;
           g->req_variant = variants[vi];
           g->req_apg = apgs[ai];

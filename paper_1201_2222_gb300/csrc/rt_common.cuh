@@ -23,21 +23,25 @@ constexpr int kMaxGroups = 512;
 
 // Per-ray constants in the plane coordinates of its group.
 template <typename T>
-struct AngleParam {
-  T wq;             // quadrature weight w_k
-  T hs;             // half the path length to the upwind face, s/2
+struct alignas(4 * sizeof(T)) AngleParam {
   T wa, wb, wc, wd; // face weights of vertices (u,v), (u-su,v), (u,v-sv), (u-su,v-sv)
+  T hs;             // half the path length to the upwind face, s/2
+  T wq;             // quadrature weight w_k
   T mu[3];          // direction cosines (x, y, z) for H and K
   int su, sv;       // sign of mu along u and v
   int angle;        // index in the full angle table
-  int pad;
 };
+
+static_assert(sizeof(AngleParam<float>) == 48, "AngleParam<float> is read as three float4");
 
 struct GroupParam {
   int axis;   // sweep axis a
   int sa;     // sign of mu_a: +1 sweeps w ascending
   int a0;     // first AngleParam of the group
   int na;     // rays in the group
+  // the group's rays are ordered by key = (mu_u > 0) + 2 (mu_v > 0); rays
+  // kb[k] .. kb[k+1]-1 (relative to a0) have key k
+  int kb[5];
 };
 
 // Canonical per-ray geometry (used by the Lambda* kernel).
@@ -58,6 +62,11 @@ struct Dims {
   long long gsize;   // ghost block per (frequency, ray): nx*ny + ny*nz + nx*nz
   long long face[3]; // face cells per canonical axis: x: nz*ny, y: nz*nx, z: ny*nx
 };
+
+// Stride of canonical axis a in a [nz][ny][nx] array.
+__host__ __device__ inline long long canon_stride(const int n[3], int a) {
+  return a == 0 ? 1LL : (a == 1 ? (long long)n[0] : (long long)n[0] * n[1]);
+}
 
 // Roles of the canonical axes for a sweep along axis a.
 __host__ __device__ inline void plane_axes(int a, int cax[3]) {

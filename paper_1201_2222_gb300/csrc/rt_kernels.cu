@@ -11,6 +11,7 @@
 // hardware cluster barrier inside one cluster, which every CTA of the cluster
 // reaches the same number of times.
 #include <cooperative_groups.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -72,51 +73,64 @@ __device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0
 
 // ------------------------------------------------------------------------ sweep
 
-template <typename T>
-__device__ __forceinline__ long long face_cell(const Dims &d, int ax, const int m[3]) {
-  return ax == 0 ? (long long)m[2] * d.n[1] + m[1]
-                 : (ax == 1 ? (long long)m[2] * d.n[0] + m[0] : (long long)m[1] * d.n[0] + m[0]);
-}
 
-// Intensity at an upwind vertex outside the domain (plane coordinates u, v, w).
-// If any out-of-range axis is non-periodic, the inflow intensity of the first such
-// face in the order z, y, x; otherwise the image cell's intensity from the previous
-// formal solution (lagged periodic ghost), read from the face buffer of the first
-// out-of-range axis in the same order.
+// Canonical axis a's entry of a 3-vector, by selects (a runtime index into a
+// register array would put the array in local memory).
+__device__ __forceinline__ int pick3(const int (&x)[3], int a) { return a == 0 ? x[0] : (a == 1 ? x[1] : x[2]); }
+__device__ __forceinline__ int pick3(int x0, int x1, int x2, int a) { return a == 0 ? x0 : (a == 1 ? x1 : x2); }
+
+// Address of the intensity at an upwind vertex outside the domain (plane
+// coordinates u, v, w), or nullptr when it is zero (fixed inflow in an
+// incremental sweep, whose inflow does not change between formal solutions).
+// If any out-of-range axis is non-periodic: the inflow intensity of the first
+// such face in the order z, y, x.  Otherwise the image cell's intensity from the
+// previous formal solution (lagged periodic ghost), read from the face buffer of
+// the first out-of-range axis in the same order.
 template <typename T>
-__device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
-                                     int Nw, int f, int angle, const T *Gp, bool inc, int u, int v,
-                                     int w) {
-  int crd[3];
-  crd[cax[0]] = u;
-  crd[cax[1]] = v;
-  crd[cax[2]] = w;
-  int m[3], oor[3], side[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int n = A.d.n[ax];
-    const int c = crd[ax];
-    oor[ax] = (c < 0) || (c >= n);
-    side[ax] = c >= n;
-    m[ax] = !oor[ax] ? c : (A.d.periodic[ax] ? (c < 0 ? c + n : c - n) : (c < 0 ? 0 : n - 1));
+__device__ __forceinline__ const T *ghost_ptr(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
+                                              int Nw, int f, int angle, const T *Gp, bool inc, int u,
+                                              int v, int w) {
+  // canonical coordinates, picked from the plane coordinates by selects
+  const int c0 = cax[0] == 0 ? u : (cax[1] == 0 ? v : w);
+  const int c1 = cax[0] == 1 ? u : (cax[1] == 1 ? v : w);
+  const int c2 = cax[0] == 2 ? u : (cax[1] == 2 ? v : w);
+  const int n0 = A.d.n[0], n1 = A.d.n[1], n2 = A.d.n[2];
+  const bool p0 = A.d.periodic[0], p1 = A.d.periodic[1], p2 = A.d.periodic[2];
+  const bool o0 = c0 < 0 || c0 >= n0, o1 = c1 < 0 || c1 >= n1, o2 = c2 < 0 || c2 >= n2;
+  const int m0 = !o0 ? c0 : (p0 ? (c0 < 0 ? c0 + n0 : c0 - n0) : (c0 < 0 ? 0 : n0 - 1));
+  const int m1 = !o1 ? c1 : (p1 ? (c1 < 0 ? c1 + n1 : c1 - n1) : (c1 < 0 ? 0 : n1 - 1));
+  const int m2 = !o2 ? c2 : (p2 ? (c2 < 0 ? c2 + n2 : c2 - n2) : (c2 < 0 ? 0 : n2 - 1));
+  int fax = -1, fside = 0;   // first non-periodic out-of-range axis in the order z, y, x
+  if (o0 && !p0) { fax = 0; fside = c0 >= n0; }
+  if (o1 && !p1) { fax = 1; fside = c1 >= n1; }
+  if (o2 && !p2) { fax = 2; fside = c2 >= n2; }
+  if (fax >= 0) {
+    if (inc) return nullptr;
+    // face cell index: x face [z][y], y face [z][x], z face [y][x]
+    const long long fc = fax == 0 ? (long long)m2 * n1 + m1
+                                  : (fax == 1 ? (long long)m2 * n0 + m0 : (long long)m1 * n0 + m0);
+    const long long fsz = fax == 0 ? A.d.face[0] : (fax == 1 ? A.d.face[1] : A.d.face[2]);
+    const long long idx = ((long long)f * A.na + angle) * fsz + fc;
+    const T *base = fax == 0 ? A.Ibc[fside] : (fax == 1 ? A.Ibc[2 + fside] : A.Ibc[4 + fside]);
+    return base + RT_IDX(idx, (long long)A.d.nf * A.na * fsz, 41);
   }
-#pragma unroll
-  for (int ax = 2; ax >= 0; --ax) {
-    if (oor[ax] && !A.d.periodic[ax]) {
-      if (inc) return T(0);   // fixed inflow does not change between formal solutions
-      const int face = 2 * ax + side[ax];
-      const long long idx = ((long long)f * A.na + angle) * A.d.face[ax] + face_cell<T>(A.d, ax, m);
-      return A.Ibc[face][RT_IDX(idx, (long long)A.d.nf * A.na * A.d.face[ax], 11)];
-    }
-  }
+  const int ax = o2 ? 2 : (o1 ? 1 : 0);
+  const int mu_ = pick3(m0, m1, m2, cax[0]), mv_ = pick3(m0, m1, m2, cax[1]), mw_ = pick3(m0, m1, m2, cax[2]);
   const long long gb = ((long long)f * A.na + angle) * A.d.gsize;
-  const int ax = oor[2] ? 2 : (oor[1] ? 1 : 0);
-  const int mu_ = m[cax[0]], mv_ = m[cax[1]], mw_ = m[cax[2]];
   long long off;
   if (ax == cax[2]) off = (long long)mv_ * Nu + mu_;
   else if (ax == cax[0]) off = (long long)Nu * Nv + (long long)mw_ * Nv + mv_;
   else off = (long long)Nu * Nv + (long long)Nw * Nv + (long long)mw_ * Nu + mu_;
-  return Gp[RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 12)];
+  return Gp + RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 42);
+}
+
+// Value of the intensity at an out-of-domain upwind vertex (see ghost_ptr).
+template <typename T>
+__device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
+                                     int Nw, int f, int angle, const T *Gp, bool inc, int u, int v,
+                                     int w) {
+  const T *q = ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, angle, Gp, inc, u, v, w);
+  return q ? *q : T(0);
 }
 
 // Outflow intensity onto a periodic face for the next formal solution.  Full
@@ -159,8 +173,11 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   }
   int cax[3];
   plane_axes(gp.axis, cax);
-  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
-  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int Nu = pick3(A.d.n, cax[0]), Nv = pick3(A.d.n, cax[1]), Nw = pick3(A.d.n, cax[2]);
+  const int perU = pick3(A.d.periodic, cax[0]), perV = pick3(A.d.periodic, cax[1]),
+            perW = pick3(A.d.periodic, cax[2]);
+  const long long csu = canon_stride(A.d.n, cax[0]), csv = canon_stride(A.d.n, cax[1]),
+                  csw = canon_stride(A.d.n, cax[2]);   // canonical strides of u, v, w
   const int v0 = (int)(((long long)rank * Nv) / C);
   const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
   const int R = v1 - v0;
@@ -211,11 +228,7 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
       const long long pidx = ((long long)w * Nv + v) * Nu + u;
       const T chi0 = chiP[RT_IDX(pidx, cells, 1)];
       const T S0 = SP[RT_IDX(pidx, cells, 2)];
-      int crd[3];
-      crd[cax[0]] = u;
-      crd[cax[1]] = v;
-      crd[cax[2]] = w;
-      const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+      const long long canon = (long long)(u) * csu + (long long)v * csv + (long long)w * csw;
       T Jacc = T(0);
       T Hm[3] = {T(0), T(0), T(0)};
       T Km[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -363,7 +376,7 @@ __device__ __forceinline__ void seg_update(const AngleParam<T> &p, const T *__re
 }
 
 template <typename T, int AMAX, bool MOM, int SEG>
-__global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_tiled_kernel(const SweepArgs<T> A) {
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;
   const int rank = blockIdx.x % C;
@@ -377,8 +390,11 @@ __global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> 
   }
   int cax[3];
   plane_axes(gp.axis, cax);
-  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
-  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int Nu = pick3(A.d.n, cax[0]), Nv = pick3(A.d.n, cax[1]), Nw = pick3(A.d.n, cax[2]);
+  const int perU = pick3(A.d.periodic, cax[0]), perV = pick3(A.d.periodic, cax[1]),
+            perW = pick3(A.d.periodic, cax[2]);
+  const long long csu = canon_stride(A.d.n, cax[0]), csv = canon_stride(A.d.n, cax[1]),
+                  csw = canon_stride(A.d.n, cax[2]);   // canonical strides of u, v, w
   const int v0 = (int)(((long long)rank * Nv) / C);
   const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
   const int R = v1 - v0;
@@ -555,11 +571,7 @@ __global__ void __launch_bounds__(512) sc_sweep_tiled_kernel(const SweepArgs<T> 
 #pragma unroll
       for (int j = 0; j < SEG; ++j) {
         if (j < ncell) {
-          int crd[3];
-          crd[cax[0]] = u0 + j;
-          crd[cax[1]] = v;
-          crd[cax[2]] = w;
-          const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+          const long long canon = (long long)(u0 + j) * csu + (long long)v * csv + (long long)w * csw;
           Jout[RT_IDX(canon, cells, 29)] = Jacc[j];
           if (MOM) {
             T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
@@ -609,44 +621,6 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
   else cp_async8(dst, src);
 }
 
-// Address of the intensity at an out-of-domain upwind vertex (see ghost_I), or
-// nullptr when it is zero (vacuum inflow, or fixed inflow in an incremental sweep).
-template <typename T>
-__device__ __forceinline__ const T *ghost_ptr(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
-                                              int Nw, int f, int angle, const T *Gp, bool inc, int u,
-                                              int v, int w) {
-  int crd[3];
-  crd[cax[0]] = u;
-  crd[cax[1]] = v;
-  crd[cax[2]] = w;
-  int m[3], oor[3], side[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int n = A.d.n[ax];
-    const int c = crd[ax];
-    oor[ax] = (c < 0) || (c >= n);
-    side[ax] = c >= n;
-    m[ax] = !oor[ax] ? c : (A.d.periodic[ax] ? (c < 0 ? c + n : c - n) : (c < 0 ? 0 : n - 1));
-  }
-#pragma unroll
-  for (int ax = 2; ax >= 0; --ax) {
-    if (oor[ax] && !A.d.periodic[ax]) {
-      if (inc) return nullptr;
-      const int face = 2 * ax + side[ax];
-      const long long idx = ((long long)f * A.na + angle) * A.d.face[ax] + face_cell<T>(A.d, ax, m);
-      return A.Ibc[face] + RT_IDX(idx, (long long)A.d.nf * A.na * A.d.face[ax], 41);
-    }
-  }
-  const long long gb = ((long long)f * A.na + angle) * A.d.gsize;
-  const int ax = oor[2] ? 2 : (oor[1] ? 1 : 0);
-  const int mu_ = m[cax[0]], mv_ = m[cax[1]], mw_ = m[cax[2]];
-  long long off;
-  if (ax == cax[2]) off = (long long)mv_ * Nu + mu_;
-  else if (ax == cax[0]) off = (long long)Nu * Nv + (long long)mw_ * Nv + mv_;
-  else off = (long long)Nu * Nv + (long long)Nw * Nv + (long long)mw_ * Nu + mu_;
-  return Gp + RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 42);
-}
-
 template <typename T>
 __device__ __forceinline__ void ghost_async(T *dst, const T *src) {
   if (src) cp_async_elem(dst, src);
@@ -654,6 +628,10 @@ __device__ __forceinline__ void ghost_async(T *dst, const T *src) {
 }
 
 constexpr int kPipeX0 = 4;   // first interior column of a staged row (16-byte aligned)
+
+// A compile-time sign of mu_u or mu_v (selects the interpolation stencil).
+template <int V>
+using SignC = std::integral_constant<int, V>;
 
 template <typename T, int SEG, int SU, int SV>
 __device__ __forceinline__ void pipe_update(const AngleParam<T> &p, const T *__restrict__ Irow,
@@ -724,7 +702,7 @@ __device__ __forceinline__ void vec_update(const AngleParam<float> &p, const flo
 }
 
 template <typename T, int AMAX, bool MOM, int SEG, bool VEC>
-__global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;
   const int rank = blockIdx.x % C;
@@ -738,8 +716,11 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
   }
   int cax[3];
   plane_axes(gp.axis, cax);
-  const int Nu = A.d.n[cax[0]], Nv = A.d.n[cax[1]], Nw = A.d.n[cax[2]];
-  const int perU = A.d.periodic[cax[0]], perV = A.d.periodic[cax[1]], perW = A.d.periodic[cax[2]];
+  const int Nu = pick3(A.d.n, cax[0]), Nv = pick3(A.d.n, cax[1]), Nw = pick3(A.d.n, cax[2]);
+  const int perU = pick3(A.d.periodic, cax[0]), perV = pick3(A.d.periodic, cax[1]),
+            perW = pick3(A.d.periodic, cax[2]);
+  const long long csu = canon_stride(A.d.n, cax[0]), csv = canon_stride(A.d.n, cax[1]),
+                  csw = canon_stride(A.d.n, cax[2]);   // canonical strides of u, v, w
   const int v0 = (int)(((long long)rank * Nv) / C);
   const int v1 = (int)(((long long)(rank + 1) * Nv) / C);
   const int R = v1 - v0;
@@ -779,6 +760,17 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
   const bool top_edge = v0 == 0 && !perV;      // no strip and no periodic image below
   const bool bot_edge = v1 == Nv && !perV;
   cg::cluster_group cluster = cg::this_cluster();
+  // intensity buffers of the strips above and below in the cluster (DSMEM); every
+  // upwind read below is then a local shared-memory load
+  T *Ntop0 = nullptr, *Nbot0 = nullptr;
+  int top_row = 0;   // this strip's first row as the top neighbour's bottom halo row
+  if (C > 1) {
+    if (rank > 0) {
+      Ntop0 = cluster.map_shared_rank(Ib, rank - 1);
+      top_row = v0 - (int)(((long long)(rank - 1) * Nv) / C) + 1;
+    }
+    if (rank < C - 1) Nbot0 = cluster.map_shared_rank(Ib, rank + 1);
+  }
   __syncthreads();
 
   // chi and S of plane wsrc (rows v0-1 .. v1, columns -1 .. Nu, wrapped or clamped) -> ring slot
@@ -846,6 +838,42 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
     }
   };
 
+  // Outflow intensities of plane wp onto the periodic faces, for the next formal
+  // solution (Sec. 3.5): the u face (one column per row), the v face (one row, in
+  // the strip that holds it) and, at the last plane, the w face (the whole strip).
+  auto ghost_pass = [&](const T *Ibuf, int wp) {
+    if (!A.write_ghosts) return;
+    const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+    if (perU) {
+      for (int idx = threadIdx.x; idx < na * R; idx += blockDim.x) {
+        const int a = idx / R, lv = idx - a * R;
+        const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
+        const int col = P[a].su > 0 ? Nu - 1 : 0;
+        ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)wp * Nv + v0 + lv, gn, 54),
+                       Ibuf[RT_IDX(a * pb + (lv + 1) * W + kPipeX0 + col, 2LL * ib, 58)], inc, emit);
+      }
+    }
+    if (perV) {
+      for (int idx = threadIdx.x; idx < na * Nu; idx += blockDim.x) {
+        const int a = idx / Nu, u = idx - a * Nu;
+        const int vr = P[a].sv > 0 ? Nv - 1 : 0;
+        if (vr < v0 || vr >= v1) continue;
+        const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
+        ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)wp * Nu + u, gn, 55),
+                       Ibuf[RT_IDX(a * pb + (vr - v0 + 1) * W + kPipeX0 + u, 2LL * ib, 59)], inc, emit);
+      }
+    }
+    if (perW && wp == wlast) {
+      for (int idx = threadIdx.x; idx < na * R * Nu; idx += blockDim.x) {
+        const int a = idx / (R * Nu), r2 = idx - a * R * Nu;
+        const int lv = r2 / Nu, u = r2 - lv * Nu;
+        const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
+        ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)(v0 + lv) * Nu + u, gn, 53),
+                       Ibuf[RT_IDX(a * pb + (lv + 1) * W + kPipeX0 + u, 2LL * ib, 60)], inc, emit);
+      }
+    }
+  };
+
   // prologue: the first plane, the upwind ghost plane, and its intensities
   const int w0 = sa > 0 ? 0 : Nw - 1;
   stage(w0, 0);
@@ -866,24 +894,17 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
     if (t + 1 < Nw) stage(w + sa, (t + 1) % 3);
     ghost_halo(Icur, w, false);
     cp_async_commit();
-    // neighbouring strips' rows of the upwind plane
-    const T *Itop = nullptr, *Ibot = nullptr;   // rows v0-1 and v1 at column X0
-    if (C > 1 && t > 0) {
-      if (rank > 0) {
-        const int rv0 = (int)(((long long)(rank - 1) * Nv) / C);
-        Itop = cluster.map_shared_rank(const_cast<T *>(Iprv), rank - 1) + (v0 - 1 - rv0 + 1) * W + kPipeX0;
-      }
-      if (rank < C - 1) {
-        Ibot = cluster.map_shared_rank(const_cast<T *>(Iprv), rank + 1) + 1 * W + kPipeX0;
-      }
-    }
-    const bool at_wlast = perW && (w == wlast);
+    // this plane's buffers of the neighbouring strips: the first and last rows of
+    // the strip are also stored into their halo rows (read there as the upwind
+    // plane of the next step, after the cluster barrier)
+    T *Ntop = Ntop0 ? Ntop0 + (t & 1) * ib + top_row * W + kPipeX0 : nullptr;
+    T *Nbot = Nbot0 ? Nbot0 + (t & 1) * ib + kPipeX0 : nullptr;
     if constexpr (VEC) {
       // float32 rows whose length is a multiple of 4: one segment per lane, a
       // warp-uniform trip count so every shuffle has the whole warp
       const int ntask = R * nseg;
       const int lane = threadIdx.x & 31;
-      const int ustride = cax[0] == 0 ? 1 : A.d.n[0];   // canonical stride along u
+      const long long ustride = csu;
       for (int base = threadIdx.x - lane; base < ntask; base += blockDim.x) {
         const int sidx = base + lane;
         const bool active = sidx < ntask;
@@ -916,68 +937,59 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
             for (int q = 0; q < 6; ++q) Km[j][q] = 0.f;
           }
         }
-        const bool seg_u_first = u0 == 0, seg_u_last = u0 + 4 >= Nu;
+        // one ray of the group; the signs of mu_u, mu_v are compile-time, so a block
+        // of rays with the same signs is straight-line code
+        auto ray = [&](auto su_c, auto sv_c, int a) {
+          constexpr int SU = decltype(su_c)::value, SV = decltype(sv_c)::value;
+          // the ray's constants in three 128-bit shared loads
+          AngleParam<float> p;
+          {
+            const float4 *pv = reinterpret_cast<const float4 *>(&P[a]);
+            const float4 x0 = pv[0], x1 = pv[1], x2 = pv[2];
+            p.wa = x0.x; p.wb = x0.y; p.wc = x0.z; p.wd = x0.w;
+            p.hs = x1.x; p.wq = x1.y; p.mu[0] = x1.z; p.mu[1] = x1.w;
+            p.mu[2] = x2.x;
+          }
+          const float *Ia = reinterpret_cast<const float *>(Iprv) + a * pb + row * W + kPipeX0 + u0;
+          const float *Iv = SV > 0 ? Ia - W : Ia + W;   // halo rows hold the neighbours' rows
+          float Ir[6], Iw[6], I0[4];
+          vec_row(Ia, haveL, haveR, Ir);
+          vec_row(Iv, haveL, haveR, Iw);
+          vec_update<SU, SV>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          if (active) {
+            const float4 o4 = make_float4(I0[0], I0[1], I0[2], I0[3]);
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Icur) + a * pb + row * W + kPipeX0 + u0) = o4;
+            if (lv == 0 && Ntop) *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Ntop) + a * pb + u0) = o4;
+            if (lv == R - 1 && Nbot) *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Nbot) + a * pb + u0) = o4;
+          }
 #pragma unroll
-        for (int a = 0; a < AMAX; ++a) {
-          if (a < na) {
-            const AngleParam<float> &p = reinterpret_cast<const AngleParam<float> &>(P[a]);
-            const float *Ia = reinterpret_cast<const float *>(Iprv) + a * pb + row * W + kPipeX0 + u0;
-            const float *Iv;
-            if (p.sv > 0) Iv = (lv == 0 && Itop) ? reinterpret_cast<const float *>(Itop) + a * pb + u0 : Ia - W;
-            else Iv = (lv == R - 1 && Ibot) ? reinterpret_cast<const float *>(Ibot) + a * pb + u0 : Ia + W;
-            float Ir[6], Iw[6], I0[4];
-            vec_row(Ia, haveL, haveR, Ir);
-            vec_row(Iv, haveL, haveR, Iw);
-            const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
-            if (key == 3) vec_update<1, 1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else if (key == 2) vec_update<-1, 1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else if (key == 1) vec_update<1, -1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else vec_update<-1, -1>(p, Ir, Iw, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            if (active)
-              *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Icur) + a * pb + row * W + kPipeX0 + u0) =
-                  make_float4(I0[0], I0[1], I0[2], I0[3]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float wI = p.wq * I0[j];
-              Jacc[j] += wI;
-              if (MOM) {
-                Hm[MOM ? j : 0][0] += wI * p.mu[0];
-                Hm[MOM ? j : 0][1] += wI * p.mu[1];
-                Hm[MOM ? j : 0][2] += wI * p.mu[2];
-                Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
-                Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
-                Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
-                Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
-                Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
-                Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
-              }
-            }
-            if (A.write_ghosts && active) {
-              const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
-              const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
-              if (at_wlast) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 53), (T)I0[j], inc, emit);
-              }
-              if (perU && (p.su > 0 ? seg_u_last : seg_u_first))
-                ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 54),
-                               (T)(p.su > 0 ? I0[3] : I0[0]), inc, emit);
-              if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                  ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 55),
-                                 (T)I0[j], inc, emit);
-              }
+          for (int j = 0; j < 4; ++j) {
+            const float wI = p.wq * I0[j];
+            Jacc[j] += wI;
+            if (MOM) {
+              Hm[MOM ? j : 0][0] += wI * p.mu[0];
+              Hm[MOM ? j : 0][1] += wI * p.mu[1];
+              Hm[MOM ? j : 0][2] += wI * p.mu[2];
+              Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+              Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+              Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+              Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+              Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+              Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
             }
           }
-        }
+        };
+        auto block = [&](auto su_c, auto sv_c, int k0, int kn) {
+#pragma unroll
+          for (int q = 0; q < AMAX; ++q)
+            if (q < kn) ray(su_c, sv_c, k0 + q);
+        };
+        block(SignC<-1>{}, SignC<-1>{}, gp.kb[0], gp.kb[1] - gp.kb[0]);
+        block(SignC<1>{}, SignC<-1>{}, gp.kb[1], gp.kb[2] - gp.kb[1]);
+        block(SignC<-1>{}, SignC<1>{}, gp.kb[2], gp.kb[3] - gp.kb[2]);
+        block(SignC<1>{}, SignC<1>{}, gp.kb[3], gp.kb[4] - gp.kb[3]);
         if (active) {
-          int crd[3];
-          crd[cax[0]] = u0;
-          crd[cax[1]] = v;
-          crd[cax[2]] = w;
-          const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+          const long long canon = (long long)(u0) * csu + (long long)v * csv + (long long)w * csw;
           float *Jf = reinterpret_cast<float *>(Jout);
           if (ustride == 1) {
             *reinterpret_cast<float4 *>(Jf + RT_IDX(canon, cells, 56)) = make_float4(Jacc[0], Jacc[1], Jacc[2], Jacc[3]);
@@ -1029,74 +1041,54 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
             for (int q = 0; q < 6; ++q) Km[MOM ? j : 0][q] = T(0);
           }
         }
-        const bool seg_u_first = u0 == 0, seg_u_last = u0 + ncell == Nu;
+        auto ray = [&](auto su_c, auto sv_c, int a) {
+          constexpr int SU = decltype(su_c)::value, SV = decltype(sv_c)::value;
+          const AngleParam<T> &p = P[a];
+          const T *Ia = Iprv + a * pb + row * W + kPipeX0 + u0;
+          T *Io = Icur + a * pb + row * W + kPipeX0 + u0;
+          const T *Iv = SV > 0 ? Ia - W : Ia + W;   // halo rows hold the neighbours' rows
+          T I0[SEG];
+          pipe_update<T, SEG, SU, SV>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+          if (lv == 0 && Ntop) {
   #pragma unroll
-        for (int a = 0; a < AMAX; ++a) {
-          if (a < na) {
-            const AngleParam<T> &p = P[a];
-            const T *Ia = Iprv + a * pb + row * W + kPipeX0 + u0;
-            T *Io = Icur + a * pb + row * W + kPipeX0 + u0;
-            T I0[SEG];
-            // row v - sv of the upwind plane: own rows, a neighbour's, or the ghost halo row
-            const T *Iv;
-            if (p.sv > 0) Iv = (lv == 0 && Itop) ? Itop + a * pb + u0 : Ia - W;
-            else Iv = (lv == R - 1 && Ibot) ? Ibot + a * pb + u0 : Ia + W;
-            const int key = (p.su > 0 ? 1 : 0) | (p.sv > 0 ? 2 : 0);
-            if (key == 3) pipe_update<T, SEG, 1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else if (key == 2) pipe_update<T, SEG, -1, 1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else if (key == 1) pipe_update<T, SEG, 1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
-            else pipe_update<T, SEG, -1, -1>(p, Ia, Iv, Io, ncell, cm, c0, cp, sm, s0, sp, chi0, S0, I0);
+            for (int j = 0; j < SEG; ++j)
+              if (j < ncell) Ntop[a * pb + u0 + j] = I0[j];
+          }
+          if (lv == R - 1 && Nbot) {
   #pragma unroll
-            for (int j = 0; j < SEG; ++j) {
-              const T wI = p.wq * I0[j];
-              Jacc[j] += wI;
-              if (MOM) {
-                Hm[MOM ? j : 0][0] += wI * p.mu[0];
-                Hm[MOM ? j : 0][1] += wI * p.mu[1];
-                Hm[MOM ? j : 0][2] += wI * p.mu[2];
-                Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
-                Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
-                Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
-                Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
-                Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
-                Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
-              }
-            }
-            if (A.write_ghosts) {
-              const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
-              const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
-              if (at_wlast) {
+            for (int j = 0; j < SEG; ++j)
+              if (j < ncell) Nbot[a * pb + u0 + j] = I0[j];
+          }
   #pragma unroll
-                for (int j = 0; j < SEG; ++j)
-                  if (j < ncell)
-                    ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + (long long)v * Nu + u0 + j, gn, 49), I0[j], inc, emit);
-              }
-              if (perU && (p.su > 0 ? seg_u_last : seg_u_first)) {
-                const int j = p.su > 0 ? ncell - 1 : 0;
-                T val = I0[0];
-  #pragma unroll
-                for (int q = 1; q < SEG; ++q)
-                  if (q == j) val = I0[q];
-                ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)w * Nv + v, gn, 50), val, inc, emit);
-              }
-              if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) {
-  #pragma unroll
-                for (int j = 0; j < SEG; ++j)
-                  if (j < ncell)
-                    ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)w * Nu + u0 + j, gn, 51),
-                                   I0[j], inc, emit);
-              }
+          for (int j = 0; j < SEG; ++j) {
+            const T wI = p.wq * I0[j];
+            Jacc[j] += wI;
+            if (MOM) {
+              Hm[MOM ? j : 0][0] += wI * p.mu[0];
+              Hm[MOM ? j : 0][1] += wI * p.mu[1];
+              Hm[MOM ? j : 0][2] += wI * p.mu[2];
+              Km[MOM ? j : 0][0] += wI * p.mu[0] * p.mu[0];
+              Km[MOM ? j : 0][1] += wI * p.mu[1] * p.mu[1];
+              Km[MOM ? j : 0][2] += wI * p.mu[2] * p.mu[2];
+              Km[MOM ? j : 0][3] += wI * p.mu[0] * p.mu[1];
+              Km[MOM ? j : 0][4] += wI * p.mu[0] * p.mu[2];
+              Km[MOM ? j : 0][5] += wI * p.mu[1] * p.mu[2];
             }
           }
-        }
+        };
+        auto block = [&](auto su_c, auto sv_c, int k0, int kn) {
+  #pragma unroll
+          for (int q = 0; q < AMAX; ++q)
+            if (q < kn) ray(su_c, sv_c, k0 + q);
+        };
+        block(SignC<-1>{}, SignC<-1>{}, gp.kb[0], gp.kb[1] - gp.kb[0]);
+        block(SignC<1>{}, SignC<-1>{}, gp.kb[1], gp.kb[2] - gp.kb[1]);
+        block(SignC<-1>{}, SignC<1>{}, gp.kb[2], gp.kb[3] - gp.kb[2]);
+        block(SignC<1>{}, SignC<1>{}, gp.kb[3], gp.kb[4] - gp.kb[3]);
   #pragma unroll
         for (int j = 0; j < SEG; ++j) {
           if (j < ncell) {
-            int crd[3];
-            crd[cax[0]] = u0 + j;
-            crd[cax[1]] = v;
-            crd[cax[2]] = w;
-            const long long canon = ((long long)crd[2] * A.d.n[1] + crd[1]) * A.d.n[0] + crd[0];
+            const long long canon = (long long)(u0 + j) * csu + (long long)v * csv + (long long)w * csw;
             Jout[RT_IDX(canon, cells, 52)] = Jacc[j];
             if (MOM) {
               T *M = A.Mpart + (long long)gi * 9 * A.d.nf * cells;
@@ -1111,10 +1103,13 @@ __global__ void __launch_bounds__(512) sc_sweep_pipe_kernel(const SweepArgs<T> A
         }
       }
     }
+    // outflow ghosts of the previous plane, read from its (still intact) buffer
+    if (t > 0) ghost_pass(Iprv, w - sa);
     cp_async_wait_all();
     if (C > 1) cluster.sync();
     else __syncthreads();
   }
+  ghost_pass(Ib + ((Nw - 1) & 1) * ib, sa > 0 ? Nw - 1 : 0);
   (void)top_edge;
   (void)bot_edge;
 }
@@ -1184,8 +1179,25 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
     if (x < nx && y < ny) {
       const long long c = ((long long)z * ny + y) * nx + x;
       const long long i = fbase + c;
-      double dJ = 0.0;
-      for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[(long long)p * A.d.nf * cells + i];
+      double dJ;
+      if (sizeof(T) == 4) {
+        // float32 partials summed exactly into a float pair (TwoSum), then one FP64
+        // add: the result is the FP64 sum to ~1e-14 at FP32 cost
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+        for (int p = 0; p < A.ngroups_per_f; ++p) {
+          const float x = (float)A.Jpart[(long long)p * A.d.nf * cells + i];
+          const float s2 = hi + x;
+          const float bp = s2 - hi;
+          lo += (hi - (s2 - bp)) + (x - bp);
+          hi = s2;
+        }
+        dJ = (double)hi + (double)lo;
+      } else {
+        dJ = 0.0;
+#pragma unroll 4
+        for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[(long long)p * A.d.nf * cells + i];
+      }
       // incremental solves accumulate J in FP64 from the swept increments
       const double J = inc ? A.J64[i] + dJ : dJ;
       double r;
@@ -1196,11 +1208,15 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
         snew = A.incremental ? T(0) : (T)A.S64[i];
       } else {
         const double S = A.S64[i], e = A.eps[i];
-        const double dS = ((1.0 - e) * J + e * A.B[i] - S) / (e + (1.0 - e) * A.oml[i]);
+        const double dS = ((1.0 - e) * J + e * A.B[i] - S) * A.iden[i];
         const double Sn = S + dS;
         A.S64[i] = Sn;
         A.Sfs[i] = S;
-        r = rel_change(dS, Sn);
+        // the float32 path takes the stopping quantity in float32 (within 1e-7 of
+        // it, relative) unless S is outside the float32 normal range
+        r = (sizeof(T) == 4 && fabs(Sn) > 1e-30 && fabs(Sn) < 1e30 && fabs(dS) < 1e30)
+                ? (double)__fdividef((float)fabs(dS), (float)fabs(Sn))
+                : rel_change(dS, Sn);
         snew = (T)(A.incremental ? dS : Sn);
       }
       A.J64[i] = J;
@@ -1219,6 +1235,14 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
     }
   }
   block_max_to(rmax, &A.st->resid_bits);
+}
+
+// Jacobi denominator of Eq. 24, inverted once per medium: the update then
+// multiplies instead of dividing in FP64 every iteration.
+__global__ void inv_denominator_kernel(long long n, const double *eps, const double *oml, double *iden) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    iden[i] = 1.0 / (eps[i] + (1.0 - eps[i]) * oml[i]);
 }
 
 // Convergence decision after one ALI iteration (single thread).
@@ -1436,14 +1460,48 @@ __global__ void eps_thick_min_kernel(Dims d, const double *eps, const double *om
 }
 
 // Q = 4 pi sum_nu w_nu eps_nu chi_nu (J_nu - B_nu)  (integral form, Sec. 4).
+// d/dx of one component of H at a cell (i along an axis of n cells, stride st):
+// centred difference, wrapped on a periodic axis, one-sided at the ends of a
+// bounded one, zero on an axis of one cell.
+__device__ __forceinline__ double ddx(const double *F, long long c, int i, int n, long long st, int per,
+                                      double h) {
+  if (n == 1) return 0.0;
+  if (per) {
+    const long long cp = i + 1 < n ? c + st : c - (long long)(n - 1) * st;
+    const long long cm = i > 0 ? c - st : c + (long long)(n - 1) * st;
+    return (F[cp] - F[cm]) / (2.0 * h);
+  }
+  if (i == 0) return (F[c + st] - F[c]) / h;
+  if (i == n - 1) return (F[c] - F[c - st]) / h;
+  return (F[c + st] - F[c - st]) / (2.0 * h);
+}
+
+// Heating rate (Sec. 4): Q^int = 4 pi sum w chi_abs (J - B), Q^dif = -4 pi sum w div H,
+// or per cell and frequency the integral form where chi dx <= 1 (form 2).
 __global__ void heating_kernel(Dims d, const double *fw, const double *chi, const double *eps,
-                               const double *J, const double *B, double *Q) {
+                               const double *J, const double *B, const double *H, double hx, double hy,
+                               double hz, double width, int form, double *Q) {
+  const long long sy = d.n[0], sz = (long long)d.n[0] * d.n[1];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.cells;
        c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % d.n[0]);
+    const int y = (int)((c / d.n[0]) % d.n[1]);
+    const int z = (int)(c / sz);
     double q = 0.0;
     for (int f = 0; f < d.nf; ++f) {
       const long long i = (long long)f * d.cells + c;
-      q += fw[f] * eps[i] * chi[i] * (J[i] - B[i]);
+      const bool integral = form == 0 || (form == 2 && chi[i] * width <= 1.0);
+      double qf;
+      if (integral) {
+        qf = eps[i] * chi[i] * (J[i] - B[i]);
+      } else {
+        const double *Hf = H + (long long)f * 3 * d.cells;
+        const double div = ddx(Hf, c, x, d.n[0], 1, d.periodic[0], hx) +
+                           ddx(Hf + d.cells, c, y, d.n[1], sy, d.periodic[1], hy) +
+                           ddx(Hf + 2 * d.cells, c, z, d.n[2], sz, d.periodic[2], hz);
+        qf = -div;
+      }
+      q += fw[f] * qf;
     }
     Q[c] = 4.0 * M_PI * q;
   }
@@ -1686,9 +1744,21 @@ cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double 
   return cudaGetLastError();
 }
 
+cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
+                                   cudaStream_t s) {
+  inv_denominator_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, eps, oml, iden);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, const double *eps,
-                           const double *J, const double *B, double *Q, cudaStream_t s) {
-  heating_kernel<<<grid_for(d.cells, 256), 256, 0, s>>>(d, fw, chi, eps, J, B, Q);
+                           const double *J, const double *B, const double *H, const double h[3],
+                           int form, double *Q, cudaStream_t s) {
+  double width = 0.0;   // largest spacing along axes of more than one cell
+  for (int a = 0; a < 3; ++a)
+    if (d.n[a] > 1) width = width > h[a] ? width : h[a];
+  if (width == 0.0) width = h[0];
+  heating_kernel<<<grid_for(d.cells, 256), 256, 0, s>>>(d, fw, chi, eps, J, B, H, h[0], h[1], h[2], width,
+                                                        form, Q);
   return cudaGetLastError();
 }
 

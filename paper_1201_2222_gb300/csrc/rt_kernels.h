@@ -35,7 +35,8 @@ struct AliArgs {
   Dims d;
   int ngroups_per_f;
   const T *Jpart;
-  const double *eps, *B, *oml;
+  const double *eps, *B;
+  const double *iden;        // 1 / [eps + (1 - eps)(1 - Lambda*)], fixed for a medium
   double *S64, *Sfs, *J64, *Jprev;
   T *SP[3];                  // permuted sweep copies of S to refresh (NULL = axis unused)
   SolveState *st;
@@ -49,6 +50,10 @@ cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int thre
                          cudaStream_t s);
 // cells per thread of the tiled sweeps
 constexpr int kSweepSeg = 4;
+// threads per CTA of the tiled and pipelined sweeps: FP64 keeps 256 so that its
+// stencils stay in registers
+template <typename T>
+constexpr int sweep_max_threads() { return sizeof(T) == 8 ? 256 : 512; }
 // staged row length of the pipelined sweep: 4 leading columns (halo at 3), Nu
 // cells, halo, segment padding, rounded to 16 bytes
 __host__ __device__ inline int pipe_row_len(int Nu, int seg) { return ((4 + Nu + 1 + seg + 3) / 4) * 4; }
@@ -64,6 +69,9 @@ cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, in
 template <typename T>
 cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s);
 cudaError_t launch_finish(SolveState *st, cudaStream_t s);
+// iden = 1 / [eps + (1 - eps)(1 - Lambda*)] (the Jacobi denominator of Eq. 24)
+cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
+                                   cudaStream_t s);
 cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cudaStream_t s);
 template <typename T>
 cudaError_t launch_lstar(const Dims &d, const double *chi, const RayGeom *rays, int na, double *lstar,
@@ -88,7 +96,10 @@ cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, co
 // as the bits of a non-negative double (atomicMin); cells with none leave 1.0
 cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double *oml,
                                  unsigned long long *out, cudaStream_t s);
+// heating rate in the integral (0), differential (1) or switched (2) form; H
+// [nf][3][cells], h the cell spacings
 cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, const double *eps,
-                           const double *J, const double *B, double *Q, cudaStream_t s);
+                           const double *J, const double *B, const double *H, const double h[3],
+                           int form, double *Q, cudaStream_t s);
 
 }  // namespace rtk
