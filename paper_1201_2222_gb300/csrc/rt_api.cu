@@ -383,7 +383,12 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
     }
   }
   *smem = sm;
-  *threads = std::max(32, std::min(sweep_thread_cap(g, variant), ((th + 31) / 32) * 32));
+  // tasks of a plane spread evenly: the fewest passes the thread cap allows, and
+  // the fewest threads that finish the plane in that many passes
+  const int cap = sweep_thread_cap(g, variant);
+  const int passes = std::max(1, (th + cap - 1) / cap);
+  const int per = (th + passes - 1) / passes;
+  *threads = std::max(32, std::min(cap, ((per + 31) / 32) * 32));
 }
 
 // Split each (crossed axis, direction) class of rays into chunks of <= apg.
@@ -1338,7 +1343,7 @@ struct TuneKey {
   bool operator==(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
 };
 struct TuneVal {
-  int variant, apg, cluster;
+  int variant, apg, cluster, threads;
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
@@ -1361,7 +1366,7 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
   const TuneKey key = tune_key(g);
-  TuneVal best{0, 0, 0};
+  TuneVal best{0, 0, 0, 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto &kv : g_tune_cache)
@@ -1389,29 +1394,35 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
       for (int ai = 0; ai < 7; ++ai) {
         for (int ci = 0; ci < 9; ++ci) {
           if (clusters[ci] > minNv) continue;
-          g->req_variant = variants[vi];
-          g->req_apg = apgs[ai];
-          g->req_cluster = clusters[ci];
-          g->req_threads = 0;
-          plan_groups(g);
-          if (g->groups.empty() || g->smem > kSweepSmemBudget || g->apg != apgs[ai] || g->cluster != clusters[ci])
-            continue;
-          if ((r = upload_plan_any(g)) != RT_OK) return r;
-          float ms = 0.0f;
-          bool ok = true;
-          for (int rep = 0; rep < 3 && ok; ++rep) {   // one warm-up, two timed
-            CU(cudaEventRecord(e0, s));
-            r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
-            if (r != RT_OK) { ok = false; cudaGetLastError(); break; }
-            CU(cudaEventRecord(e1, s));
-            CU(cudaEventSynchronize(e1));
-            float t = 0.0f;
-            CU(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) ms += t;
-          }
-          if (ok && ms < best_ms) {
-            best_ms = ms;
-            best = TuneVal{variants[vi], apgs[ai], clusters[ci]};
+          // the evenly spread CTA (planner default) and, if different, the largest
+          int balanced = 0;
+          for (int ti = 0; ti < 2; ++ti) {
+            g->req_variant = variants[vi];
+            g->req_apg = apgs[ai];
+            g->req_cluster = clusters[ci];
+            g->req_threads = ti == 0 ? 0 : sweep_thread_cap(g, variants[vi]);
+            plan_groups(g);
+            if (g->groups.empty() || g->smem > kSweepSmemBudget || g->apg != apgs[ai] || g->cluster != clusters[ci])
+              break;
+            if (ti == 0) balanced = g->threads;
+            else if (g->threads == balanced) break;
+            if ((r = upload_plan_any(g)) != RT_OK) return r;
+            float ms = 1e30f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {   // one warm-up, the best of three
+              CU(cudaEventRecord(e0, s));
+              r = g->desc.prec == RT_PREC_FP64 ? formal_once<double>(g, s) : formal_once<float>(g, s);
+              if (r != RT_OK) { ok = false; cudaGetLastError(); break; }
+              CU(cudaEventRecord(e1, s));
+              CU(cudaEventSynchronize(e1));
+              float t = 0.0f;
+              CU(cudaEventElapsedTime(&t, e0, e1));
+              if (rep > 0) ms = std::min(ms, t);
+            }
+            if (ok && ms < best_ms) {
+              best_ms = ms;
+              best = TuneVal{variants[vi], apgs[ai], clusters[ci], g->req_threads};
+            }
           }
         }
       }
@@ -1430,7 +1441,7 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
   g->req_variant = best.variant;
   g->req_apg = best.apg;
   g->req_cluster = best.cluster;
-  g->req_threads = 0;
+  g->req_threads = best.threads;
   plan_groups(g);
   if ((r = upload_plan_any(g)) != RT_OK) return r;
   // leave the solver state as rt_set_opacity_source does: S = B, fresh ghosts

@@ -1283,46 +1283,95 @@ __global__ void state_op_kernel(SolveState *st, int op, int a, double b, int c) 
 
 // ------------------------------------------------------------------- Lambda*
 // Lambda*_ii = sum_k w_k Psi0_k(i) and 1 - Lambda*_ii = sum_k w_k (1 - Psi0_k(i)),
-// from chi alone, with the sweep's precision T for the segment weights and FP64 sums.
+// from chi alone, with the sweep's precision T for the segment weights; the sums
+// are FP64 (float32 grids: exact float pairs).  The rays' constants are staged in
+// shared memory; each thread owns one cell and frequency.
+template <typename T>
+struct LstarRay {
+  T w4[4];            // weights of the four upwind face vertices
+  T hs;               // half the path length, s/2
+  double w;           // quadrature weight
+  signed char off[4][3];   // canonical offsets (x, y, z) of the four vertices
+};
+constexpr int kLstarChunk = 64;   // rays staged in shared memory at a time
+
 template <typename T>
 __global__ void __launch_bounds__(256) lstar_kernel(Dims d, const double *chi, const RayGeom *rays,
                                                     int na, double *lstar, double *oml) {
+  __shared__ LstarRay<T> R[kLstarChunk];
   const long long cells = d.cells;
   const long long N = cells * d.nf;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / cells, c = i - f * cells;
-    const int c0[3] = {(int)(c % d.n[0]), (int)((c / d.n[0]) % d.n[1]),
-                       (int)(c / ((long long)d.n[0] * d.n[1]))};
+  const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+  const int px = d.periodic[0], py = d.periodic[1], pz = d.periodic[2];
+  // every block walks the same cell range in the same chunks, so the barriers match
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nloop = (N + stride - 1) / stride;
+  for (long long it = 0; it < nloop; ++it) {
+    const long long i = it * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool live = i < N;
+    const long long f = live ? i / cells : 0, c = live ? i - f * cells : 0;
+    const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
     const double *chf = chi + f * cells;
-    const T chi0 = (T)chf[c];
-    double L = 0.0, O = 0.0;
-    for (int k = 0; k < na; ++k) {
-      const RayGeom r = rays[k];
-      const int ax = r.axis, b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
-      T chim = T(0);
-      for (int d1 = 0; d1 < 2; ++d1) {
-        for (int d2 = 0; d2 < 2; ++d2) {
-          const double wv = (d1 ? r.frac[b1] : 1.0 - r.frac[b1]) * (d2 ? r.frac[b2] : 1.0 - r.frac[b2]);
-          int cc[3];
-          cc[ax] = c0[ax] - r.sgn[ax];
-          cc[b1] = c0[b1] - d1 * r.sgn[b1];
-          cc[b2] = c0[b2] - d2 * r.sgn[b2];
-          for (int q = 0; q < 3; ++q) {
-            if (cc[q] < 0) cc[q] = d.periodic[q] ? cc[q] + d.n[q] : 0;
-            else if (cc[q] >= d.n[q]) cc[q] = d.periodic[q] ? cc[q] - d.n[q] : d.n[q] - 1;
-          }
-          chim += (T)wv * (T)chf[((long long)cc[2] * d.n[1] + cc[1]) * d.n[0] + cc[0]];
+    const T chi0 = live ? (T)chf[c] : T(0);
+    // float32 sums kept exact as a float pair (TwoSum); FP64 sums directly
+    T Lh = T(0), Ll = T(0), Oh = T(0), Ol = T(0);
+    for (int k0 = 0; k0 < na; k0 += kLstarChunk) {
+      const int nk = min(kLstarChunk, na - k0);
+      __syncthreads();
+      if (threadIdx.x < nk) {
+        const RayGeom r = rays[k0 + threadIdx.x];
+        LstarRay<T> q;
+        const int ax = r.axis, b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        const double f1 = b1 == 0 ? r.frac[0] : (b1 == 1 ? r.frac[1] : r.frac[2]);
+        const double f2 = b2 == 0 ? r.frac[0] : (b2 == 1 ? r.frac[1] : r.frac[2]);
+        for (int v = 0; v < 4; ++v) {
+          const int d1 = v >> 1, d2 = v & 1;
+          q.w4[v] = (T)((d1 ? f1 : 1.0 - f1) * (d2 ? f2 : 1.0 - f2));
+          int o[3] = {0, 0, 0};
+          o[ax] = -r.sgn[ax];
+          o[b1] = -d1 * r.sgn[b1];
+          o[b2] = -d2 * r.sgn[b2];
+          for (int a = 0; a < 3; ++a) q.off[v][a] = (signed char)o[a];
+        }
+        q.hs = (T)(0.5 * r.s);
+        q.w = r.w;
+        R[threadIdx.x] = q;
+      }
+      __syncthreads();
+      if (!live) continue;
+      for (int k = 0; k < nk; ++k) {
+        const LstarRay<T> &q = R[k];
+        T chim = T(0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          int xx = x + q.off[v][0], yy = y + q.off[v][1], zz = z + q.off[v][2];
+          xx = xx < 0 ? (px ? nx - 1 : 0) : (xx >= nx ? (px ? 0 : nx - 1) : xx);
+          yy = yy < 0 ? (py ? ny - 1 : 0) : (yy >= ny ? (py ? 0 : ny - 1) : yy);
+          zz = zz < 0 ? (pz ? nz - 1 : 0) : (zz >= nz ? (pz ? 0 : nz - 1) : zz);
+          chim += q.w4[v] * (T)chf[((long long)zz * ny + yy) * nx + xx];
+        }
+        const T dtau = (chim + chi0) * q.hs;
+        T E, psi0, om;
+        seg_weights(dtau, E, psi0, om);
+        const T wl = (T)q.w * psi0, wo = (T)q.w * om;
+        if (sizeof(T) == 4) {
+          T s2 = Lh + wl, bp = s2 - Lh;
+          Ll += (Lh - (s2 - bp)) + (wl - bp);
+          Lh = s2;
+          s2 = Oh + wo;
+          bp = s2 - Oh;
+          Ol += (Oh - (s2 - bp)) + (wo - bp);
+          Oh = s2;
+        } else {
+          Lh += q.w * (double)psi0;
+          Oh += q.w * (double)om;
         }
       }
-      const T dtau = (chim + chi0) * (T)(0.5 * r.s);
-      T E, psi0, om;
-      seg_weights(dtau, E, psi0, om);
-      L += r.w * (double)psi0;
-      O += r.w * (double)om;
     }
-    lstar[i] = L;
-    oml[i] = O;
+    if (live) {
+      lstar[i] = (double)Lh + (double)Ll;
+      oml[i] = (double)Oh + (double)Ol;
+    }
   }
 }
 
