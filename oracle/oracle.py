@@ -2,13 +2,16 @@
 
 Follows Davis, Stone & Jiang (2012):
   * ``formal_solution``  - one short-characteristics formal solution J = Lambda[S]
-    (Sec. 3.3, Eq. 20 with linear interpolation), also returning the diagonal
-    Lambda* (Sec. 3.4, Olson & Kunasz 1987) and, on request, H and K (Eqs. 18-19).
-    The sweep itself is the C function in ``sc_oracle.c``.
+    (Sec. 3.3, Eq. 20 with linear interpolation, or with monotonic quadratic
+    face interpolation and second-order Bezier-controlled segment integration),
+    also returning the diagonal Lambda* (Sec. 3.4, Olson & Kunasz 1987) and, on
+    request, H and K (Eqs. 18-19).  The sweeps are the C functions in
+    ``sc_oracle.c``.
   * ``init_ghosts``      - first-iteration periodic ghost intensities: I = S of the
     periodic image cell (the paper lags incoming periodic/subdomain intensities
     by one iteration, Sec. 3; with no previous iteration the image S is used).
-  * ``ali_solve``        - Jacobi ALI (Eq. 24):
+  * ``ali_solve``        - Jacobi ALI (Eq. 24; with the second-order scheme Lambda*
+    is taken from each formal solution):
         dS = [(1 - eps) J + eps B - S] / [1 - (1 - eps) Lambda*],  S <- S + dS,
     stopped when max |dS|/S <= delta_c (Eq. 25); when every eps = 1 the test uses
     the change of J between consecutive formal solutions (Sec. 3.4).  The
@@ -43,11 +46,14 @@ def _load():
         lib = ctypes.CDLL(path)
         d = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
-        lib.orc_formal_solution.argtypes = [
-            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-            ctypes.c_double, ip, ip, ctypes.c_int, d, d, d, d, d, d, d, d, d, d, d, d,
-            ctypes.c_int]
-        lib.orc_formal_solution.restype = ctypes.c_int
+        for fn in (lib.orc_formal_solution, lib.orc_formal_solution_quad):
+            fn.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ip, ip, ctypes.c_int, d, d, d, d, d, d, d, d, d, d, d, d,
+                ctypes.c_int]
+            fn.restype = ctypes.c_int
+        lib.orc_bezier_weights.argtypes = [ctypes.c_double, d]
+        lib.orc_bezier_weights.restype = None
         lib.orc_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -118,9 +124,20 @@ def init_ghosts(grid: Grid, S: np.ndarray) -> np.ndarray:
     return G
 
 
+def bezier_weights(dtau):
+    """(a, b, c) of the second-order segment integration (see sc_oracle.c)."""
+    out = np.empty(3)
+    _load().orc_bezier_weights(float(dtau), _ptr(out))
+    return out
+
+
 def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=False,
-                    nthreads=1):
+                    nthreads=1, interp="linear"):
     """One formal solution for one frequency.
+
+    ``interp``: "linear" (bilinear face interpolation, linear S along the segment)
+    or "quadratic" (monotonic quadratic face interpolation and second-order
+    Bezier-controlled integration of S, Sec. 3.3).
 
     ``G_prev`` defaults to ``init_ghosts(grid, S)``; ``I_fixed`` is the user
     incident-intensity array for RT_BC_FIXED faces
@@ -147,11 +164,12 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     bl = (ctypes.c_int * 3)(*grid.bc_lo)
     bh = (ctypes.c_int * 3)(*grid.bc_hi)
     mu = np.ascontiguousarray(grid.mu).reshape(-1)
-    rc = lib.orc_formal_solution(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
-                                 grid.d[2], bl, bh, grid.na, _ptr(mu), _ptr(grid.w),
-                                 _ptr(chi), _ptr(S), _ptr(B), _ptr(I_fixed), _ptr(G_prev),
-                                 _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
-                                 int(nthreads))
+    fn = {"linear": lib.orc_formal_solution, "quadratic": lib.orc_formal_solution_quad}[interp]
+    rc = fn(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
+            grid.d[2], bl, bh, grid.na, _ptr(mu), _ptr(grid.w),
+            _ptr(chi), _ptr(S), _ptr(B), _ptr(I_fixed), _ptr(G_prev),
+            _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
+            int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle formal solution failed ({rc})")
     out = dict(J=J.reshape(grid.shape), lstar=L.reshape(grid.shape), G_next=G_next)
@@ -241,7 +259,7 @@ def heating_rate_switch(grid: Grid, chi, eps, J, B, H, freq_w):
 
 
 def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_init=None,
-              I_fixed=None, nthreads=1, moments=True):
+              I_fixed=None, nthreads=1, moments=True, interp="linear"):
     """Jacobi ALI to max|dS|/S <= tol (Eqs. 24-25), all frequencies per iteration.
 
     chi, eps, B: [nf][nz][ny][nx].  I_fixed: None or a list (per frequency) of
@@ -267,9 +285,12 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
     for it in range(1, max_iter + 1):
         G_new = []
         for f in range(nf):
-            res = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f), nthreads=nthreads)
+            res = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f), nthreads=nthreads,
+                                  interp=interp)
             J[f] = res["J"]
-            if it == 1:
+            # the linear scheme's Lambda* depends on chi alone; the second-order
+            # scheme's on S too (through its clamps): take it from every solution
+            if it == 1 or interp == "quadratic":
                 lstar[f] = res["lstar"]
             G_new.append(res["G_next"])
         S_fs, G_fs = S, G
@@ -291,7 +312,7 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
         K = np.empty((nf, 6) + grid.shape)
         for f in range(nf):
             res = formal_solution(grid, chi[f], S_fs[f], B[f], G_fs[f], fixed(f), moments=True,
-                                  nthreads=nthreads)
+                                  nthreads=nthreads, interp=interp)
             H[f] = res["H"]
             K[f] = res["K"]
         out["H"] = H

@@ -280,6 +280,264 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
   return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Second-order variant (Sec. 3.3): monotonic quadratic interpolation on the
+ * crossed face and the second-order (Bezier-controlled parabolic) integration
+ * of S along the segment.
+ *
+ *   - the ray's upwind and downwind points lie on the planes c[a] -/+ 1 of its
+ *     crossed axis a, at the fractional offsets -/+ sgn*frac along the two face
+ *     axes; each is interpolated from the 3 x 3 face vertices centred on the
+ *     cell's own column, along the lower canonical face axis first, then the
+ *     other (quad1: the parabola
+ *     through three values clamped to the two bracketing ones -- no new
+ *     extrema, positivity kept, exact for monotone quadratic data);
+ *   - because that stencil reaches the vertex ahead of the ray on the upwind
+ *     face, the sweep runs plane by plane along the crossed axis (the paper's
+ *     reorientation of the sweep for shallow rays);
+ *   - I-, S-, chi- at the upwind point; S+, chi+ at the downwind point (chi and
+ *     S there follow the same ghost rules as the upwind side);
+ *   - dtau- = (chi- + chi0) s / 2, dtau+ = (chi0 + chi+) s / 2;
+ *   - S between the upwind point and the cell is the quadratic Bezier curve with
+ *     end values S-, S0 and control value Sc = S0 - (dtau-/2) S'(tau0), S' the
+ *     derivative at the cell of the parabola through (S-, S0, S+); Sc is
+ *     clamped to [min(S-, S0), max(S-, S0)] (where the parabola would
+ *     overshoot);
+ *   - I0 = I- exp(-dtau-) + a S- + b S0 + c Sc, with a, b, c the integrals of
+ *     the Bernstein polynomials against exp(-(dtau- - t)) (orc_bezier_weights);
+ *   - Lambda*_ii = sum_k w_k (b + c dSc/dS0): the local dependence of I0 on S0,
+ *     with dSc/dS0 that of the control point limited to [0, 1] (0 or 1 where it
+ *     is clamped).  It depends on S through the clamps, so an ALI solve with this
+ *     scheme takes Lambda* from each formal solution.
+ * ---------------------------------------------------------------------- */
+
+/* a, b, c of I0 = I- e^{-t} + a S- + b S0 + c Sc for a segment of optical depth t:
+ * with x the optical distance back from the cell and u = 1 - x/t,
+ * a = int (x/t)^2 e^{-x}, b = int (1 - x/t)^2 e^{-x}, c = int 2 (x/t)(1 - x/t) e^{-x},
+ * over 0 <= x <= t.  Series in t below 0.1, closed forms above. */
+void orc_bezier_weights(double t, double *w3) {
+  if (t <= 0.0) { w3[0] = w3[1] = w3[2] = 0.0; return; }
+  double m0, m1, m2;   /* m_n = int_0^t x^n e^{-x} dx / t^(n+1) */
+  if (t < 0.1) {
+    /* m_n = sum_k (-t)^k / (k! (n+k+1)) */
+    double p = 1.0, f = 1.0;
+    m0 = m1 = m2 = 0.0;
+    for (int k = 0; k < 14; ++k) {
+      m0 += p / (f * (k + 1));
+      m1 += p / (f * (k + 2));
+      m2 += p / (f * (k + 3));
+      p *= -t;
+      f *= (k + 1);
+    }
+  } else {
+    const double E = exp(-t);
+    const double E0 = -expm1(-t);
+    const double E1 = E0 - t * E;
+    const double E2 = 2.0 * E1 - t * t * E;
+    m0 = E0 / t;
+    m1 = E1 / (t * t);
+    m2 = E2 / (t * t * t);
+  }
+  /* a = t m2, b = t (m0 - 2 m1 + m2), c = 2 t (m1 - m2) */
+  w3[0] = t * m2;
+  w3[1] = t * (m0 - 2.0 * m1 + m2);
+  w3[2] = 2.0 * t * (m1 - m2);
+}
+
+/* Monotonic quadratic interpolation of f(-1), f(0), f(1) at t in [-1, 1]: the
+ * parabola through the three values, clamped to the range of the two values
+ * that bracket t.  No new extrema (positivity kept); exact for quadratic data
+ * wherever the parabola is monotone between the bracketing vertices. */
+static double quad1(double fm, double f0, double fp, double t) {
+  if (t == 0.0) return f0;
+  double v = f0 + 0.5 * t * (fp - fm) + 0.5 * t * t * (fp - 2.0 * f0 + fm);
+  const double fe = t < 0.0 ? fm : fp;
+  const double lo = fe < f0 ? fe : f0, hi = fe < f0 ? f0 : fe;
+  if (v < lo) v = lo;
+  if (v > hi) v = hi;
+  return v;
+}
+
+int orc_formal_solution_quad(int nx, int ny, int nz, double dx, double dy, double dz,
+                             const int *bc_lo, const int *bc_hi,
+                             int na, const double *mu, const double *wq,
+                             const double *chi, const double *S, const double *B,
+                             const double *I_fixed, const double *G_prev, double *G_next,
+                             double *J, double *lstar, double *H, double *K, int nthreads) {
+  geom g;
+  g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
+  g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
+  g.two_d = (nz == 1);
+  for (int a = 0; a < 3; ++a) { g.bc_lo[a] = bc_lo[a]; g.bc_hi[a] = bc_hi[a]; }
+  g.cells = (long)nx * ny * nz;
+  g.face[0] = (long)nz * ny; g.face[1] = (long)nz * nx; g.face[2] = (long)ny * nx;
+  g.goff[0] = 0; g.goff[1] = g.face[0]; g.goff[2] = g.face[0] + g.face[1];
+  g.gsize = g.face[0] + g.face[1] + g.face[2];
+  if (nx < 1 || ny < 1 || nz < 1 || na < 1) return -1;
+  if (nthreads < 1) nthreads = 1;
+
+  const long C = g.cells;
+  const int want_mom = (H != NULL) || (K != NULL);
+  const int nacc = want_mom ? 11 : 2;
+  double *acc = (double *)calloc((size_t)nthreads * C * nacc, sizeof(double));
+  double *Iw = (double *)malloc((size_t)nthreads * C * sizeof(double));
+  if (!acc || !Iw) { free(acc); free(Iw); return -2; }
+
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+  for (int k = 0; k < na; ++k) {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    double *I = Iw + (long)t * C;
+    double *accJ = acc + (long)t * C * nacc;
+    double *accL = accJ + C;
+    double *accH = accL + C;
+    double *accK = accH + 3 * C;
+    const double m[3] = {mu[3 * k], mu[3 * k + 1], mu[3 * k + 2]};
+    const double w = wq[k];
+    int sgn[3];
+    double tpath[3];
+    for (int a = 0; a < 3; ++a) {
+      sgn[a] = m[a] >= 0.0 ? 1 : -1;
+      tpath[a] = (a == 2 && g.two_d) ? INFINITY : g.d[a] / fabs(m[a]);
+    }
+    int ax = 2;
+    if (tpath[1] < tpath[ax]) ax = 1;
+    if (tpath[0] < tpath[ax]) ax = 0;
+    const double s = tpath[ax];
+    double frac[3];
+    for (int a = 0; a < 3; ++a) {
+      if (a == ax) frac[a] = 1.0;
+      else if (a == 2 && g.two_d) frac[a] = 0.0;
+      else frac[a] = s * fabs(m[a]) / g.d[a];
+    }
+    /* face axes: b1 the lower canonical axis (interpolated first), b2 the higher */
+    const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+    /* offsets of the upwind point on its face, in cells along b1, b2 */
+    const double t1 = -sgn[b1] * frac[b1], t2 = -sgn[b2] * frac[b2];
+
+    /* planes along the crossed axis in the ray's direction; within a plane any order */
+    for (int pa = 0; pa < g.n[ax]; ++pa) {
+      const int ia = sgn[ax] > 0 ? pa : g.n[ax] - 1 - pa;
+      for (int q2 = 0; q2 < g.n[b2]; ++q2) {
+        for (int q1 = 0; q1 < g.n[b1]; ++q1) {
+          int c0[3];
+          c0[ax] = ia; c0[b1] = q1; c0[b2] = q2;
+          const long ci = cell_index(&g, c0[0], c0[1], c0[2]);
+          /* 3 x 3 values on the upwind and downwind faces */
+          double Iu[3][3], Su[3][3], Cu[3][3], Sd[3][3], Cd[3][3];
+          for (int e2 = -1; e2 <= 1; ++e2) {
+            for (int e1 = -1; e1 <= 1; ++e1) {
+              int c[3];
+              c[b1] = c0[b1] + e1;
+              c[b2] = c0[b2] + e2;
+              c[ax] = c0[ax] - sgn[ax];
+              int inside = c[0] >= 0 && c[0] < nx && c[1] >= 0 && c[1] < ny && c[2] >= 0 && c[2] < nz;
+              int fi = map_field(&g, c);
+              Cu[e2 + 1][e1 + 1] = chi[fi];
+              Su[e2 + 1][e1 + 1] = S[fi];
+              Iu[e2 + 1][e1 + 1] = inside ? I[cell_index(&g, c[0], c[1], c[2])]
+                                          : ghost_I(&g, c, k, na, B, I_fixed, G_prev);
+              c[ax] = c0[ax] + sgn[ax];
+              fi = map_field(&g, c);
+              Cd[e2 + 1][e1 + 1] = chi[fi];
+              Sd[e2 + 1][e1 + 1] = S[fi];
+            }
+          }
+          double rI[3], rS[3], rC[3], rSd[3], rCd[3];
+          for (int r = 0; r < 3; ++r) {
+            rI[r] = quad1(Iu[r][0], Iu[r][1], Iu[r][2], t1);
+            rS[r] = quad1(Su[r][0], Su[r][1], Su[r][2], t1);
+            rC[r] = quad1(Cu[r][0], Cu[r][1], Cu[r][2], t1);
+            rSd[r] = quad1(Sd[r][0], Sd[r][1], Sd[r][2], -t1);
+            rCd[r] = quad1(Cd[r][0], Cd[r][1], Cd[r][2], -t1);
+          }
+          const double Im = quad1(rI[0], rI[1], rI[2], t2);
+          const double Sm = quad1(rS[0], rS[1], rS[2], t2);
+          const double chim = quad1(rC[0], rC[1], rC[2], t2);
+          const double Sp = quad1(rSd[0], rSd[1], rSd[2], -t2);
+          const double chip = quad1(rCd[0], rCd[1], rCd[2], -t2);
+          const double S0 = S[ci], chi0 = chi[ci];
+          const double hm = 0.5 * (chim + chi0) * s, hp = 0.5 * (chi0 + chip) * s;
+          double I0, dI0;
+          if (hm <= 0.0) {
+            I0 = Im;    /* no opacity along the segment */
+            dI0 = 0.0;
+          } else {
+            /* derivative at the cell of the parabola through (-hm, S-), (0, S0), (hp, S+) */
+            double dS, ddS;   /* S'(tau0) and its derivative with respect to S0 */
+            const double dm = (S0 - Sm) / hm;
+            if (hp > 0.0) {
+              const double dp = (Sp - S0) / hp;
+              dS = (hp * dm + hm * dp) / (hm + hp);
+              ddS = (hp / hm - hm / hp) / (hm + hp);
+            } else {
+              dS = dm;
+              ddS = 1.0 / hm;
+            }
+            double Sc = S0 - 0.5 * hm * dS;
+            /* dSc/dS0 for Lambda*: the control point's dependence on S0, limited to
+               [0, 1]; where the control point is clamped, that of the bound it took */
+            double dSc = 1.0 - 0.5 * hm * ddS;
+            if (dSc < 0.0) dSc = 0.0;
+            if (dSc > 1.0) dSc = 1.0;
+            const double lo = Sm < S0 ? Sm : S0, hi = Sm < S0 ? S0 : Sm;
+            if (Sc < lo) { Sc = lo; dSc = (lo == S0) ? 1.0 : 0.0; }
+            else if (Sc > hi) { Sc = hi; dSc = (hi == S0) ? 1.0 : 0.0; }
+            double w3[3];
+            orc_bezier_weights(hm, w3);
+            I0 = Im * exp(-hm) + w3[0] * Sm + w3[1] * S0 + w3[2] * Sc;
+            dI0 = w3[1] + w3[2] * dSc;
+          }
+          I[ci] = I0;
+          accJ[ci] += w * I0;
+          accL[ci] += w * dI0;
+          if (want_mom) {
+            for (int a = 0; a < 3; ++a) accH[a * C + ci] += w * I0 * m[a];
+            accK[0 * C + ci] += w * I0 * m[0] * m[0];
+            accK[1 * C + ci] += w * I0 * m[1] * m[1];
+            accK[2 * C + ci] += w * I0 * m[2] * m[2];
+            accK[3 * C + ci] += w * I0 * m[0] * m[1];
+            accK[4 * C + ci] += w * I0 * m[0] * m[2];
+            accK[5 * C + ci] += w * I0 * m[1] * m[2];
+          }
+          if (G_next) {
+            for (int a = 0; a < 3; ++a) {
+              if (g.bc_lo[a] != BC_PERIODIC) continue;
+              const int out = sgn[a] > 0 ? g.n[a] - 1 : 0;
+              if (c0[a] == out)
+                G_next[(long)k * g.gsize + g.goff[a] + face_index(&g, a, c0[0], c0[1], c0[2])] = I0;
+            }
+          }
+        }
+      }
+    }
+  }
+
+  for (long i = 0; i < C; ++i) {
+    double sJ = 0.0, sL = 0.0, sH[3] = {0, 0, 0}, sK[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < nthreads; ++t) {
+      const double *a = acc + (long)t * C * nacc;
+      sJ += a[i];
+      sL += a[C + i];
+      if (want_mom) {
+        for (int q = 0; q < 3; ++q) sH[q] += a[(2 + q) * C + i];
+        for (int q = 0; q < 6; ++q) sK[q] += a[(5 + q) * C + i];
+      }
+    }
+    J[i] = sJ;
+    if (lstar) lstar[i] = sL;
+    if (H) for (int q = 0; q < 3; ++q) H[q * C + i] = sH[q];
+    if (K) for (int q = 0; q < 6; ++q) K[q * C + i] = sK[q];
+  }
+  free(acc);
+  free(Iw);
+  return 0;
+}
+
 /* Number of OpenMP threads available (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP
