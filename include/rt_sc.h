@@ -152,6 +152,26 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
 rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, double *Q,
                      int on_device, const rt_solve_opts *opts);
 
+/* Order of the interpolation on the crossed face (Sec. 3.3).
+ *   RT_INTERP_LINEAR (default): bilinear I-, S-, chi- on the upwind face and S
+ *     linear along the segment (Eq. 20 with Psi+ = 0).
+ *   RT_INTERP_QUADRATIC: the second-order option -- I-, S-, chi- (and S+, chi+ at
+ *     the downwind point, the same offsets on the next plane) from the 3 x 3 face
+ *     vertices around the cell's column, along the lower canonical face axis
+ *     first, each time the parabola through three values clamped to the two that
+ *     bracket the point (no new extrema; exact for monotone quadratic data); S
+ *     along the segment the quadratic Bezier curve whose control value
+ *     S0 - dtau-/2 S'(tau0), S' from the parabola through S-, S0, S+, is clamped
+ *     to [min(S-, S0), max(S-, S0)] where that parabola would overshoot.
+ *     Lambda* is the local weight of S0 (the control value's dependence limited
+ *     to [0, 1]); the clamps make it depend on S, so ALI solves take it from
+ *     every formal solution, and RT_PREC_MIXED grids sweep S itself, not its
+ *     increments (float32 rounding then limits tol to about 1e-7 / eps).  Uses
+ *     the pipelined sweep (variant 3) only.
+ * Replans the sweep.  Errors: RT_ERR_ARG for another value. */
+typedef enum { RT_INTERP_LINEAR = 1, RT_INTERP_QUADRATIC = 2 } rt_interp;
+rt_status rt_set_interpolation(rt_grid g, int order);
+
 /* Form of the heating rate Q returned by rt_moments (Sec. 4).
  *   RT_HEAT_INTEGRAL:     Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu), chi_abs = eps chi.
  *   RT_HEAT_DIFFERENTIAL: Q = -4 pi sum_nu w_nu div H_nu, div H from centred

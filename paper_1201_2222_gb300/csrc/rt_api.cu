@@ -302,6 +302,9 @@ struct rt_grid_s {
   size_t tmp2_n = 0;
   double prec_limit = 1e-4;
   int heat_form = RT_HEAT_INTEGRAL;   // form of Q returned by rt_moments (Sec. 4)
+  int interp = RT_INTERP_LINEAR;      // order of the face interpolation (Sec. 3.3)
+  void *Opart = nullptr;              // second-order sweeps: group partials of 1 - Lambda*
+  size_t opart_groups = 0;
 };
 
 namespace {
@@ -370,8 +373,11 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
     const int Nu = g->d.n[cax[0]];
     const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
     if (variant == 3) {
+      // two intensity planes per ray; chi and S rings of 3 planes (4 for the
+      // second-order sweep, which also reads the downwind plane)
       const size_t W = (size_t)rtk::pipe_row_len(Nu, rtk::kSweepSeg);
-      sm = std::max(sm, (size_t)(2 * slots + 6) * (Rmax + 2) * W * g->tsize);
+      const size_t ring = g->interp == RT_INTERP_QUADRATIC ? 8 : 6;
+      sm = std::max(sm, (size_t)(2 * slots + ring) * (Rmax + 2) * W * g->tsize);
       th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
     } else if (variant == 2) {
       const size_t W = (size_t)Nu + 2 + rtk::kSweepSeg;
@@ -436,6 +442,10 @@ void make_groups(rt_grid g, int apg, std::vector<GroupParam> &groups, std::vecto
 }
 
 int resident_clusters(rt_grid g, int variant, int amax, int C, int threads, size_t smem) {
+  if (g->interp == RT_INTERP_QUADRATIC) {
+    if (g->desc.prec == RT_PREC_FP64) return rtk::quad_max_active_clusters<double>(amax, C, threads, smem);
+    return rtk::quad_max_active_clusters<float>(amax, C, threads, smem);
+  }
   const int kind = variant == 3 ? 3 : (variant == 2 ? 1 : 0);
   if (g->desc.prec == RT_PREC_FP64) return rtk::sweep_max_active_clusters<double>(kind, amax, C, threads, smem);
   return rtk::sweep_max_active_clusters<float>(kind, amax, C, threads, smem);
@@ -455,6 +465,7 @@ void plan_groups(rt_grid g) {
   }
   int variant = g->req_variant;
   if (variant == 0) variant = g->desc.prec == RT_PREC_FP64 ? 1 : 3;
+  if (g->interp == RT_INTERP_QUADRATIC) variant = 3;   // the second-order sweep is pipelined only
   const int Cmax = std::min(16, minNv);
   double best = 1e300;
   int bapg = 1, bC = 1;
@@ -559,6 +570,12 @@ rt_status upload_plan(rt_grid g) {
     CU(cudaMalloc(&g->Jpart, need * (size_t)N_of(g) * sizeof(T)));
     g->jpart_groups = need;
   }
+  if (g->interp == RT_INTERP_QUADRATIC && need > g->opart_groups) {
+    if (g->Opart) cudaFree(g->Opart);
+    g->Opart = nullptr;
+    CU(cudaMalloc(&g->Opart, need * (size_t)N_of(g) * sizeof(T)));
+    g->opart_groups = need;
+  }
   return RT_OK;
 }
 
@@ -659,6 +676,7 @@ rtk::SweepArgs<T> sweep_args(rt_grid g) {
   A.grp = g->grp;
   A.ngroups = (int)g->groups.size();
   A.Jpart = (T *)g->Jpart;
+  A.Opart = g->interp == RT_INTERP_QUADRATIC ? (T *)g->Opart : nullptr;
   A.Mpart = (T *)g->Mpart;
   A.st = g->st;
   A.parity_offset = 0;
@@ -681,7 +699,9 @@ rt_status enqueue_sweep(rt_grid g, rtk::SweepArgs<T> &A, bool moments, cudaStrea
     CU(cudaEventCreate(&p.b));
     CU(cudaEventRecord(p.a, s));
   }
-  if (g->variant == 3) {
+  if (g->interp == RT_INTERP_QUADRATIC) {
+    CU(rtk::launch_sweep_quad<T>(A, g->amax, moments, g->threads, g->smem, s));
+  } else if (g->variant == 3) {
     CU(rtk::launch_sweep_pipe<T>(A, g->amax, moments, g->threads, g->smem, s));
   } else if (g->variant == 2) {
     CU(rtk::launch_sweep_tiled<T>(A, g->amax, moments, g->threads, g->smem, s));
@@ -728,7 +748,9 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   g->launches++;
   // The mixed path sweeps increments after the first formal solution so that
   // float32 rounding scales with the update, not with S (J accumulated in FP64).
-  const int incremental = g->desc.prec == RT_PREC_MIXED ? 1 : 0;
+  // (the second-order sweep is nonlinear in S -- its clamps -- so it never
+  // sweeps increments; it also brings its own Lambda* every iteration)
+  const int incremental = (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR) ? 1 : 0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
   A.incremental = incremental;
   rtk::AliArgs<T> L{};
@@ -738,6 +760,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   L.eps = g->eps;
   L.B = g->B;
   L.iden = g->iden;
+  L.Opart = g->interp == RT_INTERP_QUADRATIC ? (const T *)g->Opart : nullptr;
   L.S64 = g->S;
   L.Sfs = g->Sfs;
   L.J64 = g->J;
@@ -801,6 +824,10 @@ rt_status formal_once(rt_grid g, cudaStream_t s) {
   rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
   if (r != RT_OK) return r;
   CU(rtk::launch_reduce_J<T>(g->d, (int)g->groups.size(), (const T *)g->Jpart, g->J, s));
+  if (g->interp == RT_INTERP_QUADRATIC) {   // this solution's Lambda*
+    CU(rtk::launch_quad_lstar<T>(g->d, (int)g->groups.size(), (const T *)g->Opart, g->lstar, s));
+    g->launches++;
+  }
   CU(rtk::launch_state_op(g->st, 1, 0, 0.0, 0, s));
   g->launches += 2;
   if (g->timing) {
@@ -900,6 +927,7 @@ rt_status plan_precision(rt_grid g) {
     d.nfreq = (int)ill.size();
     rt_status r = rt_create_grid(&d, &g->sub64);
     if (r != RT_OK) return r;
+    if ((r = rt_set_interpolation(g->sub64, g->interp)) != RT_OK) return r;
     g->bins64 = ill;
   }
   const size_t C = (size_t)g->d.cells, m = ill.size();
@@ -1047,7 +1075,7 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->Gd[0], g->Gd[1],
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
                   g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
-                  g->Jpart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp};
+                  g->Jpart, g->Opart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (g->own) cudaStreamDestroy(g->own);
@@ -1323,6 +1351,19 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
   return RT_OK;
 }
 
+rt_status rt_set_interpolation(rt_grid g, int order) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (order != RT_INTERP_LINEAR && order != RT_INTERP_QUADRATIC)
+    return fail(RT_ERR_ARG, "interpolation order must be 1 (linear) or 2 (quadratic), not %d", order);
+  if (order == g->interp) return RT_OK;
+  g->interp = order;
+  plan_groups(g);
+  rt_status r = upload_plan_any(g);
+  if (r != RT_OK) return r;
+  if (g->sub64) return rt_set_interpolation(g->sub64, order);
+  return RT_OK;
+}
+
 rt_status rt_set_heating_form(rt_grid g, int form) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   if (form != RT_HEAT_INTEGRAL && form != RT_HEAT_DIFFERENTIAL && form != RT_HEAT_SWITCH)
@@ -1339,7 +1380,7 @@ rt_status rt_enable_timing(rt_grid g, int enable) {
 
 // Plans chosen by rt_autotune, keyed by problem shape (process-wide cache).
 struct TuneKey {
-  int n[3], nf, n_mu, prec, bc[6];
+  int n[3], nf, n_mu, prec, bc[6], interp;
   bool operator==(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
 };
 struct TuneVal {
@@ -1359,6 +1400,7 @@ TuneKey tune_key(rt_grid g) {
   k.nf = g->d.nf;
   k.n_mu = g->desc.n_mu;
   k.prec = g->desc.prec;
+  k.interp = g->interp;
   return k;
 }
 
@@ -1390,7 +1432,8 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best_ms = 1e300;
-    for (int vi = 0; vi < 3; ++vi) {
+    const int nvar = g->interp == RT_INTERP_QUADRATIC ? 1 : 3;   // second order: pipelined only
+    for (int vi = 0; vi < nvar; ++vi) {
       for (int ai = 0; ai < 7; ++ai) {
         for (int ci = 0; ci < 9; ++ci) {
           if (clusters[ci] > minNv) continue;

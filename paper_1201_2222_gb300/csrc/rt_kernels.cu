@@ -18,27 +18,13 @@
 #include <cstdio>
 
 #include "rt_common.cuh"
+#include "rt_device.cuh"
 #include "rt_kernels.h"
 
 namespace cg = cooperative_groups;
 
 namespace rtk {
 
-#ifdef RT_DEBUG_BOUNDS
-// Debug builds: every indexed access is checked; a bad index is recorded in the
-// solve state and replaced by 0 so that no access leaves its buffer.
-__device__ __forceinline__ long long chk(long long i, long long n, SolveState *st, int code) {
-  if (i < 0 || i >= n) {
-    atomicCAS(&st->err, 0, code);
-    st->err_info = (int)i;
-    return 0;
-  }
-  return i;
-}
-#define RT_IDX(i, n, code) chk((i), (n), A.st, (code))
-#else
-#define RT_IDX(i, n, code) (i)
-#endif
 
 // ----------------------------------------------------------------- segment weights
 // Linear short-characteristics weights for one segment of optical depth dtau:
@@ -73,81 +59,6 @@ __device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0
 
 // ------------------------------------------------------------------------ sweep
 
-
-// Canonical axis a's entry of a 3-vector, by selects (a runtime index into a
-// register array would put the array in local memory).
-__device__ __forceinline__ int pick3(const int (&x)[3], int a) { return a == 0 ? x[0] : (a == 1 ? x[1] : x[2]); }
-__device__ __forceinline__ int pick3(int x0, int x1, int x2, int a) { return a == 0 ? x0 : (a == 1 ? x1 : x2); }
-
-// Address of the intensity at an upwind vertex outside the domain (plane
-// coordinates u, v, w), or nullptr when it is zero (fixed inflow in an
-// incremental sweep, whose inflow does not change between formal solutions).
-// If any out-of-range axis is non-periodic: the inflow intensity of the first
-// such face in the order z, y, x.  Otherwise the image cell's intensity from the
-// previous formal solution (lagged periodic ghost), read from the face buffer of
-// the first out-of-range axis in the same order.
-template <typename T>
-__device__ __forceinline__ const T *ghost_ptr(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
-                                              int Nw, int f, int angle, const T *Gp, bool inc, int u,
-                                              int v, int w) {
-  // canonical coordinates, picked from the plane coordinates by selects
-  const int c0 = cax[0] == 0 ? u : (cax[1] == 0 ? v : w);
-  const int c1 = cax[0] == 1 ? u : (cax[1] == 1 ? v : w);
-  const int c2 = cax[0] == 2 ? u : (cax[1] == 2 ? v : w);
-  const int n0 = A.d.n[0], n1 = A.d.n[1], n2 = A.d.n[2];
-  const bool p0 = A.d.periodic[0], p1 = A.d.periodic[1], p2 = A.d.periodic[2];
-  const bool o0 = c0 < 0 || c0 >= n0, o1 = c1 < 0 || c1 >= n1, o2 = c2 < 0 || c2 >= n2;
-  const int m0 = !o0 ? c0 : (p0 ? (c0 < 0 ? c0 + n0 : c0 - n0) : (c0 < 0 ? 0 : n0 - 1));
-  const int m1 = !o1 ? c1 : (p1 ? (c1 < 0 ? c1 + n1 : c1 - n1) : (c1 < 0 ? 0 : n1 - 1));
-  const int m2 = !o2 ? c2 : (p2 ? (c2 < 0 ? c2 + n2 : c2 - n2) : (c2 < 0 ? 0 : n2 - 1));
-  int fax = -1, fside = 0;   // first non-periodic out-of-range axis in the order z, y, x
-  if (o0 && !p0) { fax = 0; fside = c0 >= n0; }
-  if (o1 && !p1) { fax = 1; fside = c1 >= n1; }
-  if (o2 && !p2) { fax = 2; fside = c2 >= n2; }
-  if (fax >= 0) {
-    if (inc) return nullptr;
-    // face cell index: x face [z][y], y face [z][x], z face [y][x]
-    const long long fc = fax == 0 ? (long long)m2 * n1 + m1
-                                  : (fax == 1 ? (long long)m2 * n0 + m0 : (long long)m1 * n0 + m0);
-    const long long fsz = fax == 0 ? A.d.face[0] : (fax == 1 ? A.d.face[1] : A.d.face[2]);
-    const long long idx = ((long long)f * A.na + angle) * fsz + fc;
-    const T *base = fax == 0 ? A.Ibc[fside] : (fax == 1 ? A.Ibc[2 + fside] : A.Ibc[4 + fside]);
-    return base + RT_IDX(idx, (long long)A.d.nf * A.na * fsz, 41);
-  }
-  const int ax = o2 ? 2 : (o1 ? 1 : 0);
-  const int mu_ = pick3(m0, m1, m2, cax[0]), mv_ = pick3(m0, m1, m2, cax[1]), mw_ = pick3(m0, m1, m2, cax[2]);
-  const long long gb = ((long long)f * A.na + angle) * A.d.gsize;
-  long long off;
-  if (ax == cax[2]) off = (long long)mv_ * Nu + mu_;
-  else if (ax == cax[0]) off = (long long)Nu * Nv + (long long)mw_ * Nv + mv_;
-  else off = (long long)Nu * Nv + (long long)Nw * Nv + (long long)mw_ * Nu + mu_;
-  return Gp + RT_IDX(gb + off, (long long)A.d.nf * A.na * A.d.gsize, 42);
-}
-
-// Value of the intensity at an out-of-domain upwind vertex (see ghost_ptr).
-template <typename T>
-__device__ __forceinline__ T ghost_I(const SweepArgs<T> &A, const int cax[3], int Nu, int Nv,
-                                     int Nw, int f, int angle, const T *Gp, bool inc, int u, int v,
-                                     int w) {
-  const T *q = ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, angle, Gp, inc, u, v, w);
-  return q ? *q : T(0);
-}
-
-// Outflow intensity onto a periodic face for the next formal solution.  Full
-// solutions store I; the first one of an incremental solve also stores its
-// change against the ghost it replaces; incremental ones store the change and
-// advance the full ghost by it.
-template <typename T>
-__device__ __forceinline__ void ghost_store(const T *Gp, T *Gn, T *Gdn, long long off, T I0, bool inc,
-                                            bool emit) {
-  if (inc) {
-    Gdn[off] = I0;
-    Gn[off] = Gp[off] + I0;
-  } else {
-    if (emit) Gdn[off] = I0 - Gp[off];
-    Gn[off] = I0;
-  }
-}
 
 // One sweep group (rays sharing the crossed-face axis a and sign(mu_a)) for one
 // frequency.  The plane normal to a is split into C strips of rows (v) over the C
@@ -600,38 +511,6 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_tiled_kernel(
 //  * rows of neighbouring strips are read directly from their CTAs' shared
 //    memory (DSMEM), so each plane costs one cluster barrier.
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src));
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src));
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
-  if (sizeof(T) == 4) cp_async4(dst, src);
-  else cp_async8(dst, src);
-}
-
-template <typename T>
-__device__ __forceinline__ void ghost_async(T *dst, const T *src) {
-  if (src) cp_async_elem(dst, src);
-  else *dst = T(0);
-}
-
-constexpr int kPipeX0 = 4;   // first interior column of a staged row (16-byte aligned)
-
-// A compile-time sign of mu_u or mu_v (selects the interpolation stencil).
-template <int V>
-using SignC = std::integral_constant<int, V>;
 
 template <typename T, int SEG, int SU, int SV>
 __device__ __forceinline__ void pipe_update(const AngleParam<T> &p, const T *__restrict__ Irow,
@@ -1208,7 +1087,15 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
         snew = A.incremental ? T(0) : (T)A.S64[i];
       } else {
         const double S = A.S64[i], e = A.eps[i];
-        const double dS = ((1.0 - e) * J + e * A.B[i] - S) * A.iden[i];
+        double iden;
+        if (A.Opart) {   // second-order sweeps: 1 - Lambda* of this formal solution
+          double om = 0.0;
+          for (int p = 0; p < A.ngroups_per_f; ++p) om += (double)A.Opart[(long long)p * A.d.nf * cells + i];
+          iden = 1.0 / (e + (1.0 - e) * om);
+        } else {
+          iden = A.iden[i];
+        }
+        const double dS = ((1.0 - e) * J + e * A.B[i] - S) * iden;
         const double Sn = S + dS;
         A.S64[i] = Sn;
         A.Sfs[i] = S;

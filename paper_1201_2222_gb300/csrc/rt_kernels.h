@@ -20,6 +20,7 @@ struct SweepArgs {
   const GroupParam *grp;
   int ngroups;               // groups per frequency
   T *Jpart;                  // [ngroups][nf][cells] canonical
+  T *Opart;                  // second-order sweeps: sum_k w_k (1 - dI0/dS0) per group, same layout
   T *Mpart;                  // [ngroups][9][nf][cells] (moments launches only)
   SolveState *st;
   int parity_offset;         // ghost parity = (st->fs_count + parity_offset) & 1
@@ -37,6 +38,8 @@ struct AliArgs {
   const T *Jpart;
   const double *eps, *B;
   const double *iden;        // 1 / [eps + (1 - eps)(1 - Lambda*)], fixed for a medium
+  const T *Opart;            // second-order sweeps: group partials of 1 - Lambda* of this
+                             // formal solution (used instead of iden; NULL = linear)
   double *S64, *Sfs, *J64, *Jprev;
   T *SP[3];                  // permuted sweep copies of S to refresh (NULL = axis unused)
   SolveState *st;
@@ -60,6 +63,16 @@ __host__ __device__ inline int pipe_row_len(int Nu, int seg) { return ((4 + Nu +
 template <typename T>
 cudaError_t launch_sweep_pipe(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                               cudaStream_t s);
+// second-order sweep (rt_quad.cu): monotonic quadratic face interpolation and
+// Bezier-controlled segment integration, chi/S staged in a four-plane ring
+template <typename T>
+cudaError_t launch_sweep_quad(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
+                              cudaStream_t s);
+template <typename T>
+int quad_max_active_clusters(int amax, int cluster, int threads, size_t smem);
+// Lambda* of a second-order formal solution: 1 - sum over groups of Opart
+template <typename T>
+cudaError_t launch_quad_lstar(const Dims &d, int ngroups, const T *Opart, double *lstar, cudaStream_t s);
 // clusters of one sweep configuration that can be resident at once (-1 on error)
 template <typename T>
 int sweep_max_active_clusters(int tiled, int amax, int cluster, int threads, size_t smem);

@@ -18,6 +18,7 @@ from . import build as _build
 PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 HEAT_INTEGRAL, HEAT_DIFFERENTIAL, HEAT_SWITCH = 0, 1, 2
+INTERP_LINEAR, INTERP_QUADRATIC = 1, 2
 
 RT_OK = 0
 RT_ERR_ARG = -1
@@ -69,6 +70,7 @@ _SIGS = {
     "rt_get_S": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts)]),
     "rt_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_set_heating_form": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rt_set_interpolation": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(rt_stats)]),
     "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rt_get_sweep_plan": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
@@ -305,6 +307,12 @@ class Grid:
         o = self._opts(on_device=on_device)
         _check(load().rt_get_S(self._h, self._ptr(S), 1 if on_device else 0, ctypes.byref(o)))
         return S
+
+    def set_interpolation(self, order):
+        """Face interpolation: INTERP_LINEAR / "linear" or INTERP_QUADRATIC / "quadratic"."""
+        if isinstance(order, str):
+            order = {"linear": INTERP_LINEAR, "quadratic": INTERP_QUADRATIC}[order.lower()]
+        _check(load().rt_set_interpolation(self._h, int(order)))
 
     def set_heating_form(self, form):
         """Form of Q returned by ``moments``: HEAT_INTEGRAL, HEAT_DIFFERENTIAL or
