@@ -298,6 +298,26 @@ def run_gpu(args):
                 "updates_per_s": p.cells * p.n_angles * p.nf * it64 / t64}
         g64.close()
 
+    # the second-order option (quadratic face interpolation): formal-solution rate
+    # on the same medium, mixed precision, its own tuned plan
+    quad = None
+    if not args.skip_quad:
+        gq = rt.Grid.from_problem(p, prec=rt.MIXED)
+        gq.set_interpolation(rt.INTERP_QUADRATIC)
+        gq.set_opacity_source(chi, eps, B, fw)
+        gq.autotune()
+        gq.enable_timing(True)
+        gq.formal_solve(None)
+        qms = []
+        for _ in range(5):
+            gq.formal_solve(None)
+            qms.append(gq.stats()["sweep_ms"])
+        qms.sort()
+        quad = {"kernel": "sc_sweep_quad_kernel<float>", "sweep_ms_median": qms[len(qms) // 2],
+                "updates_per_s": p.cells * p.n_angles * p.nf / (qms[len(qms) // 2] / 1e3),
+                "plan": gq.sweep_plan()}
+        gq.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -318,6 +338,7 @@ def run_gpu(args):
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
         "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
         "fp64_path": fp64,
+        "quadratic_path": quad,
         "sweep_plan": g.sweep_plan(),
         "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[g.sweep_plan()["variant"]],
                      "achieved": achieved,
@@ -346,6 +367,8 @@ def run_profile(args):
     build.build()
     p = workload()
     g = rt.Grid.from_problem(p, prec=rt.FP64 if args.fp64 else rt.MIXED)
+    if args.quadratic:
+        g.set_interpolation(rt.INTERP_QUADRATIC)
     g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
     if args.plan:
         v, apg, c = (int(x) for x in args.plan.split(","))
@@ -358,6 +381,52 @@ def run_profile(args):
     return 0
 
 
+def run_serve(args):
+    """A sample of the mixed-size request stream through the request server:
+    Poisson arrivals at ``--rate`` requests/s, ``--workers`` solves in flight;
+    prints one JSON line with p50/p99 latency (arrival to result) and throughput."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1201_2222_gb300 import build, rt, workloads as W
+    build.build()
+    stream = W.serving_stream(args.serve, seed=7, rate=args.rate)
+    # bounded sample: eps clipped to >= 1e-3 (below about 6e-4 every frequency bin
+    # switches to FP64 sweeps and one 128^3 x 16-bin request takes many minutes)
+    stream = [dict(d, eps=max(d["eps"], 1e-3)) for d in stream]
+    probs = [W.build_request(d) for d in stream]
+    srv = rt.Server(workers=args.workers)
+    t0 = time.perf_counter()
+    ids = []
+    for d, p in zip(stream, probs):
+        wait = d["t_arrival"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append((srv.submit(p, prec=rt.MIXED, max_iter=20000), time.perf_counter() - t0, p))
+    lat, upd, iters, bad = [], 0, [], 0
+    for rid, t_sub, p in ids:
+        info = srv.wait(rid, timeout=3600)
+        srv.fetch(rid, raise_on_fail=False)
+        print(f"request {rid}: {p.name} iters {info['iters']} status {info['status']} "
+              f"queue {info['queue_ms']:.0f} ms solve {info['solve_ms']:.0f} ms", file=sys.stderr, flush=True)
+        bad += info["status"] != rt.RT_OK
+        lat.append(info["queue_ms"] + info["solve_ms"])
+        upd += p.cells * p.n_angles * p.nf * info["iters"]
+        iters.append(info["iters"])
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    line = {"mode": "serve", "requests": len(ids), "workers": args.workers, "rate_per_s": args.rate,
+            "metric": METRIC, "value": upd / wall, "unit": UNIT, "solves_per_s": len(ids) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "failed": int(bad), "iters_median": float(np.median(iters)), "wall_s": wall,
+            "data": "synthetic", "dtype": "f32+f64",
+            "config": {"workload": "serving stream sample: sizes 32^3..128^3 and 512x512 2D, "
+                                   "1/4/16 frequencies, 24/48/80 rays, eps log-uniform in [1e-4, 1] "
+                                   "clipped to >= 1e-3"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,12 +435,19 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU comparison solves")
+    ap.add_argument("--skip-quad", action="store_true", help="omit the second-order formal-solution rate")
     ap.add_argument("--profile", action="store_true", help="one short solve for profilers")
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
+    ap.add_argument("--quadratic", action="store_true", help="with --profile: the second-order sweep")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
     ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster instead of autotuning")
+    ap.add_argument("--serve", type=int, default=0, help="run N requests of the serving stream instead")
+    ap.add_argument("--rate", type=float, default=2.0, help="with --serve: arrivals per second")
+    ap.add_argument("--workers", type=int, default=4, help="with --serve: solves in flight")
     args = ap.parse_args(argv)
+    if args.serve:
+        return run_serve(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -39,7 +39,7 @@ typedef enum {
   RT_ERR_OOM = -2,            /* device allocation failed */
   RT_ERR_CUDA = -3,           /* a CUDA call failed (message has the CUDA error) */
   RT_ERR_NOT_CONVERGED = -4,  /* max_iter formal solutions without meeting tol */
-  RT_ERR_TIMEOUT = -5,        /* reserved: a bounded device-side wait gave up */
+  RT_ERR_TIMEOUT = -5,        /* a wait gave up (rt_wait) */
   RT_ERR_STATE = -6           /* call out of order (e.g. solve before set_opacity_source) */
 } rt_status;
 
@@ -264,6 +264,58 @@ rt_status rt_autotune(rt_grid g, int *plan_out);
 #define RT_NOALLOC_SCRATCH_BYTES (64ULL << 20)
 rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const double *chi, const double *S,
                                   const double *B, double *J_out, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ * A request server (no counterpart in the paper: the library's serving layer).
+ * Submitted ALI solves queue in arrival order; each of the server's worker
+ * threads takes the oldest one as soon as the estimated device footprint of the
+ * solves already running plus the new one fits the server's budget (a solve
+ * larger than the budget runs when nothing else does), creates its grid on the
+ * worker's own CUDA stream, solves, takes J, S and Q back to host memory and
+ * frees the grid.  Solves on different workers overlap on the GPU; each result
+ * is the same as that of the same solve run alone (deterministic kernels and a
+ * plan that depends on the problem only).  All calls are thread-safe. */
+typedef struct rt_server_s *rt_server;
+typedef struct {
+  long long device_bytes;   /* admission budget; <= 0: 80 % of the free device memory */
+  int workers;              /* solves in flight at most (>= 1) */
+} rt_server_opts;
+typedef struct {
+  rt_grid_desc desc;
+  int interp;               /* RT_INTERP_LINEAR / RT_INTERP_QUADRATIC (0 = linear) */
+  const double *chi, *eps, *B, *freq_w;   /* host arrays as for rt_set_opacity_source;
+                                             copied at submission (freq_w may be NULL: 1) */
+  double tol;
+  int max_iter;
+} rt_request;
+enum { RT_REQ_QUEUED = 0, RT_REQ_RUNNING = 1, RT_REQ_DONE = 2 };
+typedef struct {
+  int state;                /* RT_REQ_* */
+  int status;               /* the solve's rt_status once done */
+  int iters;
+  double resid;
+  double queue_ms;          /* submission to start */
+  double solve_ms;          /* start to done (grid set-up, solve, moments, copies) */
+  long long footprint;      /* estimated device bytes */
+} rt_request_info;
+
+/* Estimated device memory of a grid with this description (upper bound of the
+ * arrays it allocates, with the moments pass).  Errors: RT_ERR_ARG. */
+rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes);
+rt_status rt_server_create(const rt_server_opts *opts, rt_server *out);
+/* Waits for the running solves; queued ones are dropped. */
+rt_status rt_server_destroy(rt_server s);
+/* Copies the request's inputs and queues it.  Errors: RT_ERR_ARG (NULL or bad
+ * description; the medium itself is validated when the solve runs). */
+rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out);
+/* State of a request.  Errors: RT_ERR_ARG for an unknown id. */
+rt_status rt_poll(rt_server s, long long id, rt_request_info *info);
+/* Blocks until the request is done or timeout_s has passed (RT_ERR_TIMEOUT). */
+rt_status rt_wait(rt_server s, long long id, double timeout_s, rt_request_info *info);
+/* Copies the results of a finished request to host arrays (any may be NULL):
+ * J and S [nf][cells], Q [cells] (the integral form), and forgets the request.
+ * Returns the solve's status (RT_ERR_STATE if it is not done). */
+rt_status rt_fetch(rt_server s, long long id, double *J, double *S, double *Q);
 
 /* Message describing the last error on this thread (never NULL). */
 const char *rt_last_error(void);

@@ -1085,6 +1085,26 @@ rt_status rt_destroy_grid(rt_grid g) {
 
 int rt_num_angles(rt_grid g) { return g ? g->na : 0; }
 
+rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes) {
+  if (!desc || !bytes) return fail(RT_ERR_ARG, "rt_grid_footprint: NULL argument");
+  const rt_grid_desc &D = *desc;
+  if (D.nx < 1 || D.ny < 1 || D.nz < 1 || D.nfreq < 1) return fail(RT_ERR_ARG, "grid sizes and nfreq must be >= 1");
+  std::vector<double> m, q;
+  if (!level_symmetric(D.n_mu, D.nz == 1, m, q)) return fail(RT_ERR_ARG, "bad n_mu %d", D.n_mu);
+  const long long na = (long long)q.size();
+  const long long cells = (long long)D.nx * D.ny * D.nz, N = cells * D.nfreq;
+  const long long ts = D.prec == RT_PREC_FP64 ? 8 : 4;
+  const long long gsize = (long long)D.nx * D.ny + (long long)D.ny * D.nz + (long long)D.nx * D.nz;
+  const long long groups = (na + 1) / 2 + 6;   // the planner groups at least two rays where it can
+  long long b = 8 * N * 11                     // FP64 fields and state
+              + ts * N * 6                     // permuted chi, S copies
+              + 6 * D.nfreq * na * gsize * ts  // ghosts (two parities, increments) and inflow faces
+              + groups * N * ts * 11           // J, Lambda* and moment partials
+              + 8 * (16 * N + cells);          // moments outputs
+  *bytes = b;
+  return RT_OK;
+}
+
 int rt_angle_table(int n_mu, int two_d, double *mu, double *w) {
   std::vector<double> m, q;
   if (!level_symmetric(n_mu, two_d != 0, m, q)) {

@@ -16,6 +16,9 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "rt_common.cuh"
 #include "rt_device.cuh"
@@ -703,8 +706,13 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     for (int idx = threadIdx.x; idx < na * 2 * (R + 2); idx += blockDim.x) {
       const int a = idx / (2 * (R + 2)), r2 = idx - a * 2 * (R + 2);
       const int side = r2 / (R + 2), row = r2 - side * (R + 2);
-      ghost_async(Ibuf + RT_IDX(a * pb + row * W + (side ? kPipeX0 + Nu : kPipeX0 - 1), 2LL * ib, 47),
-                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, side ? Nu : -1, v0 - 1 + row, wsrc));
+      const int vv = v0 - 1 + row;
+      // a periodic u face with v inside the grid: the lagged ghost is the u-face
+      // entry (w, v) of the ray's block (the general lookup gives the same address)
+      const T *src = (perU && vv >= 0 && vv < Nv)
+                         ? Gsrc + ((long long)f * A.na + P[a].angle) * A.d.gsize + plane + (long long)wsrc * Nv + vv
+                         : ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, side ? Nu : -1, vv, wsrc);
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + (side ? kPipeX0 + Nu : kPipeX0 - 1), 2LL * ib, 47), src);
     }
     const int nrow = (v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0);   // rows outside the domain in v
     for (int idx = threadIdx.x; idx < na * nrow * Nu; idx += blockDim.x) {
@@ -712,8 +720,11 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       const int which = r2 / Nu, u = r2 - which * Nu;
       const bool lo = (v0 == 0) && (which == 0);
       const int row = lo ? 0 : R + 1;
-      ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 + u, 2LL * ib, 48),
-                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, u, lo ? -1 : Nv, wsrc));
+      // a periodic v face (u inside the grid): the v-face entry (w, u) of the ray's block
+      const T *src = perV ? Gsrc + ((long long)f * A.na + P[a].angle) * A.d.gsize + plane + (long long)Nw * Nv +
+                                (long long)wsrc * Nu + u
+                          : ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gsrc, inc, u, lo ? -1 : Nv, wsrc);
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 + u, 2LL * ib, 48), src);
     }
   };
 
@@ -1445,6 +1456,26 @@ __global__ void heating_kernel(Dims d, const double *fw, const double *chi, cons
 
 // ---------------------------------------------------------------- launchers
 
+cudaError_t prepare_kernel(const void *fn) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+  done.insert({fn, dev});
+  return cudaSuccess;
+}
+
 static int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -1456,12 +1487,8 @@ template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = sc_sweep_kernel<T, AMAX, MOM>;
   // set on every launch: occupancy queries for other plans change these attributes
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prepare_kernel((const void *)kern);
   if (e != cudaSuccess) return e;
-  if (A.cluster > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1481,12 +1508,8 @@ template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_tiled_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = sc_sweep_tiled_kernel<T, AMAX, MOM, kSweepSeg>;
   // set on every launch: occupancy queries for other plans change these attributes
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prepare_kernel((const void *)kern);
   if (e != cudaSuccess) return e;
-  if (A.cluster > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1513,12 +1536,8 @@ template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_pipe_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = pipe_vec_ok<T>(A.d) ? sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg, (sizeof(T) == 4)>
                                   : sc_sweep_pipe_kernel<T, AMAX, MOM, kSweepSeg, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prepare_kernel((const void *)kern);
   if (e != cudaSuccess) return e;
-  if (A.cluster > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1575,9 +1594,7 @@ static int max_active_t(int tiled, int cluster, int threads, size_t smem) {
   const void *kern = tiled == 3 ? (const void *)sc_sweep_pipe_kernel<T, AMAX, false, kSweepSeg, false>
                     : (tiled ? (const void *)sc_sweep_tiled_kernel<T, AMAX, false, kSweepSeg>
                              : (const void *)sc_sweep_kernel<T, AMAX, false>);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-  if (cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return -1;
+  if (prepare_kernel((const void *)kern) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cluster, 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);

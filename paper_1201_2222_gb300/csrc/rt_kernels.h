@@ -48,6 +48,12 @@ struct AliArgs {
   const unsigned char *fmask; // frequencies solved elsewhere (skipped; NULL = none)
 };
 
+// Sets, once per kernel and device, the largest dynamic shared memory the kernel
+// may request and permission for non-portable cluster sizes.  The values never
+// change afterwards, so launches and occupancy queries from several host threads
+// (the request server's workers) cannot race on them.
+cudaError_t prepare_kernel(const void *fn);
+
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                          cudaStream_t s);

@@ -238,8 +238,13 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_quad_kernel(c
     for (int idx = threadIdx.x; idx < na * 2 * (R + 2); idx += blockDim.x) {
       const int a = idx / (2 * (R + 2)), r2 = idx - a * 2 * (R + 2);
       const int side = r2 / (R + 2), row = r2 - side * (R + 2);
-      ghost_async(Ibuf + RT_IDX(a * pb + row * W + (side ? kPipeX0 + Nu : kPipeX0 - 1), 2LL * ib, 64),
-                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gp, false, side ? Nu : -1, v0 - 1 + row, wsrc));
+      const int vv = v0 - 1 + row;
+      // a periodic u face with v inside the grid: the lagged ghost is the u-face
+      // entry (w, v) of the ray's block (the general lookup gives the same address)
+      const T *src = (perU && vv >= 0 && vv < Nv)
+                         ? Gp + ((long long)f * A.na + P[a].angle) * A.d.gsize + plane + (long long)wsrc * Nv + vv
+                         : ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gp, false, side ? Nu : -1, vv, wsrc);
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + (side ? kPipeX0 + Nu : kPipeX0 - 1), 2LL * ib, 64), src);
     }
     const int nrow = (v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0);
     for (int idx = threadIdx.x; idx < na * nrow * Nu; idx += blockDim.x) {
@@ -247,8 +252,11 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_quad_kernel(c
       const int which = r2 / Nu, u = r2 - which * Nu;
       const bool lo = (v0 == 0) && (which == 0);
       const int row = lo ? 0 : R + 1;
-      ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 + u, 2LL * ib, 65),
-                  ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gp, false, u, lo ? -1 : Nv, wsrc));
+      // a periodic v face (u inside the grid): the v-face entry (w, u) of the ray's block
+      const T *src = perV ? Gp + ((long long)f * A.na + P[a].angle) * A.d.gsize + plane + (long long)Nw * Nv +
+                                (long long)wsrc * Nu + u
+                          : ghost_ptr<T>(A, cax, Nu, Nv, Nw, f, P[a].angle, Gp, false, u, lo ? -1 : Nv, wsrc);
+      ghost_async(Ibuf + RT_IDX(a * pb + row * W + kPipeX0 + u, 2LL * ib, 65), src);
     }
   };
   // outflow intensities of plane wp onto the periodic faces (as in the linear sweep)
@@ -423,12 +431,8 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_quad_kernel(c
 template <typename T, int AMAX, bool MOM>
 static cudaError_t launch_quad_t(const SweepArgs<T> &A, int threads, size_t smem, cudaStream_t s) {
   auto kern = sc_sweep_quad_kernel<T, AMAX, MOM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = prepare_kernel((const void *)kern);
   if (e != cudaSuccess) return e;
-  if (A.cluster > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(A.cluster * A.ngroups * A.d.nf), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -459,9 +463,7 @@ cudaError_t launch_sweep_quad(const SweepArgs<T> &A, int amax, bool moments, int
 template <typename T, int AMAX>
 static int quad_clusters_t(int cluster, int threads, size_t smem) {
   auto kern = sc_sweep_quad_kernel<T, AMAX, false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-  if (cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return -1;
+  if (prepare_kernel((const void *)kern) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cluster, 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);

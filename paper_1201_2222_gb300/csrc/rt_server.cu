@@ -1,0 +1,237 @@
+// Request server: queued ALI solves on worker threads, admitted by estimated
+// device footprint, each on its own grid and CUDA stream (see rt_sc.h).  Host
+// code only; it drives the grids through the library's public C API.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rt_sc.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+  long long id = 0;
+  rt_grid_desc desc{};
+  int interp = RT_INTERP_LINEAR;
+  std::vector<double> chi, eps, B, fw;
+  double tol = 1e-6;
+  int max_iter = 1000;
+  long long footprint = 0;
+  int state = RT_REQ_QUEUED;
+  int status = RT_OK;
+  int iters = 0;
+  double resid = 0.0;
+  Clock::time_point t_submit, t_start, t_done;
+  std::vector<double> J, S, Q;
+};
+
+}  // namespace
+
+struct rt_server_s {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request *> queue;
+  std::unordered_map<long long, Request *> reqs;
+  long long budget = 0;
+  long long resident = 0;   // footprints of the running solves
+  int device = 0;
+  bool stop = false;
+  long long next_id = 1;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// One solve, on the calling worker thread (its grid has its own stream).
+void run_solve(Request *r, int device) {
+  cudaSetDevice(device);
+  rt_grid g = nullptr;
+  rt_status st = rt_create_grid(&r->desc, &g);
+  if (st == RT_OK && r->interp != RT_INTERP_LINEAR) st = rt_set_interpolation(g, r->interp);
+  if (st == RT_OK)
+    st = rt_set_opacity_source(g, r->chi.data(), r->eps.data(), r->B.data(), r->fw.data(), 0);
+  int iters = 0;
+  double resid = 0.0;
+  if (st == RT_OK) {
+    rt_solve_opts o{};
+    o.tol = r->tol;
+    o.max_iter = r->max_iter;
+    st = rt_ali_solve(g, nullptr, 0, &o, &iters, &resid);
+  }
+  if (st == RT_OK || st == RT_ERR_NOT_CONVERGED) {
+    const size_t N = r->chi.size(), C = N / (size_t)r->desc.nfreq;
+    r->J.resize(N);
+    r->S.resize(N);
+    r->Q.resize(C);
+    rt_status s2 = rt_moments(g, r->J.data(), nullptr, nullptr, nullptr, r->Q.data(), 0, nullptr);
+    if (s2 == RT_OK) s2 = rt_get_S(g, r->S.data(), 0, nullptr);
+    if (s2 != RT_OK) st = s2;
+  }
+  if (g) rt_destroy_grid(g);
+  r->status = st;
+  r->iters = iters;
+  r->resid = resid;
+}
+
+void worker_loop(rt_server s) {
+  for (;;) {
+    Request *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] {
+        if (s->stop) return true;
+        if (s->queue.empty()) return false;
+        const long long fp = s->queue.front()->footprint;
+        return s->resident == 0 || s->resident + fp <= s->budget;
+      });
+      if (s->stop) return;
+      r = s->queue.front();
+      s->queue.pop_front();
+      s->resident += r->footprint;
+      r->state = RT_REQ_RUNNING;
+      r->t_start = Clock::now();
+    }
+    run_solve(r, s->device);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->resident -= r->footprint;
+      r->state = RT_REQ_DONE;
+      r->t_done = Clock::now();
+    }
+    s->cv.notify_all();
+  }
+}
+
+void fill_info(const Request *r, rt_request_info *info) {
+  if (!info) return;
+  info->state = r->state;
+  info->status = r->status;
+  info->iters = r->iters;
+  info->resid = r->resid;
+  const Clock::time_point now = Clock::now();
+  info->queue_ms = ms_between(r->t_submit, r->state == RT_REQ_QUEUED ? now : r->t_start);
+  info->solve_ms = r->state == RT_REQ_QUEUED ? 0.0 : ms_between(r->t_start, r->state == RT_REQ_DONE ? r->t_done : now);
+  info->footprint = r->footprint;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
+  if (!opts || !out || opts->workers < 1) return RT_ERR_ARG;
+  *out = nullptr;
+  rt_server s = new rt_server_s();
+  cudaGetDevice(&s->device);
+  s->budget = opts->device_bytes;
+  if (s->budget <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete s;
+      return RT_ERR_CUDA;
+    }
+    s->budget = (long long)(0.8 * (double)fr);
+  }
+  for (int i = 0; i < opts->workers; ++i) s->workers.emplace_back(worker_loop, s);
+  *out = s;
+  return RT_OK;
+}
+
+rt_status rt_server_destroy(rt_server s) {
+  if (!s) return RT_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  for (auto &t : s->workers) t.join();
+  for (auto &kv : s->reqs) delete kv.second;
+  delete s;
+  return RT_OK;
+}
+
+rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
+  if (!s || !req || !id_out || !req->chi || !req->eps || !req->B) return RT_ERR_ARG;
+  long long fp = 0;
+  rt_status st = rt_grid_footprint(&req->desc, &fp);
+  if (st != RT_OK) return st;
+  if (req->interp != 0 && req->interp != RT_INTERP_LINEAR && req->interp != RT_INTERP_QUADRATIC) return RT_ERR_ARG;
+  Request *r = new Request();
+  r->desc = req->desc;
+  r->interp = req->interp == 0 ? RT_INTERP_LINEAR : req->interp;
+  const size_t N = (size_t)req->desc.nx * req->desc.ny * req->desc.nz * req->desc.nfreq;
+  r->chi.assign(req->chi, req->chi + N);
+  r->eps.assign(req->eps, req->eps + N);
+  r->B.assign(req->B, req->B + N);
+  if (req->freq_w) r->fw.assign(req->freq_w, req->freq_w + req->desc.nfreq);
+  else r->fw.assign((size_t)req->desc.nfreq, 1.0);
+  r->tol = req->tol;
+  r->max_iter = req->max_iter;
+  r->footprint = fp;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *id_out = r->id;
+  }
+  s->cv.notify_all();
+  return RT_OK;
+}
+
+rt_status rt_poll(rt_server s, long long id, rt_request_info *info) {
+  if (!s) return RT_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return RT_ERR_ARG;
+  fill_info(it->second, info);
+  return RT_OK;
+}
+
+rt_status rt_wait(rt_server s, long long id, double timeout_s, rt_request_info *info) {
+  if (!s) return RT_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return RT_ERR_ARG;
+  Request *r = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
+  const bool done = s->cv.wait_until(lk, deadline, [&] { return r->state == RT_REQ_DONE; });
+  fill_info(r, info);
+  return done ? RT_OK : RT_ERR_TIMEOUT;
+}
+
+rt_status rt_fetch(rt_server s, long long id, double *J, double *S, double *Q) {
+  if (!s) return RT_ERR_ARG;
+  Request *r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return RT_ERR_ARG;
+    r = it->second;
+    if (r->state != RT_REQ_DONE) return RT_ERR_STATE;
+    s->reqs.erase(it);
+  }
+  if (J && !r->J.empty()) std::memcpy(J, r->J.data(), r->J.size() * sizeof(double));
+  if (S && !r->S.empty()) std::memcpy(S, r->S.data(), r->S.size() * sizeof(double));
+  if (Q && !r->Q.empty()) std::memcpy(Q, r->Q.data(), r->Q.size() * sizeof(double));
+  const rt_status st = (rt_status)r->status;
+  delete r;
+  return st;
+}
+
+}  // extern "C"

@@ -47,6 +47,25 @@ class rt_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong)]
 
 
+class rt_server_opts(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_longlong), ("workers", ctypes.c_int)]
+
+
+class rt_request(ctypes.Structure):
+    _fields_ = [("desc", rt_grid_desc), ("interp", ctypes.c_int), ("chi", ctypes.c_void_p),
+                ("eps", ctypes.c_void_p), ("B", ctypes.c_void_p), ("freq_w", ctypes.c_void_p),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class rt_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("resid", ctypes.c_double), ("queue_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("footprint", ctypes.c_longlong)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
+
+
 class RTError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"rt status {status}: {msg}")
@@ -77,6 +96,13 @@ _SIGS = {
     "rt_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "rt_angle_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP]),
     "rt_formal_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(rt_grid_desc), _VP, _VP, _VP, _VP, _VP]),
+    "rt_grid_footprint": (ctypes.c_int, [ctypes.POINTER(rt_grid_desc), ctypes.POINTER(ctypes.c_longlong)]),
+    "rt_server_create": (ctypes.c_int, [ctypes.POINTER(rt_server_opts), ctypes.POINTER(_VP)]),
+    "rt_server_destroy": (ctypes.c_int, [_VP]),
+    "rt_submit": (ctypes.c_int, [_VP, ctypes.POINTER(rt_request), ctypes.POINTER(ctypes.c_longlong)]),
+    "rt_poll": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.POINTER(rt_request_info)]),
+    "rt_wait": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(rt_request_info)]),
+    "rt_fetch": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP, _VP, _VP]),
     "rt_last_error": (ctypes.c_char_p, []),
 }
 
@@ -329,3 +355,78 @@ class Grid:
         s = rt_stats()
         _check(load().rt_get_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in rt_stats._fields_}
+
+
+def _desc_of(p, prec):
+    if isinstance(prec, str):
+        prec = {"fp64": FP64, "mixed": MIXED}[prec.lower()]
+    return rt_grid_desc(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, p.n_mu, p.nf, (ctypes.c_int * 3)(*p.bc_lo),
+                        (ctypes.c_int * 3)(*p.bc_hi), prec)
+
+
+def grid_footprint(p, prec=MIXED):
+    """Estimated device bytes of a grid for problem ``p`` (rt_grid_footprint)."""
+    out = ctypes.c_longlong(0)
+    _check(load().rt_grid_footprint(ctypes.byref(_desc_of(p, prec)), ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """Request server (rt_server_*): queued ALI solves on worker threads, admitted
+    by estimated device footprint; results come back as host arrays."""
+
+    def __init__(self, workers=2, device_bytes=0):
+        self._h = _VP()
+        _check(load().rt_server_create(ctypes.byref(rt_server_opts(int(device_bytes), int(workers))),
+                                       ctypes.byref(self._h)))
+        self._shapes = {}
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            load().rt_server_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, p, prec=MIXED, tol=None, max_iter=1000, interp=INTERP_LINEAR):
+        """Queue an ALI solve of the workloads.Problem ``p``; returns its id."""
+        if isinstance(interp, str):
+            interp = {"linear": INTERP_LINEAR, "quadratic": INTERP_QUADRATIC}[interp.lower()]
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.chi, p.eps, p.B, p.freq_w)]
+        req = rt_request(_desc_of(p, prec), int(interp), *[a.ctypes.data for a in arrs],
+                         float(p.tol if tol is None else tol), int(max_iter))
+        rid = ctypes.c_longlong(0)
+        _check(load().rt_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
+        self._shapes[rid.value] = (p.nf, p.nz, p.ny, p.nx)
+        return rid.value
+
+    @staticmethod
+    def _info(i):
+        return {k: getattr(i, k) for k, _ in rt_request_info._fields_}
+
+    def poll(self, rid):
+        i = rt_request_info()
+        _check(load().rt_poll(self._h, ctypes.c_longlong(rid), ctypes.byref(i)))
+        return self._info(i)
+
+    def wait(self, rid, timeout=600.0):
+        """Info once the request is done; raises RTError(RT_ERR_TIMEOUT) after ``timeout`` s."""
+        i = rt_request_info()
+        _check(load().rt_wait(self._h, ctypes.c_longlong(rid), float(timeout), ctypes.byref(i)))
+        return self._info(i)
+
+    def fetch(self, rid, raise_on_fail=True):
+        """(J, S, Q) host arrays of a finished request, and its status."""
+        nf, nz, ny, nx = self._shapes.pop(rid)
+        J = np.empty((nf, nz, ny, nx))
+        S = np.empty_like(J)
+        Q = np.empty((nz, ny, nx))
+        st = load().rt_fetch(self._h, ctypes.c_longlong(rid), J.ctypes.data, S.ctypes.data, Q.ctypes.data)
+        if st != RT_OK and (raise_on_fail or st not in (RT_ERR_NOT_CONVERGED,)):
+            _check(st)
+        return J, S, Q, st

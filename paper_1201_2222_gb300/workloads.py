@@ -233,6 +233,40 @@ def random_box(nx: int, ny: int, nz: int, seed: int, n_mu: int = 4, nf: int = 1,
                    bc_hi=tuple(bc_hi))
 
 
+def build_request(d: dict, tol: float = 1e-6) -> Problem:
+    """The transfer problem of one ``serving_stream`` descriptor.
+
+    3D sizes: the turbulent box's fields (density and temperature from the
+    request's seed), box optical depth 30, fully periodic; ``nf`` bins with
+    chi_nu = chi (1 + nu/nf) and B_nu = T^4 (1 + nu/nf)^-1, eps the request's
+    value everywhere.  2D (512 x 512 x 1): a y-stratified atmosphere (the
+    stratified optical-depth profile along y), x periodic, I = B below, vacuum
+    above, T from the request's seed on the plane."""
+    nx, ny, nz = d["shape"]
+    nf, eps0, seed = int(d["nf"]), float(d["eps"]), int(d["seed"])
+    if nz > 1:
+        n = max(nx, ny, nz)   # fields of the enclosing cube, cut to the grid
+        rho, T = _turbulent_fields(n, seed, seed + 1)
+        rho, T = rho[:nz, :ny, :nx], T[:nz, :ny, :nx]
+        chi0 = rho * (0.1 * rho * T ** (-3.5) + 0.9)
+        chi0 = chi0 * (30.0 / (chi0.mean() * n))
+        bc_lo = bc_hi = (PERIODIC, PERIODIC, PERIODIC)
+    else:
+        prof, _ = stratified_profile(ny)
+        rng = np.random.default_rng(seed)
+        T = np.exp(0.1 * rng.standard_normal((1, ny, nx)))
+        chi0 = np.broadcast_to(prof[None, :, None], (1, ny, nx)) * T ** (-1.0)
+        bc_lo, bc_hi = (PERIODIC, THERMAL, PERIODIC), (PERIODIC, VACUUM, PERIODIC)
+    shape = (nf, nz, ny, nx)
+    scale = 1.0 + np.arange(nf, dtype=np.float64) / nf
+    chi = np.ascontiguousarray(np.broadcast_to(chi0.reshape((1, nz, ny, nx)), shape) * scale[:, None, None, None])
+    B = np.ascontiguousarray(np.broadcast_to((T ** 4).reshape((1, nz, ny, nx)), shape) / scale[:, None, None, None])
+    return Problem(name=f"request_{seed}_{nx}x{ny}x{nz}_nf{nf}_lq{d['n_mu']}", nx=nx, ny=ny, nz=nz,
+                   n_mu=int(d["n_mu"]), chi=chi, eps=np.full(shape, eps0), B=B,
+                   freq_w=np.full(nf, 1.0 / nf), bc_lo=bc_lo, bc_hi=bc_hi, tol=tol,
+                   recipe="serving request: turbulent fields (3D) or y-stratified plane (2D), see build_request")
+
+
 def serving_stream(n_requests: int = 1024, seed: int = 7, rate: float = 1.0):
     """Request descriptors for a mixed-size request stream (Poisson arrivals).
 

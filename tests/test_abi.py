@@ -60,3 +60,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "lib_path", lambda debug=False: str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="missing"):
         rt.load()
+
+
+def test_grid_footprint_is_host_only_and_grows_with_the_problem():
+    from paper_1201_2222_gb300 import rt, workloads as W
+    small = rt.grid_footprint(W.random_box(8, 8, 8, seed=1, n_mu=4))
+    big = rt.grid_footprint(W.random_box(16, 16, 16, seed=1, n_mu=4))
+    more_rays = rt.grid_footprint(W.random_box(8, 8, 8, seed=1, n_mu=8))
+    fp64 = rt.grid_footprint(W.random_box(8, 8, 8, seed=1, n_mu=4), prec="fp64")
+    assert 0 < small < more_rays and small < fp64
+    assert 7 * small < big < 9 * small
