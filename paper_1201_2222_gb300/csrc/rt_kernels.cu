@@ -773,6 +773,15 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   cp_async_wait_all();
   if (C > 1) cluster.sync();
   else __syncthreads();
+  // asynchronous loads a plane step issues for later steps: the next plane's chi
+  // and S, and the halo ghosts of this plane's intensities (the next upwind plane)
+  auto issue = [&](int tt) {
+    const int ww = sa > 0 ? tt : Nw - 1 - tt;
+    if (tt + 1 < Nw) stage(ww + sa, (tt + 1) % 3);
+    ghost_halo(Ib + (tt & 1) * ib, ww, false);
+    cp_async_commit();
+  };
+  issue(0);
 
   for (int t = 0; t < Nw; ++t) {
     const int w = sa > 0 ? t : Nw - 1 - t;
@@ -780,10 +789,6 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     const T *Iprv = Ib + ((t + 1) & 1) * ib;
     const T *Cc = Cr + (t % 3) * pb, *Cp = Cr + ((t + 2) % 3) * pb;
     const T *Sc = Sr + (t % 3) * pb, *Sp = Sr + ((t + 2) % 3) * pb;
-    // next plane's chi and S, and this plane's halo ghosts for the next step
-    if (t + 1 < Nw) stage(w + sa, (t + 1) % 3);
-    ghost_halo(Icur, w, false);
-    cp_async_commit();
     // this plane's buffers of the neighbouring strips: the first and last rows of
     // the strip are also stored into their halo rows (read there as the upwind
     // plane of the next step, after the cluster barrier)
@@ -996,8 +1001,17 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     // outflow ghosts of the previous plane, read from its (still intact) buffer
     if (t > 0) ghost_pass(Iprv, w - sa);
     cp_async_wait_all();
-    if (C > 1) cluster.sync();
-    else __syncthreads();
+    // the CTA is done with the chi/S slot and the halo columns the next issue
+    // refills; the cluster barrier (strip edges pushed to the neighbours) is
+    // split around that issue so its latency overlaps the copies' set-up
+    __syncthreads();
+    if (C > 1) {
+      cluster.barrier_arrive();
+      if (t + 1 < Nw) issue(t + 1);
+      cluster.barrier_wait();
+    } else if (t + 1 < Nw) {
+      issue(t + 1);
+    }
   }
   ghost_pass(Ib + ((Nw - 1) & 1) * ib, sa > 0 ? Nw - 1 : 0);
   (void)top_edge;
