@@ -207,8 +207,8 @@ def run_gpu(args):
     g = rt.Grid.from_problem(p, prec=rt.MIXED)
     g.set_opacity_source(chi, eps, B, fw)
     if args.plan:                 # a given sweep plan (e.g. to list one run's launches)
-        v, apg, c = (int(x) for x in args.plan.split(","))
-        g.set_sweep_config(apg, c, 0, v)
+        v, apg, c, th = (int(x) for x in (args.plan + ",0").split(",")[:4])
+        g.set_sweep_config(apg, c, th, v)
     else:                         # set-up: pick the sweep launch plan once per problem shape
         g.autotune()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -371,8 +371,8 @@ def run_profile(args):
         g.set_interpolation(rt.INTERP_QUADRATIC)
     g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
     if args.plan:
-        v, apg, c = (int(x) for x in args.plan.split(","))
-        g.set_sweep_config(apg, c, 0, v)
+        v, apg, c, th = (int(x) for x in (args.plan + ",0").split(",")[:4])
+        g.set_sweep_config(apg, c, th, v)
     elif not args.no_autotune:
         g.autotune()
     it, resid, st = g.ali_solve(tol=TOL, max_iter=args.profile_iters, raise_on_fail=False)
@@ -441,7 +441,7 @@ def main(argv=None):
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
     ap.add_argument("--quadratic", action="store_true", help="with --profile: the second-order sweep")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
-    ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster instead of autotuning")
+    ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster[,threads] instead of autotuning")
     ap.add_argument("--serve", type=int, default=0, help="run N requests of the serving stream instead")
     ap.add_argument("--rate", type=float, default=2.0, help="with --serve: arrivals per second")
     ap.add_argument("--workers", type=int, default=4, help="with --serve: solves in flight")

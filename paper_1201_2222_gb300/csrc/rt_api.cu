@@ -28,6 +28,17 @@ namespace {
 
 thread_local std::string g_err = "no error";
 
+}  // namespace
+
+// Records the calling thread's error message for rt_last_error (used by the
+// request server's translation unit); returns st.
+rt_status rt_internal_error(rt_status st, const char *msg) {
+  g_err = msg;
+  return st;
+}
+
+namespace {
+
 rt_status fail(rt_status st, const char *fmt, ...) {
   char buf[512];
   va_list ap;

@@ -874,10 +874,11 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
             }
           }
         };
+        // a short unroll: fully unrolled blocks (4 x AMAX ray bodies) overflow the
+        // instruction cache; two bodies per trip keep some overlap between rays
         auto block = [&](auto su_c, auto sv_c, int k0, int kn) {
-#pragma unroll
-          for (int q = 0; q < AMAX; ++q)
-            if (q < kn) ray(su_c, sv_c, k0 + q);
+#pragma unroll 2
+          for (int q = 0; q < kn; ++q) ray(su_c, sv_c, k0 + q);
         };
         block(SignC<-1>{}, SignC<-1>{}, gp.kb[0], gp.kb[1] - gp.kb[0]);
         block(SignC<1>{}, SignC<-1>{}, gp.kb[1], gp.kb[2] - gp.kb[1]);
@@ -972,9 +973,8 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
           }
         };
         auto block = [&](auto su_c, auto sv_c, int k0, int kn) {
-  #pragma unroll
-          for (int q = 0; q < AMAX; ++q)
-            if (q < kn) ray(su_c, sv_c, k0 + q);
+  #pragma unroll 2
+          for (int q = 0; q < kn; ++q) ray(su_c, sv_c, k0 + q);
         };
         block(SignC<-1>{}, SignC<-1>{}, gp.kb[0], gp.kb[1] - gp.kb[0]);
         block(SignC<1>{}, SignC<-1>{}, gp.kb[1], gp.kb[2] - gp.kb[1]);

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -13,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include "rt_sc.h"
+
+rt_status rt_internal_error(rt_status st, const char *msg);   // rt_api.cu
 
 namespace {
 
@@ -36,6 +39,7 @@ struct Request {
   double resid = 0.0;
   Clock::time_point t_submit, t_start, t_done;
   std::vector<double> J, S, Q;
+  std::string message;       // the solve's error message (worker thread's rt_last_error)
 };
 
 }  // namespace
@@ -80,6 +84,7 @@ void run_solve(Request *r, int device) {
     if (s2 == RT_OK) s2 = rt_get_S(g, r->S.data(), 0, nullptr);
     if (s2 != RT_OK) st = s2;
   }
+  if (st != RT_OK) r->message = rt_last_error();
   if (g) rt_destroy_grid(g);
   r->status = st;
   r->iters = iters;
@@ -132,7 +137,7 @@ void fill_info(const Request *r, rt_request_info *info) {
 extern "C" {
 
 rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
-  if (!opts || !out || opts->workers < 1) return RT_ERR_ARG;
+  if (!opts || !out || opts->workers < 1) return rt_internal_error(RT_ERR_ARG, "rt_server_create: NULL argument or workers < 1");
   *out = nullptr;
   rt_server s = new rt_server_s();
   cudaGetDevice(&s->device);
@@ -141,7 +146,7 @@ rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       delete s;
-      return RT_ERR_CUDA;
+      return rt_internal_error(RT_ERR_CUDA, "rt_server_create: cudaMemGetInfo failed");
     }
     s->budget = (long long)(0.8 * (double)fr);
   }
@@ -151,7 +156,7 @@ rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
 }
 
 rt_status rt_server_destroy(rt_server s) {
-  if (!s) return RT_ERR_ARG;
+  if (!s) return rt_internal_error(RT_ERR_ARG, "rt_server_destroy: NULL server");
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
@@ -164,11 +169,13 @@ rt_status rt_server_destroy(rt_server s) {
 }
 
 rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
-  if (!s || !req || !id_out || !req->chi || !req->eps || !req->B) return RT_ERR_ARG;
+  if (!s || !req || !id_out || !req->chi || !req->eps || !req->B)
+    return rt_internal_error(RT_ERR_ARG, "rt_submit: NULL argument");
   long long fp = 0;
   rt_status st = rt_grid_footprint(&req->desc, &fp);
   if (st != RT_OK) return st;
-  if (req->interp != 0 && req->interp != RT_INTERP_LINEAR && req->interp != RT_INTERP_QUADRATIC) return RT_ERR_ARG;
+  if (req->interp != 0 && req->interp != RT_INTERP_LINEAR && req->interp != RT_INTERP_QUADRATIC)
+    return rt_internal_error(RT_ERR_ARG, "rt_submit: interp must be 0, 1 or 2");
   Request *r = new Request();
   r->desc = req->desc;
   r->interp = req->interp == 0 ? RT_INTERP_LINEAR : req->interp;
@@ -194,44 +201,45 @@ rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
 }
 
 rt_status rt_poll(rt_server s, long long id, rt_request_info *info) {
-  if (!s) return RT_ERR_ARG;
+  if (!s) return rt_internal_error(RT_ERR_ARG, "rt_poll: NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return RT_ERR_ARG;
+  if (it == s->reqs.end()) return rt_internal_error(RT_ERR_ARG, "rt_poll: unknown request id");
   fill_info(it->second, info);
   return RT_OK;
 }
 
 rt_status rt_wait(rt_server s, long long id, double timeout_s, rt_request_info *info) {
-  if (!s) return RT_ERR_ARG;
+  if (!s) return rt_internal_error(RT_ERR_ARG, "rt_wait: NULL server");
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return RT_ERR_ARG;
+  if (it == s->reqs.end()) return rt_internal_error(RT_ERR_ARG, "rt_wait: unknown request id");
   Request *r = it->second;
   const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
                                            std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
   const bool done = s->cv.wait_until(lk, deadline, [&] { return r->state == RT_REQ_DONE; });
   fill_info(r, info);
-  return done ? RT_OK : RT_ERR_TIMEOUT;
+  return done ? RT_OK : rt_internal_error(RT_ERR_TIMEOUT, "rt_wait: the request is not done yet");
 }
 
 rt_status rt_fetch(rt_server s, long long id, double *J, double *S, double *Q) {
-  if (!s) return RT_ERR_ARG;
+  if (!s) return rt_internal_error(RT_ERR_ARG, "rt_fetch: NULL server");
   Request *r = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->reqs.find(id);
-    if (it == s->reqs.end()) return RT_ERR_ARG;
+    if (it == s->reqs.end()) return rt_internal_error(RT_ERR_ARG, "rt_fetch: unknown request id");
     r = it->second;
-    if (r->state != RT_REQ_DONE) return RT_ERR_STATE;
+    if (r->state != RT_REQ_DONE) return rt_internal_error(RT_ERR_STATE, "rt_fetch: the request is not done");
     s->reqs.erase(it);
   }
   if (J && !r->J.empty()) std::memcpy(J, r->J.data(), r->J.size() * sizeof(double));
   if (S && !r->S.empty()) std::memcpy(S, r->S.data(), r->S.size() * sizeof(double));
   if (Q && !r->Q.empty()) std::memcpy(Q, r->Q.data(), r->Q.size() * sizeof(double));
   const rt_status st = (rt_status)r->status;
+  const std::string msg = r->message;
   delete r;
-  return st;
+  return st == RT_OK ? st : rt_internal_error(st, msg.c_str());
 }
 
 }  // extern "C"
