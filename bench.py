@@ -43,6 +43,17 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
+# DRAM read + write bytes per launch of the sweep kernel from an ncu capture of
+# this workload and plan (profiles/sc_sweep_pipe_kernel_turbulent_box_128_lq8.md);
+# reported only for that plan, and to be re-taken whenever the kernel changes
+PROFILED_TRAFFIC = {("turbulent_box_128^3_lq8", 3, 7, 10, 512): 118.019328e6 + 100.530176e6}
+
+
+def profiled_traffic(plan, p):
+    key = (p.name, plan["variant"], plan["rays_per_group"], plan["cluster"], plan["threads"])
+    return PROFILED_TRAFFIC.get(key)
+
+
 # sweep kernel of each planner variant (simple, tiled, pipelined)
 SWEEP_KERNEL_NAMES = {1: "sc_sweep_kernel<float>", 2: "sc_sweep_tiled_kernel<float>",
                       3: "sc_sweep_pipe_kernel<float>"}
@@ -342,7 +353,8 @@ def run_gpu(args):
         "sweep_plan": g.sweep_plan(),
         "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[g.sweep_plan()["variant"]],
                      "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(g.sweep_plan(), p),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
                      "flops_per_update": FLOPS_PER_UPDATE, "avg_launch_ms": avg_launch_s * 1e3,
                      "launches": sweep_n},
