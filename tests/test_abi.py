@@ -70,3 +70,13 @@ def test_grid_footprint_is_host_only_and_grows_with_the_problem():
     fp64 = rt.grid_footprint(W.random_box(8, 8, 8, seed=1, n_mu=4), prec="fp64")
     assert 0 < small < more_rays and small < fp64
     assert 7 * small < big < 9 * small
+
+
+def test_grid_footprint_rejects_bad_descriptions():
+    import dataclasses
+    from paper_1201_2222_gb300 import rt, workloads as W
+    p = W.random_box(4, 4, 4, seed=1, n_mu=4)
+    with pytest.raises(rt.RTError):
+        rt.grid_footprint(dataclasses.replace(p, n_mu=5))
+    with pytest.raises(rt.RTError):
+        rt.grid_footprint(dataclasses.replace(p, nx=0))
