@@ -388,7 +388,9 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
       // second-order sweep, which also reads the downwind plane)
       const size_t W = (size_t)rtk::pipe_row_len(Nu, rtk::kSweepSeg);
       const size_t ring = g->interp == RT_INTERP_QUADRATIC ? 8 : 6;
-      sm = std::max(sm, (size_t)(2 * slots + ring) * (Rmax + 2) * W * g->tsize);
+      // plus, for the linear sweep, two buffers of prefetched ghosts per ray slot
+      const size_t pre = g->interp == RT_INTERP_QUADRATIC ? 0 : (size_t)2 * slots * (Rmax + Nu);
+      sm = std::max(sm, ((size_t)(2 * slots + ring) * (Rmax + 2) * W + pre) * g->tsize);
       th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
     } else if (variant == 2) {
       const size_t W = (size_t)Nu + 2 + rtk::kSweepSeg;

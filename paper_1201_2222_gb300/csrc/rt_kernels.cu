@@ -617,6 +617,8 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   T *Ib = reinterpret_cast<T *>(smem_raw);   // [2][slots][RX][W]   intensities
   T *Cr = Ib + 2 * ib;                       // [3][RX][W]          chi ring
   T *Sr = Cr + 3 * pb;                       // [3][RX][W]          S ring
+  T *Gpre = Sr + 3 * pb;                     // [2][slots][Rmax + Nu] lagged ghosts for the outflow pass
+  const int gpl = Rmax + Nu;                 // one ray's prefetched u-face rows and v-face row
 #ifdef RT_DEBUG_BOUNDS
   const long long smem_n = 2LL * ib + 6LL * pb;
 #endif
@@ -731,16 +733,18 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   // Outflow intensities of plane wp onto the periodic faces, for the next formal
   // solution (Sec. 3.5): the u face (one column per row), the v face (one row, in
   // the strip that holds it) and, at the last plane, the w face (the whole strip).
-  auto ghost_pass = [&](const T *Ibuf, int wp) {
-    if (!A.write_ghosts) return;
-    const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+  // The incremental and increment-recording sweeps read the previous ghosts
+  // where they write new ones; those values are fetched into shared memory one
+  // plane step ahead (buffer buf), so the outflow pass does not wait on memory.
+  const bool need_pre = A.write_ghosts && A.incremental;
+  auto ghost_prefetch = [&](int wp, int buf) {
+    if (!need_pre) return;
+    T *dst = Gpre + (long long)buf * A.ray_slots * gpl;
     if (perU) {
       for (int idx = threadIdx.x; idx < na * R; idx += blockDim.x) {
         const int a = idx / R, lv = idx - a * R;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
-        const int col = P[a].su > 0 ? Nu - 1 : 0;
-        ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)wp * Nv + v0 + lv, gn, 54),
-                       Ibuf[RT_IDX(a * pb + (lv + 1) * W + kPipeX0 + col, 2LL * ib, 58)], inc, emit);
+        cp_async_elem(dst + a * gpl + lv, Gp + gb + plane + (long long)wp * Nv + v0 + lv);
       }
     }
     if (perV) {
@@ -749,8 +753,45 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
         const int vr = P[a].sv > 0 ? Nv - 1 : 0;
         if (vr < v0 || vr >= v1) continue;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
-        ghost_store<T>(Gp, Gn, Gdn, RT_IDX(gb + plane + (long long)Nw * Nv + (long long)wp * Nu + u, gn, 55),
-                       Ibuf[RT_IDX(a * pb + (vr - v0 + 1) * W + kPipeX0 + u, 2LL * ib, 59)], inc, emit);
+        cp_async_elem(dst + a * gpl + Rmax + u, Gp + gb + plane + (long long)Nw * Nv + (long long)wp * Nu + u);
+      }
+    }
+  };
+  // store with the previous ghost value taken from the prefetch buffer
+  auto store_pre = [&](long long off, T I0, T pre) {
+    if (inc) {
+      Gdn[off] = I0;
+      Gn[off] = pre + I0;
+    } else {
+      if (emit) Gdn[off] = I0 - pre;
+      Gn[off] = I0;
+    }
+  };
+  auto ghost_pass = [&](const T *Ibuf, int wp, int buf) {
+    if (!A.write_ghosts) return;
+    const long long gn = (long long)A.d.nf * A.na * A.d.gsize;
+    const T *pre = Gpre + (long long)buf * A.ray_slots * gpl;
+    if (perU) {
+      for (int idx = threadIdx.x; idx < na * R; idx += blockDim.x) {
+        const int a = idx / R, lv = idx - a * R;
+        const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
+        const int col = P[a].su > 0 ? Nu - 1 : 0;
+        const long long off = RT_IDX(gb + plane + (long long)wp * Nv + v0 + lv, gn, 54);
+        const T I0 = Ibuf[RT_IDX(a * pb + (lv + 1) * W + kPipeX0 + col, 2LL * ib, 58)];
+        if (need_pre) store_pre(off, I0, pre[a * gpl + lv]);
+        else ghost_store<T>(Gp, Gn, Gdn, off, I0, inc, emit);
+      }
+    }
+    if (perV) {
+      for (int idx = threadIdx.x; idx < na * Nu; idx += blockDim.x) {
+        const int a = idx / Nu, u = idx - a * Nu;
+        const int vr = P[a].sv > 0 ? Nv - 1 : 0;
+        if (vr < v0 || vr >= v1) continue;
+        const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
+        const long long off = RT_IDX(gb + plane + (long long)Nw * Nv + (long long)wp * Nu + u, gn, 55);
+        const T I0 = Ibuf[RT_IDX(a * pb + (vr - v0 + 1) * W + kPipeX0 + u, 2LL * ib, 59)];
+        if (need_pre) store_pre(off, I0, pre[a * gpl + Rmax + u]);
+        else ghost_store<T>(Gp, Gn, Gdn, off, I0, inc, emit);
       }
     }
     if (perW && wp == wlast) {
@@ -779,6 +820,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     const int ww = sa > 0 ? tt : Nw - 1 - tt;
     if (tt + 1 < Nw) stage(ww + sa, (tt + 1) % 3);
     ghost_halo(Ib + (tt & 1) * ib, ww, false);
+    ghost_prefetch(ww, tt & 1);   // for this plane's outflow pass, one step later
     cp_async_commit();
   };
   issue(0);
@@ -999,7 +1041,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       }
     }
     // outflow ghosts of the previous plane, read from its (still intact) buffer
-    if (t > 0) ghost_pass(Iprv, w - sa);
+    if (t > 0) ghost_pass(Iprv, w - sa, (t + 1) & 1);
     cp_async_wait_all();
     // the CTA is done with the chi/S slot and the halo columns the next issue
     // refills; the cluster barrier (strip edges pushed to the neighbours) is
@@ -1013,7 +1055,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       issue(t + 1);
     }
   }
-  ghost_pass(Ib + ((Nw - 1) & 1) * ib, sa > 0 ? Nw - 1 : 0);
+  ghost_pass(Ib + ((Nw - 1) & 1) * ib, sa > 0 ? Nw - 1 : 0, (Nw - 1) & 1);
   (void)top_edge;
   (void)bot_edge;
 }
