@@ -46,11 +46,12 @@ FP32_LANES_PER_SM = 128
 # DRAM read + write bytes per launch of the sweep kernel from an ncu capture of
 # this workload and plan (profiles/sc_sweep_pipe_kernel_turbulent_box_128_lq8.md);
 # reported only for that plan, and to be re-taken whenever the kernel changes
-PROFILED_TRAFFIC = {("turbulent_box_128^3_lq8", 3, 7, 10, 512): 118.019328e6 + 100.530176e6}
+# (keyed by workload, plan and shared-memory size, which changes with the kernel's layout)
+PROFILED_TRAFFIC = {("turbulent_box_128^3_lq8", 3, 7, 10, 512, 168000): 118.019328e6 + 100.530176e6}
 
 
 def profiled_traffic(plan, p):
-    key = (p.name, plan["variant"], plan["rays_per_group"], plan["cluster"], plan["threads"])
+    key = (p.name, plan["variant"], plan["rays_per_group"], plan["cluster"], plan["threads"], plan["smem"])
     return PROFILED_TRAFFIC.get(key)
 
 
