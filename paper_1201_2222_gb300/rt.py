@@ -316,17 +316,20 @@ class Grid:
             _check(st)
         return it.value, r.value, st
 
-    def moments(self, on_device=False):
+    def moments(self, on_device=False, want=("J", "H", "K", "f", "Q"), out=None):
+        """J, H, K, f = K/J and Q of the last formal solution (rt_moments).
+
+        ``want``: the outputs to return (the others are not copied); ``out``: a dict
+        of caller arrays to fill instead of new ones (e.g. pinned host tensors)."""
         nf = self.nfreq
         sp = self.shape[1:]
-        out = dict(J=self._out((nf,) + sp, on_device), H=self._out((nf, 3) + sp, on_device),
-                   K=self._out((nf, 6) + sp, on_device), f=self._out((nf, 6) + sp, on_device),
-                   Q=self._out(sp, on_device))
+        shapes = dict(J=(nf,) + sp, H=(nf, 3) + sp, K=(nf, 6) + sp, f=(nf, 6) + sp, Q=sp)
+        res = {k: (out[k] if out and k in out else self._out(shapes[k], on_device)) for k in want}
+        ptr = lambda k: self._ptr(res[k]) if k in res else None
         o = self._opts(on_device=on_device)
-        _check(load().rt_moments(self._h, self._ptr(out["J"]), self._ptr(out["H"]), self._ptr(out["K"]),
-                                 self._ptr(out["f"]), self._ptr(out["Q"]), 1 if on_device else 0,
-                                 ctypes.byref(o)))
-        return out
+        _check(load().rt_moments(self._h, ptr("J"), ptr("H"), ptr("K"), ptr("f"), ptr("Q"),
+                                 1 if on_device else 0, ctypes.byref(o)))
+        return res
 
     def get_S(self, on_device=False):
         S = self._out(self.shape, on_device)
