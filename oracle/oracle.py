@@ -16,6 +16,10 @@ Follows Davis, Stone & Jiang (2012):
     stopped when max |dS|/S <= delta_c (Eq. 25); when every eps = 1 the test uses
     the change of J between consecutive formal solutions (Sec. 3.4).  The
     iteration count is the number of formal solutions performed.
+  * ``ali_solve(method="gauss_seidel")`` - the Gauss-Seidel ALI of Sec. 3.4 in
+    its plane-wavefront form (``gs_reverse_rays``, ``gs_reverse`` and
+    ``orc_gs_reverse`` in sc_oracle.c): forward rays from the old S, then the
+    reverse sweep updating S plane by plane with the freshest J.
   * ``heating_rate``     - Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu) (Sec. 4, Q^int).
   * ``heating_rate_dif`` - Q^dif = -4 pi sum_nu w_nu div H_nu (Sec. 4), div H by
     centred differences of the cell-centred H (one-sided at non-periodic faces).
@@ -52,6 +56,13 @@ def _load():
                 ctypes.c_double, ip, ip, ctypes.c_int, d, d, d, d, d, d, d, d, d, d, d, d,
                 ctypes.c_int]
             fn.restype = ctypes.c_int
+        lib.orc_gs_reverse.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, ip, ip, ctypes.c_int, d, d, ip, d, d, d, d, d, d, d, d, d, d, d, d]
+        lib.orc_gs_reverse.restype = ctypes.c_int
+        lib.orc_gs_is_reverse.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double]
+        lib.orc_gs_is_reverse.restype = ctypes.c_int
         lib.orc_bezier_weights.argtypes = [ctypes.c_double, d]
         lib.orc_bezier_weights.restype = None
         lib.orc_max_threads.restype = ctypes.c_int
@@ -131,8 +142,20 @@ def bezier_weights(dtau):
     return out
 
 
+def _ray_subset_fixed(grid: Grid, I_fixed, rays):
+    """Rows of the rays ``rays`` of a [6][na][face] boundary array."""
+    out = []
+    off = 0
+    for f in range(6):
+        n = grid.face[f // 2]
+        block = I_fixed[off:off + grid.na * n].reshape(grid.na, n)
+        out.append(block[rays].ravel())
+        off += grid.na * n
+    return np.concatenate(out)
+
+
 def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=False,
-                    nthreads=1, interp="linear"):
+                    nthreads=1, interp="linear", rays=None):
     """One formal solution for one frequency.
 
     ``interp``: "linear" (bilinear face interpolation, linear S along the segment)
@@ -142,6 +165,8 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     ``G_prev`` defaults to ``init_ghosts(grid, S)``; ``I_fixed`` is the user
     incident-intensity array for RT_BC_FIXED faces
     ([6][na][face cells], faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi).
+    ``rays``: indices of the rays to solve (default all); J, lstar, H, K then
+    sum over those rays only and G_next holds their rows only.
     Returns a dict with J, lstar, G_next (and H [3], K [6] when ``moments``)."""
     lib = _load()
     C = grid.cells
@@ -157,16 +182,25 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
         need = 2 * grid.na * sum(grid.face)
         if I_fixed.size != need:
             raise ValueError(f"I_fixed must hold {need} values")
+    mu, wq, na = grid.mu, grid.w, grid.na
+    if rays is not None:
+        rays = np.asarray(rays, dtype=np.int64)
+        mu, wq, na = grid.mu[rays], grid.w[rays], len(rays)
+        G_prev = np.ascontiguousarray(G_prev[rays])
+        G_next = G_prev.copy()
+        if I_fixed is not None:
+            I_fixed = _ray_subset_fixed(grid, I_fixed, rays)
     J = np.empty(C)
     L = np.empty(C)
     H = np.empty(3 * C) if moments else None
     K = np.empty(6 * C) if moments else None
     bl = (ctypes.c_int * 3)(*grid.bc_lo)
     bh = (ctypes.c_int * 3)(*grid.bc_hi)
-    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    mu = np.ascontiguousarray(mu).reshape(-1)
+    wq = np.ascontiguousarray(wq)
     fn = {"linear": lib.orc_formal_solution, "quadratic": lib.orc_formal_solution_quad}[interp]
     rc = fn(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
-            grid.d[2], bl, bh, grid.na, _ptr(mu), _ptr(grid.w),
+            grid.d[2], bl, bh, na, _ptr(mu), _ptr(wq),
             _ptr(chi), _ptr(S), _ptr(B), _ptr(I_fixed), _ptr(G_prev),
             _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
             int(nthreads))
@@ -185,6 +219,47 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
         out["H"] = H
         out["K"] = K
     return out
+
+
+def gs_reverse_rays(grid: Grid) -> np.ndarray:
+    """Mask of the reverse rays of the Gauss-Seidel iteration: crossed face
+    normal to z (y in 2D), ties with that axis included, and mu along it < 0."""
+    lib = _load()
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    return np.array([bool(lib.orc_gs_is_reverse(grid.n[2], _ptr(mu), k, *grid.d))
+                     for k in range(grid.na)])
+
+
+def gs_reverse(grid: Grid, chi, eps, B, lstar, J_F, S, G_prev, G_next, I_fixed=None):
+    """The reverse phase of one Gauss-Seidel iteration for one frequency (see
+    orc_gs_reverse).  S is updated in place; G_next receives the reverse rays'
+    outflow ghosts.  Returns dict(J, dS, C): the J each cell was updated with,
+    the change of S and the first-order correction of the forward rays."""
+    lib = _load()
+    C = grid.cells
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    chi, eps, B, lstar, J_F = f64(chi), f64(eps), f64(B), f64(lstar), f64(J_F)
+    assert S.dtype == np.float64 and S.flags.c_contiguous and S.size == C
+    assert G_next.dtype == np.float64 and G_next.flags.c_contiguous
+    G_prev = np.ascontiguousarray(G_prev, dtype=np.float64)
+    if I_fixed is not None:
+        I_fixed = f64(I_fixed)
+    rev = np.ascontiguousarray(gs_reverse_rays(grid), dtype=np.int32)
+    J = np.empty(C)
+    dS = np.empty(C)
+    corr = np.empty(C)
+    bl = (ctypes.c_int * 3)(*grid.bc_lo)
+    bh = (ctypes.c_int * 3)(*grid.bc_hi)
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    rc = lib.orc_gs_reverse(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1], grid.d[2],
+                            bl, bh, grid.na, _ptr(mu), _ptr(grid.w),
+                            rev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            _ptr(chi), _ptr(B), _ptr(eps), _ptr(lstar), _ptr(J_F), _ptr(S),
+                            _ptr(I_fixed), _ptr(G_prev), _ptr(G_next), _ptr(J), _ptr(dS),
+                            _ptr(corr))
+    if rc != 0:
+        raise RuntimeError(f"oracle Gauss-Seidel sweep failed ({rc})")
+    return dict(J=J.reshape(grid.shape), dS=dS.reshape(grid.shape), C=corr.reshape(grid.shape))
 
 
 def max_relative_change(dS: np.ndarray, S: np.ndarray) -> float:
@@ -259,13 +334,22 @@ def heating_rate_switch(grid: Grid, chi, eps, J, B, H, freq_w):
 
 
 def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_init=None,
-              I_fixed=None, nthreads=1, moments=True, interp="linear"):
-    """Jacobi ALI to max|dS|/S <= tol (Eqs. 24-25), all frequencies per iteration.
+              I_fixed=None, nthreads=1, moments=True, interp="linear", method="jacobi"):
+    """Jacobi (or Gauss-Seidel) ALI to max|dS|/S <= tol (Eqs. 24-25), all
+    frequencies per iteration.
 
     chi, eps, B: [nf][nz][ny][nx].  I_fixed: None or a list (per frequency) of
     user boundary arrays.  Returns dict(S, J, lstar, H, K, f, Q, iters, resid,
     converged, history); J, H, K are those of the last formal solution, S is the
-    source function after the last update."""
+    source function after the last update.
+
+    method="gauss_seidel" (linear interpolation, eps < 1 somewhere): each
+    iteration solves the forward rays with the old S, then ``gs_reverse``
+    updates S plane by plane; the J, H, K returned are those of a formal
+    solution of the S (and ghosts) that the last iteration started from, and
+    ``J_gs`` holds the J each cell was last updated with."""
+    if method not in ("jacobi", "gauss_seidel"):
+        raise ValueError(f"unknown ALI method {method!r}")
     chi = np.asarray(chi, dtype=np.float64).reshape((-1,) + grid.shape)
     eps = np.asarray(eps, dtype=np.float64).reshape(chi.shape)
     B = np.asarray(B, dtype=np.float64).reshape(chi.shape)
@@ -282,7 +366,40 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
     r = math.inf
     it = 0
     S_fs, G_fs = S, G
+    gs = method == "gauss_seidel" and not lte
+    if gs and interp != "linear":
+        raise ValueError("the Gauss-Seidel iteration takes linear interpolation")
+    fwd = np.flatnonzero(~gs_reverse_rays(grid)) if gs else None
+    J_gs = np.empty_like(chi) if gs else None
     for it in range(1, max_iter + 1):
+        if gs:
+            S_new = S.copy()
+            dS = np.empty_like(S)
+            G_new = []
+            for f in range(nf):
+                if it == 1:
+                    lstar[f] = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f),
+                                               nthreads=nthreads)["lstar"]
+                res = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f),
+                                      nthreads=nthreads, rays=fwd)
+                Gn = G[f].copy()
+                Gn[fwd] = res["G_next"]
+                Sf = np.ascontiguousarray(S_new[f]).reshape(-1)
+                out = gs_reverse(grid, chi[f], eps[f], B[f], lstar[f], res["J"], Sf, G[f], Gn,
+                                 fixed(f))
+                S_new[f] = Sf.reshape(grid.shape)
+                dS[f] = out["dS"]
+                J_gs[f] = out["J"]
+                J[f] = out["J"]
+                G_new.append(Gn)
+            S_fs, G_fs = S, G
+            G = G_new
+            S = S_new
+            r = max_relative_change(dS, S)
+            history.append(r)
+            if r <= tol:
+                break
+            continue
         G_new = []
         for f in range(nf):
             res = formal_solution(grid, chi[f], S[f], B[f], G[f], fixed(f), nthreads=nthreads,
@@ -305,8 +422,15 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
         history.append(r)
         if r <= tol:
             break
+    if gs:
+        # outputs of the formal solution the last iteration started from
+        for f in range(nf):
+            J[f] = formal_solution(grid, chi[f], S_fs[f], B[f], G_fs[f], fixed(f),
+                                   nthreads=nthreads)["J"]
     out = dict(S=S, J=J.copy(), lstar=lstar, iters=it, resid=r, converged=r <= tol,
                history=history, Q=heating_rate(chi, eps, J, B, fw))
+    if gs:
+        out["J_gs"] = J_gs
     if moments:
         H = np.empty((nf, 3) + grid.shape)
         K = np.empty((nf, 6) + grid.shape)

@@ -538,6 +538,268 @@ int orc_formal_solution_quad(int nx, int ny, int nz, double dx, double dy, doubl
   return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Gauss-Seidel ALI (Sec. 3.4, after Trujillo Bueno & Fabiani Bendicho 1995),
+ * in its plane-wavefront form.
+ *
+ * The reverse axis V is z (y in 2D).  The reverse rays are those whose crossed
+ * face is the V face (ties with V included) and whose mu_V < 0: their upwind
+ * vertices all lie on the plane above.  Every other ray is a forward ray; its
+ * formal solution is done beforehand with the old S (J_F below).  Then the
+ * planes of V are visited from the top (index n_V - 1) down; at plane k:
+ *   1. the reverse rays' intensities at plane k, from the plane above, whose S
+ *      is already the new one and whose intensities are already corrected;
+ *      S0 of the cell itself is still the old one;
+ *   2. J = J_F + C + sum over reverse rays of w I, where C corrects, to first
+ *      order, the forward rays' use of the old S of the plane above (its cells
+ *      hold their new S now): C = sum over forward rays and over their upwind
+ *      vertices on plane k+1 of w Psi- (vertex weight) dS(vertex cell);
+ *   3. dS = [(1 - eps) J + eps B - S] / [1 - (1 - eps) Lambda*], S <- S + dS
+ *      (Eq. 24 with the freshest J);
+ *   4. the reverse rays' intensities at plane k take the change of every S
+ *      they used from plane k: I += Psi0 dS(cell) + Psi- (sum of the weights
+ *      of upwind vertices whose S is read from a cell of plane k times its dS)
+ *      -- the second term only on the top plane of a bounded V axis, whose
+ *      ghost layer copies plane k (they are the upwind values of plane k-1 and
+ *      the outflow ghosts).
+ * At convergence dS = 0, C = 0, and the fixed point is that of the Jacobi
+ * iteration.
+ *
+ * rev      [na]    1 for a reverse ray (rays with rev == 0 are forward rays)
+ * J_F      [cells] sum over forward rays of w I, from the old S
+ * S        [cells] in: S^n; out: S^{n+1}
+ * lstar    [cells] the full Lambda* (all rays)
+ * G_prev   ghosts read by the reverse rays (as in orc_formal_solution)
+ * G_next   outflow ghosts of the reverse rays are written (other rows untouched)
+ * J_out    [cells] the J of step 2;  dS_out [cells];  C_out [cells] or NULL
+ * ---------------------------------------------------------------------- */
+
+/* crossed axis (ties to z, then y, then x), path length and face offsets */
+static void ray_geometry(const geom *g, const double m[3], int *ax_out, double *s_out,
+                         double frac[3], int sgn[3]) {
+  double tpath[3];
+  for (int a = 0; a < 3; ++a) {
+    sgn[a] = m[a] >= 0.0 ? 1 : -1;
+    tpath[a] = (a == 2 && g->two_d) ? INFINITY : g->d[a] / fabs(m[a]);
+  }
+  int ax = 2;
+  if (tpath[1] < tpath[ax]) ax = 1;
+  if (tpath[0] < tpath[ax]) ax = 0;
+  const double s = tpath[ax];
+  for (int a = 0; a < 3; ++a) {
+    if (a == ax) frac[a] = 1.0;
+    else if (a == 2 && g->two_d) frac[a] = 0.0;
+    else frac[a] = s * fabs(m[a]) / g->d[a];
+  }
+  *ax_out = ax;
+  *s_out = s;
+}
+
+/* the SC segment weights of Eq. 20 (linear): E, Psi0 and Psi- */
+static void sc_weights(double dtau, double *E, double *psi0, double *psim) {
+  *E = exp(-dtau);
+  const double e0 = -expm1(-dtau);
+  if (dtau < 1e-3) {
+    *psi0 = dtau * (0.5 - dtau * (1.0 / 6.0 - dtau * (1.0 / 24.0 - dtau / 120.0)));
+  } else {
+    *psi0 = (dtau - e0) / dtau;
+  }
+  *psim = e0 - *psi0;
+}
+
+/* coordinate along axis V of the cell with index fi */
+static int plane_of(const geom *g, long fi, int V) {
+  if (V == 2) return (int)(fi / ((long)g->n[0] * g->n[1]));
+  if (V == 1) return (int)((fi / g->n[0]) % g->n[1]);
+  return (int)(fi % g->n[0]);
+}
+
+/* 1 if ray k is a reverse ray of the Gauss-Seidel iteration */
+int orc_gs_is_reverse(int nz, const double *mu, int k, double dx, double dy, double dz) {
+  geom g;
+  g.two_d = (nz == 1);
+  g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
+  const int V = g.two_d ? 1 : 2;
+  int ax, sgn[3];
+  double s, frac[3];
+  ray_geometry(&g, &mu[3 * k], &ax, &s, frac, sgn);
+  return ax == V && mu[3 * k + V] < 0.0;
+}
+
+int orc_gs_reverse(int nx, int ny, int nz, double dx, double dy, double dz,
+                   const int *bc_lo, const int *bc_hi,
+                   int na, const double *mu, const double *wq, const int *rev,
+                   const double *chi, const double *B, const double *eps, const double *lstar,
+                   const double *J_F, double *S, const double *I_fixed,
+                   const double *G_prev, double *G_next,
+                   double *J_out, double *dS_out, double *C_out) {
+  geom g;
+  g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
+  g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
+  g.two_d = (nz == 1);
+  for (int a = 0; a < 3; ++a) { g.bc_lo[a] = bc_lo[a]; g.bc_hi[a] = bc_hi[a]; }
+  g.cells = (long)nx * ny * nz;
+  g.face[0] = (long)nz * ny; g.face[1] = (long)nz * nx; g.face[2] = (long)ny * nx;
+  g.goff[0] = 0; g.goff[1] = g.face[0]; g.goff[2] = g.face[0] + g.face[1];
+  g.gsize = g.face[0] + g.face[1] + g.face[2];
+  if (nx < 1 || ny < 1 || nz < 1 || na < 1) return -1;
+  const int V = g.two_d ? 1 : 2;
+  const int P0 = 0, P1 = V == 2 ? 1 : 2;   /* the two in-plane axes */
+  const long C = g.cells;
+  int nrev = 0;
+  for (int k = 0; k < na; ++k) nrev += rev[k] != 0;
+  double *Ir = (double *)malloc((size_t)(nrev ? nrev : 1) * C * sizeof(double));
+  double *Pr = (double *)malloc((size_t)(nrev ? nrev : 1) * C * sizeof(double));
+  double *Mr = (double *)malloc((size_t)(nrev ? nrev : 1) * C * sizeof(double));
+  if (!Ir || !Pr || !Mr) { free(Ir); free(Pr); free(Mr); return -2; }
+  for (long i = 0; i < C; ++i) dS_out[i] = 0.0;
+
+  for (int kk = 0; kk < g.n[V]; ++kk) {
+    const int kv = g.n[V] - 1 - kk;
+    /* 1. reverse rays on plane kv */
+    int r = 0;
+    for (int k = 0; k < na; ++k) {
+      if (!rev[k]) continue;
+      const double *m = &mu[3 * k];
+      int ax, sgn[3];
+      double s, frac[3];
+      ray_geometry(&g, m, &ax, &s, frac, sgn);
+      const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+      double *I = Ir + (long)r * C;
+      double *Pz = Pr + (long)r * C;
+      double *Pm = Mr + (long)r * C;
+      for (int q = 0; q < g.n[P1]; ++q) {
+        for (int p = 0; p < g.n[P0]; ++p) {
+          int c0[3];
+          c0[V] = kv; c0[P0] = p; c0[P1] = q;
+          const long ci = cell_index(&g, c0[0], c0[1], c0[2]);
+          double chim = 0.0, Sm = 0.0, Im = 0.0;
+          for (int d1 = 0; d1 < 2; ++d1) {
+            for (int d2 = 0; d2 < 2; ++d2) {
+              const double wv = (d1 ? frac[b1] : 1.0 - frac[b1]) * (d2 ? frac[b2] : 1.0 - frac[b2]);
+              if (wv == 0.0) continue;
+              int c[3];
+              c[ax] = c0[ax] - sgn[ax];
+              c[b1] = c0[b1] - d1 * sgn[b1];
+              c[b2] = c0[b2] - d2 * sgn[b2];
+              const int inside = c[0] >= 0 && c[0] < nx && c[1] >= 0 && c[1] < ny &&
+                                 c[2] >= 0 && c[2] < nz;
+              const int fi = map_field(&g, c);
+              chim += wv * chi[fi];
+              Sm += wv * S[fi];
+              Im += wv * (inside ? I[cell_index(&g, c[0], c[1], c[2])]
+                                 : ghost_I(&g, c, k, na, B, I_fixed, G_prev));
+            }
+          }
+          double E, psi0, psim;
+          sc_weights(0.5 * (chim + chi[ci]) * s, &E, &psi0, &psim);
+          I[ci] = Im * E + psim * Sm + psi0 * S[ci];
+          Pz[ci] = psi0;
+          Pm[ci] = psim;
+        }
+      }
+      ++r;
+    }
+    /* 2.-3. J with the first-order correction, then the update, on plane kv */
+    for (int q = 0; q < g.n[P1]; ++q) {
+      for (int p = 0; p < g.n[P0]; ++p) {
+        int c0[3];
+        c0[V] = kv; c0[P0] = p; c0[P1] = q;
+        const long ci = cell_index(&g, c0[0], c0[1], c0[2]);
+        double corr = 0.0;
+        if (kv + 1 < g.n[V]) {
+          for (int k = 0; k < na; ++k) {
+            if (rev[k]) continue;
+            const double *m = &mu[3 * k];
+            int ax, sgn[3];
+            double s, frac[3];
+            ray_geometry(&g, m, &ax, &s, frac, sgn);
+            const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+            double chim = 0.0, part = 0.0;
+            for (int d1 = 0; d1 < 2; ++d1) {
+              for (int d2 = 0; d2 < 2; ++d2) {
+                const double wv = (d1 ? frac[b1] : 1.0 - frac[b1]) * (d2 ? frac[b2] : 1.0 - frac[b2]);
+                if (wv == 0.0) continue;
+                int c[3];
+                c[ax] = c0[ax] - sgn[ax];
+                c[b1] = c0[b1] - d1 * sgn[b1];
+                c[b2] = c0[b2] - d2 * sgn[b2];
+                const int fi = map_field(&g, c);
+                chim += wv * chi[fi];
+                if (c[V] == kv + 1) part += wv * dS_out[fi];
+              }
+            }
+            if (part != 0.0) {
+              double E, psi0, psim;
+              sc_weights(0.5 * (chim + chi[ci]) * s, &E, &psi0, &psim);
+              corr += wq[k] * psim * part;
+            }
+          }
+        }
+        double JR = 0.0;
+        r = 0;
+        for (int k = 0; k < na; ++k) {
+          if (!rev[k]) continue;
+          JR += wq[k] * Ir[(long)r * C + ci];
+          ++r;
+        }
+        const double J = J_F[ci] + corr + JR;
+        const double e = eps[ci];
+        const double dS = ((1.0 - e) * J + e * B[ci] - S[ci]) / (1.0 - (1.0 - e) * lstar[ci]);
+        S[ci] += dS;
+        dS_out[ci] = dS;
+        J_out[ci] = J;
+        if (C_out) C_out[ci] = corr;
+      }
+    }
+    /* 4. the reverse rays' intensities take the changes of the S they read
+       from this plane; outflow ghosts */
+    r = 0;
+    for (int k = 0; k < na; ++k) {
+      if (!rev[k]) continue;
+      const double *m = &mu[3 * k];
+      int ax, sgn[3];
+      double s, frac[3];
+      ray_geometry(&g, m, &ax, &s, frac, sgn);
+      const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+      for (int q = 0; q < g.n[P1]; ++q) {
+        for (int p = 0; p < g.n[P0]; ++p) {
+          int c0[3];
+          c0[V] = kv; c0[P0] = p; c0[P1] = q;
+          const long ci = cell_index(&g, c0[0], c0[1], c0[2]);
+          double ghost = 0.0;   /* upwind vertices whose S comes from this plane */
+          for (int d1 = 0; d1 < 2; ++d1) {
+            for (int d2 = 0; d2 < 2; ++d2) {
+              const double wv = (d1 ? frac[b1] : 1.0 - frac[b1]) * (d2 ? frac[b2] : 1.0 - frac[b2]);
+              if (wv == 0.0) continue;
+              int c[3];
+              c[ax] = c0[ax] - sgn[ax];
+              c[b1] = c0[b1] - d1 * sgn[b1];
+              c[b2] = c0[b2] - d2 * sgn[b2];
+              const int fi = map_field(&g, c);
+              if (plane_of(&g, fi, V) == kv) ghost += wv * dS_out[fi];
+            }
+          }
+          const double I0 = Ir[(long)r * C + ci] + Pr[(long)r * C + ci] * dS_out[ci] +
+                            Mr[(long)r * C + ci] * ghost;
+          Ir[(long)r * C + ci] = I0;
+          for (int a = 0; a < 3; ++a) {
+            if (g.bc_lo[a] != BC_PERIODIC) continue;
+            const int out = sgn[a] > 0 ? g.n[a] - 1 : 0;
+            if (c0[a] == out)
+              G_next[(long)k * g.gsize + g.goff[a] + face_index(&g, a, c0[0], c0[1], c0[2])] = I0;
+          }
+        }
+      }
+      ++r;
+    }
+  }
+  free(Ir);
+  free(Pr);
+  free(Mr);
+  return 0;
+}
+
 /* Number of OpenMP threads available (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP
