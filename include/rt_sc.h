@@ -168,9 +168,38 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
  *     every formal solution, and RT_PREC_MIXED grids sweep S itself, not its
  *     increments (float32 rounding then limits tol to about 1e-7 / eps).  Uses
  *     the pipelined sweep (variant 3) only.
- * Replans the sweep.  Errors: RT_ERR_ARG for another value. */
+ * Replans the sweep.  Errors: RT_ERR_ARG for another value; RT_ERR_STATE for
+ * quadratic interpolation on a Gauss-Seidel grid (rt_set_iteration). */
 typedef enum { RT_INTERP_LINEAR = 1, RT_INTERP_QUADRATIC = 2 } rt_interp;
 rt_status rt_set_interpolation(rt_grid g, int order);
+
+/* Iteration scheme of rt_ali_solve (Sec. 3.4).
+ *   RT_ITER_JACOBI (default): every S update uses the J of one formal solution
+ *     of the previous S (Eq. 24).
+ *   RT_ITER_GAUSS_SEIDEL: the Gauss-Seidel scheme (after Trujillo Bueno &
+ *     Fabiani Bendicho 1995) in plane-wavefront form.  The reverse axis V is z
+ *     (y for 2D grids); the reverse rays are those whose upwind face is normal
+ *     to V (ties with V included) with mu_V < 0.  Each iteration solves every
+ *     other ray with the current S, then sweeps the reverse rays from the top
+ *     plane of V down; each plane's S is updated by Eq. 24 with
+ *     J = (other rays' J) + (a first-order correction of the other rays for
+ *     the plane above, whose S is already new: the Psi- weights of their
+ *     upwind vertices there times its change) + (the reverse rays' J, which
+ *     already see the new S above), and the reverse rays' intensities on that
+ *     plane then take the change of the S they read from it (Psi0 dS, and on
+ *     the top plane of a bounded V axis Psi- times the ghost layer's change).
+ *     The fixed point is the Jacobi one; fewer iterations reach it.  Sweeps
+ *     are never incremental (RT_PREC_MIXED grids sweep S itself, so float32
+ *     rounding limits tol to about 1e-7 / eps); a medium with eps = 1
+ *     everywhere uses the Jacobi test of Eq. 25 on J.  Needs linear
+ *     interpolation.  The reverse phase is one cooperative launch whose planes
+ *     are separated by grid barriers; a barrier wait that gives up makes the
+ *     solve return RT_ERR_CUDA (device error code 60).
+ * Rebuilds the rays' sweep groups (tied rays join the V groups) and replans.
+ * Errors: RT_ERR_ARG for another value; RT_ERR_STATE for Gauss-Seidel on a
+ * grid with quadratic interpolation. */
+typedef enum { RT_ITER_JACOBI = 0, RT_ITER_GAUSS_SEIDEL = 1 } rt_iteration;
+rt_status rt_set_iteration(rt_grid g, int scheme);
 
 /* Form of the heating rate Q returned by rt_moments (Sec. 4).
  *   RT_HEAT_INTEGRAL:     Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu), chi_abs = eps chi.

@@ -316,6 +316,18 @@ struct rt_grid_s {
   int interp = RT_INTERP_LINEAR;      // order of the face interpolation (Sec. 3.3)
   void *Opart = nullptr;              // second-order sweeps: group partials of 1 - Lambda*
   size_t opart_groups = 0;
+
+  // Gauss-Seidel iteration (rt_set_iteration): correction weights [nf][9][cells],
+  // the reverse kernel's intensity / weight planes, its barrier counter and the
+  // forward group and ray lists
+  int iteration = RT_ITER_JACOBI;
+  double *gsw = nullptr;
+  bool gs_ready = false;              // gsw matches the medium and the rays
+  void *gsIr = nullptr;
+  size_t gsIr_bytes = 0;
+  unsigned *gs_bar = nullptr;
+  int *gs_list = nullptr;             // forward groups, then forward rays with mu_V < 0
+  size_t gs_list_n = 0;
 };
 
 namespace {
@@ -341,12 +353,16 @@ void build_rays(rt_grid g) {
     const double tmin = std::min(t[0], std::min(t[1], t[2]));
     // first-crossed face; a tie (the ray leaves through an edge) gives identical
     // interpolants on either face, so tied rays go to the least-loaded sweep group
+    // -- except under Gauss-Seidel, where a ray tied with the reverse axis V is a
+    // V ray (its upwind vertices all lie on the plane of V it comes from)
     int best = -1;
+    const int V = g->two_d ? 1 : 2;
     for (int a = 2; a >= 0; --a) {
       if (t[a] != tmin) continue;
       const int sd = r.sgn[a] > 0 ? 0 : 1;
       if (best < 0 || count[a][sd] < count[best][r.sgn[best] > 0 ? 0 : 1]) best = a;
     }
+    if (g->iteration == RT_ITER_GAUSS_SEIDEL && t[V] == tmin) best = V;
     r.axis = best;
     r.s = t[best];
     r.w = g->wq[k];
@@ -752,6 +768,85 @@ rt_status collect_events(std::vector<EventPair> &ev, double *ms_out, int *n_out,
   return RT_OK;
 }
 
+// Gauss-Seidel set-up: the reverse groups (crossed axis V, mu_V < 0), which
+// make_groups leaves adjacent with their rays adjacent in the angle table; the
+// forward groups and the forward rays with mu_V < 0 (device lists); the
+// correction weights (once per medium and ray set); the reverse kernel's
+// buffers.
+template <typename T>
+rt_status gs_setup(rt_grid g, cudaStream_t s, rtk::GsArgs<T> &G) {
+  const int V = g->two_d ? 1 : 2;
+  std::vector<int> fg, fr;
+  int rev_first = -1, nrev = 0, rev0 = 0;
+  for (size_t gi = 0; gi < g->groups.size(); ++gi) {
+    const GroupParam &gp = g->groups[gi];
+    if (gp.axis == V && gp.sa < 0) {
+      if (rev_first < 0) {
+        rev_first = (int)gi;
+        rev0 = gp.a0;
+      } else if (gp.a0 != rev0 + nrev) {
+        return fail(RT_ERR_STATE, "reverse sweep groups are not adjacent in the angle table");
+      }
+      nrev += gp.na;
+    } else {
+      fg.push_back((int)gi);
+    }
+  }
+  if (nrev < 1 || nrev > rtk::kGsMaxRev)
+    return fail(RT_ERR_STATE, "Gauss-Seidel needs 1..%d reverse rays, the angle set gives %d", rtk::kGsMaxRev, nrev);
+  for (int k = 0; k < g->na; ++k) {
+    const RayGeom &r = g->rays[k];
+    if (!(r.axis == V && r.sgn[V] < 0) && g->mu[3 * k + V] < 0.0) fr.push_back(k);
+  }
+  std::vector<int> list(fg);
+  list.insert(list.end(), fr.begin(), fr.end());
+  if (list.size() > g->gs_list_n) {
+    if (g->gs_list) cudaFree(g->gs_list);
+    g->gs_list = nullptr;
+    g->gs_list_n = 0;
+    CU(cudaMalloc((void **)&g->gs_list, list.size() * sizeof(int)));
+    g->gs_list_n = list.size();
+  }
+  CU(cudaMemcpyAsync(g->gs_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  const size_t N = (size_t)N_of(g);
+  if (!g->gsw) CU(cudaMalloc((void **)&g->gsw, 9 * N * sizeof(double)));
+  if (!g->gs_bar) CU(cudaMalloc((void **)&g->gs_bar, sizeof(unsigned)));
+  int cax[3];
+  rtk::plane_axes(V, cax);
+  const size_t plane = (size_t)g->d.n[cax[0]] * g->d.n[cax[1]];
+  const size_t irb = 4 * (size_t)g->d.nf * nrev * plane * sizeof(T);
+  if (irb > g->gsIr_bytes) {
+    if (g->gsIr) cudaFree(g->gsIr);
+    g->gsIr = nullptr;
+    g->gsIr_bytes = 0;
+    CU(cudaMalloc(&g->gsIr, irb));
+    g->gsIr_bytes = irb;
+  }
+  if (!g->gs_ready) {
+    CU(rtk::launch_gs_weights<T>(g->d, V, g->chi, g->rays_d, g->gs_list + fg.size(), (int)fr.size(), g->gsw, s));
+    g->launches++;
+    g->gs_ready = true;
+  }
+  G.V = V;
+  G.nrev = nrev;
+  G.rev0 = rev0;
+  G.fgroups = g->gs_list;
+  G.nfg = (int)fg.size();
+  G.chi = g->chi;
+  G.eps = g->eps;
+  G.B = g->B;
+  G.iden = g->iden;
+  G.S64 = g->S;
+  G.Sfs = g->Sfs;
+  G.J64 = g->J;
+  G.dS = g->Jprev;   // Jprev serves only the eps = 1 test, which Gauss-Seidel leaves to Jacobi
+  G.gsw = g->gsw;
+  G.Ir = (T *)g->gsIr;
+  G.fmask = g->fmask;
+  G.bar = g->gs_bar;
+  return RT_OK;
+}
+
 template <typename T>
 rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *iters, double *resid,
                    bool *converged) {
@@ -763,9 +858,19 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   // float32 rounding scales with the update, not with S (J accumulated in FP64).
   // (the second-order sweep is nonlinear in S -- its clamps -- so it never
   // sweeps increments; it also brings its own Lambda* every iteration)
-  const int incremental = (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR) ? 1 : 0;
+  const bool gs = g->iteration == RT_ITER_GAUSS_SEIDEL && !g->lte;
+  const int incremental =
+      (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR && !gs) ? 1 : 0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
   A.incremental = incremental;
+  rtk::GsArgs<T> GA{};
+  if (gs) {
+    rt_status r = gs_setup<T>(g, s, GA);
+    if (r != RT_OK) return r;
+    A.gs_forward = 1;
+    A.gs_axis = GA.V;
+    GA.A = A;
+  }
   rtk::AliArgs<T> L{};
   L.d = g->d;
   L.ngroups_per_f = (int)g->groups.size();
@@ -797,9 +902,16 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     for (int i = 0; i < m; ++i) {
       rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
       if (r != RT_OK) return r;
-      CU(rtk::launch_ali<T>(L, s));
+      if (gs) {   // reverse phase (updates S), then the sweep copies of the new S
+        CU(rtk::launch_gs_reverse<T>(GA, s));
+        CU(rtk::launch_permute<T>(g->d, g->S, L.SP[0], L.SP[1], L.SP[2], s));
+        g->launches += 2;
+      } else {
+        CU(rtk::launch_ali<T>(L, s));
+        g->launches++;
+      }
       CU(rtk::launch_finish(g->st, s));
-      g->launches += 2;
+      g->launches++;
     }
     enqueued += m;
     CU(cudaMemcpyAsync(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost, s));
@@ -941,6 +1053,7 @@ rt_status plan_precision(rt_grid g) {
     rt_status r = rt_create_grid(&d, &g->sub64);
     if (r != RT_OK) return r;
     if ((r = rt_set_interpolation(g->sub64, g->interp)) != RT_OK) return r;
+    if ((r = rt_set_iteration(g->sub64, g->iteration)) != RT_OK) return r;
     g->bins64 = ill;
   }
   const size_t C = (size_t)g->d.cells, m = ill.size();
@@ -1088,7 +1201,8 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->Gd[0], g->Gd[1],
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
                   g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
-                  g->Jpart, g->Opart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp};
+                  g->Jpart, g->Opart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp,
+                  g->gsw, g->gsIr, g->gs_bar, g->gs_list};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (g->own) cudaStreamDestroy(g->own);
@@ -1193,6 +1307,7 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
   for (int f = 0; f < 6; ++f)
     if ((r = fill_bc_any(g, f, s)) != RT_OK) return r;
   if (g->desc.prec == RT_PREC_MIXED && (r = plan_precision(g)) != RT_OK) return r;
+  g->gs_ready = false;
   g->have_medium = true;
   return RT_OK;
 }
@@ -1389,11 +1504,55 @@ rt_status rt_set_interpolation(rt_grid g, int order) {
   if (order != RT_INTERP_LINEAR && order != RT_INTERP_QUADRATIC)
     return fail(RT_ERR_ARG, "interpolation order must be 1 (linear) or 2 (quadratic), not %d", order);
   if (order == g->interp) return RT_OK;
+  if (order == RT_INTERP_QUADRATIC && g->iteration == RT_ITER_GAUSS_SEIDEL)
+    return fail(RT_ERR_STATE, "the Gauss-Seidel iteration takes linear interpolation");
   g->interp = order;
   plan_groups(g);
   rt_status r = upload_plan_any(g);
   if (r != RT_OK) return r;
   if (g->sub64) return rt_set_interpolation(g->sub64, order);
+  return RT_OK;
+}
+
+rt_status rt_set_iteration(rt_grid g, int scheme) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (scheme != RT_ITER_JACOBI && scheme != RT_ITER_GAUSS_SEIDEL)
+    return fail(RT_ERR_ARG, "iteration scheme must be 0 (Jacobi) or 1 (Gauss-Seidel), not %d", scheme);
+  if (scheme == RT_ITER_GAUSS_SEIDEL && g->interp != RT_INTERP_LINEAR)
+    return fail(RT_ERR_STATE, "the Gauss-Seidel iteration takes linear interpolation");
+  if (scheme == g->iteration) return RT_OK;
+  g->iteration = scheme;
+  // tied rays change sweep groups: rays, their axes' buffers, plan, Lambda*
+  // (same values, other summation order) and the ghosts (laid out per group axis)
+  build_rays(g);
+  cudaStream_t s = g->own;
+  const size_t N = (size_t)N_of(g);
+  for (int a = 0; a < 3; ++a) {
+    if (!g->used_axis[a] || g->SP[a]) continue;
+    CU(cudaMalloc(&g->chiP[a], N * g->tsize));
+    CU(cudaMalloc(&g->SP[a], N * g->tsize));
+  }
+  CU(cudaMemcpyAsync(g->rays_d, g->rays.data(), g->na * sizeof(RayGeom), cudaMemcpyHostToDevice, s));
+  plan_groups(g);
+  rt_status r = upload_plan_any(g);
+  if (r != RT_OK) return r;
+  g->gs_ready = false;
+  if (g->have_medium) {
+    if ((r = permute_any(g, g->chi, g->chiP, s)) != RT_OK) return r;
+    if (g->desc.prec == RT_PREC_FP64) {
+      CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+    } else {
+      CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+    }
+    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
+    g->launches += 2;
+    if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+    g->sp_is_delta = false;
+    if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+    g->fs_total = 0;
+  }
+  CU(cudaStreamSynchronize(s));
+  if (g->sub64) return rt_set_iteration(g->sub64, scheme);
   return RT_OK;
 }
 
@@ -1413,7 +1572,7 @@ rt_status rt_enable_timing(rt_grid g, int enable) {
 
 // Plans chosen by rt_autotune, keyed by problem shape (process-wide cache).
 struct TuneKey {
-  int n[3], nf, n_mu, prec, bc[6], interp;
+  int n[3], nf, n_mu, prec, bc[6], interp, iteration;
   bool operator==(const TuneKey &o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
 };
 struct TuneVal {
@@ -1434,6 +1593,7 @@ TuneKey tune_key(rt_grid g) {
   k.n_mu = g->desc.n_mu;
   k.prec = g->desc.prec;
   k.interp = g->interp;
+  k.iteration = g->iteration;
   return k;
 }
 

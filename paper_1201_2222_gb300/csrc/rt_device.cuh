@@ -1,7 +1,8 @@
 // Device helpers shared by the sweep kernels' translation units (rt_kernels.cu,
-// rt_quad.cu): checked indexing of debug builds, the ghost-intensity lookup and
-// outflow store of the lagged boundary scheme (Sec. 3.5), and the asynchronous
-// shared-memory copies of the pipelined sweeps.
+// rt_quad.cu, rt_gs.cu): checked indexing of debug builds, the ghost-intensity
+// lookup and outflow store of the lagged boundary scheme (Sec. 3.5), the linear
+// segment weights of Eq. 20, and the asynchronous shared-memory copies of the
+// pipelined sweeps.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -130,6 +131,37 @@ template <typename T>
 __device__ __forceinline__ void ghost_async(T *dst, const T *src) {
   if (src) cp_async_elem(dst, src);
   else *dst = T(0);
+}
+
+// ----------------------------------------------------------------- segment weights
+// Linear short-characteristics weights for one segment of optical depth dtau:
+// E = exp(-dtau), Psi0 = 1 - (1 - E)/dtau (weight of S at the cell), and
+// om = 1 - Psi0, all without cancellation: below the threshold Psi0 is the
+// Taylor series of 1 - (1 - e^-x)/x = sum_{n>=1} (-1)^(n+1) x^n/(n+1)!.
+
+__device__ __forceinline__ void seg_weights(float dtau, float &E, float &psi0, float &om) {
+  E = __expf(-dtau);
+  const float q = __fdividef(1.0f - E, dtau);
+  const float x = dtau;
+  const float ser =
+      x * (1.0f / 2 - x * (1.0f / 6 - x * (1.0f / 24 - x * (1.0f / 120 - x * (1.0f / 720 -
+      x * (1.0f / 5040 - x * (1.0f / 40320 - x * (1.0f / 362880))))))));
+  const bool small = dtau < 0.5f;
+  psi0 = small ? ser : 1.0f - q;
+  om = small ? 1.0f - ser : q;
+}
+
+__device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0, double &om) {
+  E = exp(-dtau);
+  if (dtau < 1e-2) {
+    const double x = dtau;
+    psi0 = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 -
+           x * (1.0 / 5040 - x * (1.0 / 40320)))))));
+    om = 1.0 - psi0;
+  } else {
+    om = -expm1(-dtau) / dtau;
+    psi0 = 1.0 - om;
+  }
 }
 
 constexpr int kPipeX0 = 4;   // first interior column of a staged row (16-byte aligned)

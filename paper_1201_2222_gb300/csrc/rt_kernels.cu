@@ -29,37 +29,6 @@ namespace cg = cooperative_groups;
 namespace rtk {
 
 
-// ----------------------------------------------------------------- segment weights
-// Linear short-characteristics weights for one segment of optical depth dtau:
-// E = exp(-dtau), Psi0 = 1 - (1 - E)/dtau (weight of S at the cell), and
-// om = 1 - Psi0, all without cancellation: below the threshold Psi0 is the
-// Taylor series of 1 - (1 - e^-x)/x = sum_{n>=1} (-1)^(n+1) x^n/(n+1)!.
-
-__device__ __forceinline__ void seg_weights(float dtau, float &E, float &psi0, float &om) {
-  E = __expf(-dtau);
-  const float q = __fdividef(1.0f - E, dtau);
-  const float x = dtau;
-  const float ser =
-      x * (1.0f / 2 - x * (1.0f / 6 - x * (1.0f / 24 - x * (1.0f / 120 - x * (1.0f / 720 -
-      x * (1.0f / 5040 - x * (1.0f / 40320 - x * (1.0f / 362880))))))));
-  const bool small = dtau < 0.5f;
-  psi0 = small ? ser : 1.0f - q;
-  om = small ? 1.0f - ser : q;
-}
-
-__device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0, double &om) {
-  E = exp(-dtau);
-  if (dtau < 1e-2) {
-    const double x = dtau;
-    psi0 = x * (1.0 / 2 - x * (1.0 / 6 - x * (1.0 / 24 - x * (1.0 / 120 - x * (1.0 / 720 -
-           x * (1.0 / 5040 - x * (1.0 / 40320)))))));
-    om = 1.0 - psi0;
-  } else {
-    om = -expm1(-dtau) / dtau;
-    psi0 = 1.0 - om;
-  }
-}
-
 // ------------------------------------------------------------------------ sweep
 
 
@@ -81,6 +50,7 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
+  if (A.gs_forward && gp.axis == A.gs_axis && gp.sa < 0) return;   // swept in the reverse phase
   if (gp.na > A.ray_slots) {   // plan inconsistent with the shared-memory layout: refuse to run
     if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
     return;
@@ -298,6 +268,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_tiled_kernel(
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
+  if (A.gs_forward && gp.axis == A.gs_axis && gp.sa < 0) return;   // swept in the reverse phase
   if (gp.na > A.ray_slots) {   // plan inconsistent with the shared-memory layout: refuse to run
     if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
     return;
@@ -592,6 +563,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
+  if (A.gs_forward && gp.axis == A.gs_axis && gp.sa < 0) return;   // swept in the reverse phase
   if (gp.na > A.ray_slots) {
     if (threadIdx.x == 0) atomicCAS(&A.st->err, 0, 30);
     return;

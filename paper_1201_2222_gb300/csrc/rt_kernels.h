@@ -29,6 +29,8 @@ struct SweepArgs {
   int cluster;               // CTAs per cluster = strips per plane
   int incremental;           // ALI solve sweeping increments after its first formal solution
   int ray_slots;             // shared-memory planes per ray slot (>= rays of any group)
+  int gs_forward;            // 1: Gauss-Seidel forward phase -- groups crossing the
+  int gs_axis;               //    gs_axis face with mu < 0 (the reverse rays) do nothing
 };
 
 template <typename T>
@@ -47,6 +49,40 @@ struct AliArgs {
   int incremental;           // partials are increments of J; SP receives dS
   const unsigned char *fmask; // frequencies solved elsewhere (skipped; NULL = none)
 };
+
+// Reverse phase of the Gauss-Seidel ALI (rt_gs.cu, Sec. 3.4): the reverse rays
+// (crossed face normal to the reverse axis V, mu_V < 0) swept plane by plane from
+// the top of V down, each plane's S updated with the freshest J before the next
+// plane is swept.  One cooperative launch; the planes are separated by a grid
+// barrier whose waits are bounded (on expiry: st->err = kGsBarrierTimeout).
+constexpr int kGsMaxRev = 64;          // reverse rays per frequency
+constexpr int kGsThreads = 256;
+constexpr int kGsBarrierTimeout = 60;
+
+template <typename T>
+struct GsArgs {
+  SweepArgs<T> A;            // grid, ghosts, inflow faces, solve state
+  int V;                     // reverse axis (2; 1 in 2D)
+  int nrev;                  // reverse rays, A.ang[rev0 .. rev0 + nrev)
+  int rev0;
+  const int *fgroups;        // the forward groups (their J partials are summed)
+  int nfg;
+  const double *chi, *eps, *B, *iden;
+  double *S64, *Sfs, *J64, *dS;
+  const double *gsw;         // [nf][9][cells] first-order correction weights
+  T *Ir;                     // [4][nf][nrev][plane]: intensities (2 planes), Psi0, Psi-
+  const unsigned char *fmask;
+  unsigned *bar;             // grid-barrier counter, zero at launch
+};
+
+// Correction weights of the forward rays: for each cell and each of the 3 x 3
+// cells of the plane above (V + 1), sum over forward rays with an upwind vertex
+// there of w Psi- (vertex weight).  `fwd` lists the forward rays with mu_V < 0.
+template <typename T>
+cudaError_t launch_gs_weights(const Dims &d, int V, const double *chi, const RayGeom *rays,
+                              const int *fwd, int nfwd, double *gsw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gs_reverse(const GsArgs<T> &G, cudaStream_t s);
 
 // Sets, once per kernel and device, the largest dynamic shared memory the kernel
 // may request and permission for non-portable cluster sizes.  The values never

@@ -19,6 +19,7 @@ PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 HEAT_INTEGRAL, HEAT_DIFFERENTIAL, HEAT_SWITCH = 0, 1, 2
 INTERP_LINEAR, INTERP_QUADRATIC = 1, 2
+ITER_JACOBI, ITER_GAUSS_SEIDEL = 0, 1
 
 RT_OK = 0
 RT_ERR_ARG = -1
@@ -90,6 +91,7 @@ _SIGS = {
     "rt_enable_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_set_heating_form": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_set_interpolation": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rt_set_iteration": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(rt_stats)]),
     "rt_set_sweep_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "rt_get_sweep_plan": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
@@ -336,6 +338,12 @@ class Grid:
         o = self._opts(on_device=on_device)
         _check(load().rt_get_S(self._h, self._ptr(S), 1 if on_device else 0, ctypes.byref(o)))
         return S
+
+    def set_iteration(self, scheme):
+        """ALI scheme: ITER_JACOBI / "jacobi" or ITER_GAUSS_SEIDEL / "gauss_seidel"."""
+        if isinstance(scheme, str):
+            scheme = {"jacobi": ITER_JACOBI, "gauss_seidel": ITER_GAUSS_SEIDEL}[scheme.lower()]
+        _check(load().rt_set_iteration(self._h, int(scheme)))
 
     def set_interpolation(self, order):
         """Face interpolation: INTERP_LINEAR / "linear" or INTERP_QUADRATIC / "quadratic"."""

@@ -1,0 +1,126 @@
+"""GPU parity of the Gauss-Seidel ALI (rt_set_iteration) against the oracle's.
+
+* Iteration by iteration: S after 1, 2 and 4 iterations (tol 0, the solve stops
+  on max_iter) equals the oracle's Gauss-Seidel S: FP64 to 1e-11 relative, the
+  mixed path (float32 sweeps of S itself) within float32 rounding amplified by
+  the update (2e-4 relative, floor 1e-6 of the bin's largest S).
+* Converged: same iteration count (FP64; within one for mixed), S and J of the
+  final formal solution within the FP64 tolerance, and fewer iterations than
+  the library's own Jacobi solve.
+* Cases span the reverse axis bounded (the top plane's ghost correction) and
+  periodic, 2D (reverse axis y), several frequencies, tied rays (LQ6, LQ8) and
+  planes of several tiles with a ragged last tile.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1201_2222_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P, V, T, F = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1201_2222_gb300 import build, rt as _rt
+    build.build()
+    return _rt
+
+
+CASES = {
+    "atmosphere": lambda: W.stratified_atmosphere(12, n_mu=4, nxy=10),
+    "periodic_lq6": lambda: W.random_box(10, 9, 11, seed=21, n_mu=6, bc_lo=(P, P, P), bc_hi=(P, P, P)),
+    "two_d": lambda: W.random_box(13, 11, 1, seed=22, n_mu=4, bc_lo=(P, T, P), bc_hi=(P, V, P)),
+    "multi_freq": lambda: W.random_box(7, 8, 9, seed=23, n_mu=4, nf=3, bc_lo=(T, P, T), bc_hi=(V, P, V)),
+    "ragged_lq8": lambda: W.random_box(33, 17, 9, seed=24, n_mu=8, bc_lo=(P, V, T), bc_hi=(P, T, V)),
+}
+
+
+def _gpu(rt, p, prec, scheme="gauss_seidel"):
+    g = rt.Grid.from_problem(p, prec=prec)
+    g.set_iteration(scheme)
+    g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+    return g
+
+
+def _binwise_ok(x, ref, rtol, floor):
+    binmax = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1).reshape((-1,) + (1,) * (ref.ndim - 1))
+    return bool(np.all(np.abs(x - ref) <= rtol * np.abs(ref) + floor * binmax))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_iterations_match_the_oracle(rt, case, prec):
+    p = CASES[case]()
+    og = O.Grid.from_problem(p)
+    g = _gpu(rt, p, prec)
+    for k in (1, 2, 4):
+        ref = O.ali_solve(og, p.chi, p.eps, p.B, p.freq_w, tol=0.0, max_iter=k, moments=False,
+                          method="gauss_seidel", nthreads=O.max_threads())
+        iters, resid, st = g.ali_solve(tol=0.0, max_iter=k, raise_on_fail=False)
+        assert st == rt.RT_ERR_NOT_CONVERGED and iters == k
+        S = g.get_S()
+        if prec == "fp64":
+            np.testing.assert_allclose(S, ref["S"], rtol=1e-11)
+            assert resid == pytest.approx(ref["resid"], rel=1e-9)
+        else:
+            assert _binwise_ok(S, ref["S"], 2e-4, 1e-6), (case, k)
+            assert resid == pytest.approx(ref["resid"], rel=1e-2, abs=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["atmosphere", "periodic_lq6", "two_d"])
+def test_converged_solve(rt, case, prec):
+    p = CASES[case]()
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    og = O.Grid.from_problem(p)
+    ref = O.ali_solve(og, p.chi, p.eps, p.B, p.freq_w, tol=tol, max_iter=5000, moments=True,
+                      method="gauss_seidel", nthreads=O.max_threads())
+    assert ref["converged"]
+    g = _gpu(rt, p, prec)
+    iters, resid, st = g.ali_solve(tol=tol, max_iter=5000)
+    assert st == rt.RT_OK and resid <= tol
+    S = g.get_S()
+    m = g.moments()
+    if prec == "fp64":
+        assert iters == ref["iters"]
+        np.testing.assert_allclose(S, ref["S"], rtol=1e-9)
+        np.testing.assert_allclose(m["J"], ref["J"], rtol=1e-9)
+        np.testing.assert_allclose(m["K"], ref["K"], rtol=1e-8, atol=1e-12 * np.abs(ref["K"]).max())
+    else:
+        assert abs(iters - ref["iters"]) <= 1, (iters, ref["iters"])
+        assert _binwise_ok(S, ref["S"], 1e-3, 1e-5)
+        assert _binwise_ok(m["J"], ref["J"], 1e-3, 1e-5)
+    jac = _gpu(rt, p, prec, "jacobi")
+    it_j, _, st_j = jac.ali_solve(tol=tol, max_iter=5000)
+    assert st_j == rt.RT_OK and it_j > iters
+
+
+def test_fixed_point_is_the_jacobi_one(rt):
+    p = W.stratified_atmosphere(16, n_mu=4, nxy=8)
+    gs = _gpu(rt, p, "fp64")
+    gs.ali_solve(tol=1e-11, max_iter=5000)
+    jac = _gpu(rt, p, "fp64", "jacobi")
+    jac.ali_solve(tol=1e-11, max_iter=5000)
+    np.testing.assert_allclose(gs.get_S(), jac.get_S(), rtol=1e-8)
+
+
+def test_switching_schemes_and_validation(rt):
+    p = W.random_box(6, 5, 7, seed=25, n_mu=6)
+    g = _gpu(rt, p, "fp64", "jacobi")
+    J0 = g.formal_solve(p.B)
+    g.set_iteration("gauss_seidel")           # regroups tied rays; same formal solution
+    np.testing.assert_allclose(g.formal_solve(p.B), J0, rtol=1e-13)
+    with pytest.raises(rt.RTError):
+        g.set_interpolation("quadratic")
+    with pytest.raises(rt.RTError):
+        g.set_iteration(2)
+    g.set_iteration("jacobi")
+    g.set_interpolation("quadratic")
+    with pytest.raises(rt.RTError):
+        g.set_iteration("gauss_seidel")
