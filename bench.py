@@ -211,7 +211,7 @@ def run_gpu(args):
         dist = tdist
     else:
         torch.cuda.set_device(0)
-    from paper_1201_2222_gb300 import build, rt
+    from paper_1201_2222_gb300 import build, rt, workloads as W
     build.build()
     p = workload()
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -338,6 +338,28 @@ def run_gpu(args):
                 "plan": gq.sweep_plan()}
         gq.close()
 
+    # the Gauss-Seidel scheme against Jacobi on the stratified scattering
+    # atmosphere (32^3, LQ4, eps 1e-2, FP64, tol 1e-6): iterations and solve time
+    gs = None
+    if not args.skip_gs:
+        pa = W.stratified_atmosphere(32)
+        gs = {"workload": f"{pa.name} (FP64, tol {pa.tol:g})"}
+        for scheme in ("jacobi", "gauss_seidel"):
+            ga = rt.Grid.from_problem(pa, prec=rt.FP64)
+            ga.set_iteration(scheme)
+            ga.set_opacity_source(pa.chi, pa.eps, pa.B, pa.freq_w)
+            ga.ali_solve(tol=pa.tol, max_iter=5000)
+            best = math.inf
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                ita, _, _ = ga.ali_solve(tol=pa.tol, max_iter=5000)
+                best = min(best, time.perf_counter() - t)
+            gs[scheme] = {"iters": ita, "ms_per_solve": 1e3 * best, "ms_per_iter": 1e3 * best / ita}
+            ga.close()
+        gs["iteration_ratio"] = gs["jacobi"]["iters"] / gs["gauss_seidel"]["iters"]
+        gs["time_ratio"] = gs["jacobi"]["ms_per_solve"] / gs["gauss_seidel"]["ms_per_solve"]
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -358,6 +380,7 @@ def run_gpu(args):
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
         "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
         "fp64_path": fp64,
+        "gauss_seidel": gs,
         "quadratic_path": quad,
         "sweep_plan": g.sweep_plan(),
         "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[g.sweep_plan()["variant"]],
@@ -457,6 +480,7 @@ def main(argv=None):
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU comparison solves")
     ap.add_argument("--skip-quad", action="store_true", help="omit the second-order formal-solution rate")
+    ap.add_argument("--skip-gs", action="store_true", help="omit the Gauss-Seidel against Jacobi comparison")
     ap.add_argument("--profile", action="store_true", help="one short solve for profilers")
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")

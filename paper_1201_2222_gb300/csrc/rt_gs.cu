@@ -40,9 +40,9 @@ namespace {
 // groups: u = cax[0], v = cax[1] (V = z: x, y; V = y in 2D: x, z).
 __host__ __device__ inline int slot_of(int ou, int ov) { return (ov + 1) * 3 + (ou + 1); }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
   unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -57,7 +57,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned target, SolveState *st) {
     __threadfence();
     atomicAdd(bar, 1u);
     long long polls = 0;
-    while (ld_acquire(bar) < target) {
+    while (ld_relaxed(bar) < target) {   // the fence below orders what follows
       if (*(volatile int *)&st->err == kGsBarrierTimeout || ++polls > (1LL << 22)) {
         atomicCAS(&st->err, 0, kGsBarrierTimeout);
         good = 0;
@@ -167,7 +167,7 @@ cudaError_t launch_gs_weights(const Dims &d, int V, const double *chi, const Ray
 // corrections.  The planes of all frequencies advance together, one grid
 // barrier apart.
 template <typename T>
-__global__ void __launch_bounds__(kGsThreads) gs_reverse_kernel(const GsArgs<T> G) {
+__global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<T> G) {
   const SweepArgs<T> &A = G.A;
   SolveState *st = A.st;
   if (st->done) return;   // converged earlier in this batch: every block returns
@@ -175,8 +175,10 @@ __global__ void __launch_bounds__(kGsThreads) gs_reverse_kernel(const GsArgs<T> 
   __shared__ double jr[kGsThreads];
   __shared__ double dsm[kGsThreads];
   __shared__ double rmax_s[kGsThreads / 32];
+  __shared__ int fgs[kMaxGroups];
   const int nrev = G.nrev;
   for (int k = threadIdx.x; k < nrev; k += blockDim.x) P[k] = A.ang[G.rev0 + k];
+  for (int k = threadIdx.x; k < G.nfg; k += blockDim.x) fgs[k] = G.fgroups[k];
   int cax[3];
   plane_axes(G.V, cax);
   const int Nu = pick3(A.d.n, cax[0]), Nv = pick3(A.d.n, cax[1]), Nw = pick3(A.d.n, cax[2]);
@@ -258,31 +260,49 @@ __global__ void __launch_bounds__(kGsThreads) gs_reverse_kernel(const GsArgs<T> 
       // ---- 2. the cell's update with the freshest J
       if (threadIdx.x < TC && live) {
         const long long i = fc + c;
+        // the forward partials and the correction's 9 weights and changes: all
+        // loads issued before any is used (latency, not bandwidth, bounds this)
+        const T *jp = A.Jpart + (long long)f * cells + c;
+        const long long gstride = (long long)nf * cells;
         double JF;
         if (sizeof(T) == 4) {   // float partials summed as an exact float pair (TwoSum)
           float hi = 0.f, lo = 0.f;
-          for (int q = 0; q < G.nfg; ++q) {
-            const float x = (float)A.Jpart[((long long)G.fgroups[q] * nf + f) * cells + c];
-            const float s2 = hi + x;
-            const float bp = s2 - hi;
-            lo += (hi - (s2 - bp)) + (x - bp);
-            hi = s2;
+          for (int q0 = 0; q0 < G.nfg; q0 += 8) {
+            float xs[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xs[q] = q0 + q < G.nfg ? (float)jp[fgs[q0 + q] * gstride] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float x = xs[q];
+              const float s2 = hi + x;
+              const float bp = s2 - hi;
+              lo += (hi - (s2 - bp)) + (x - bp);
+              hi = s2;
+            }
           }
           JF = (double)hi + (double)lo;
         } else {
           JF = 0.0;
-          for (int q = 0; q < G.nfg; ++q) JF += (double)A.Jpart[((long long)G.fgroups[q] * nf + f) * cells + c];
+          for (int q0 = 0; q0 < G.nfg; q0 += 8) {
+            double xs[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xs[q] = q0 + q < G.nfg ? (double)jp[fgs[q0 + q] * gstride] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) JF += xs[q];
+          }
         }
         double corr = 0.0;
         if (w + 1 < Nw) {
+          double cw[9], ds[9];
 #pragma unroll
           for (int q = 0; q < 9; ++q) {
-            const double cw = G.gsw[((long long)f * 9 + q) * cells + c];
-            if (cw == 0.0) continue;
             const int ou = q % 3 - 1, ov = q / 3 - 1;
             const int mu_ = map_coord(u + ou, Nu, perU), mv_ = map_coord(v + ov, Nv, perV);
-            corr += cw * ldcg(G.dS + fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)(w + 1) * csw);
+            cw[q] = G.gsw[((long long)f * 9 + q) * cells + c];
+            ds[q] = ldcg(G.dS + fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)(w + 1) * csw);
           }
+#pragma unroll
+          for (int q = 0; q < 9; ++q) corr += cw[q] * ds[q];
         }
         double JR = 0.0;
         for (int r = 0; r < nrev; ++r) JR += jr[r * TC + threadIdx.x];
