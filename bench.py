@@ -413,6 +413,8 @@ def run_profile(args):
     g = rt.Grid.from_problem(p, prec=rt.FP64 if args.fp64 else rt.MIXED)
     if args.quadratic:
         g.set_interpolation(rt.INTERP_QUADRATIC)
+    if args.gauss_seidel:
+        g.set_iteration(rt.ITER_GAUSS_SEIDEL)
     g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
     if args.plan:
         v, apg, c, th = (int(x) for x in (args.plan + ",0").split(",")[:4])
@@ -485,6 +487,7 @@ def main(argv=None):
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--fp64", action="store_true", help="with --profile: the FP64 path")
     ap.add_argument("--quadratic", action="store_true", help="with --profile: the second-order sweep")
+    ap.add_argument("--gauss-seidel", action="store_true", help="with --profile: the Gauss-Seidel iteration")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
     ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster[,threads] instead of autotuning")
     ap.add_argument("--serve", type=int, default=0, help="run N requests of the serving stream instead")

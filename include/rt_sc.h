@@ -316,6 +316,7 @@ typedef struct {
                                              copied at submission (freq_w may be NULL: 1) */
   double tol;
   int max_iter;
+  int iteration;            /* RT_ITER_JACOBI (0) / RT_ITER_GAUSS_SEIDEL (linear only) */
 } rt_request;
 enum { RT_REQ_QUEUED = 0, RT_REQ_RUNNING = 1, RT_REQ_DONE = 2 };
 typedef struct {

@@ -29,6 +29,7 @@ struct Request {
   long long id = 0;
   rt_grid_desc desc{};
   int interp = RT_INTERP_LINEAR;
+  int iteration = RT_ITER_JACOBI;
   std::vector<double> chi, eps, B, fw;
   double tol = 1e-6;
   int max_iter = 1000;
@@ -65,6 +66,7 @@ void run_solve(Request *r, int device) {
   rt_grid g = nullptr;
   rt_status st = rt_create_grid(&r->desc, &g);
   if (st == RT_OK && r->interp != RT_INTERP_LINEAR) st = rt_set_interpolation(g, r->interp);
+  if (st == RT_OK && r->iteration != RT_ITER_JACOBI) st = rt_set_iteration(g, r->iteration);
   if (st == RT_OK)
     st = rt_set_opacity_source(g, r->chi.data(), r->eps.data(), r->B.data(), r->fw.data(), 0);
   int iters = 0;
@@ -176,6 +178,10 @@ rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
   if (st != RT_OK) return st;
   if (req->interp != 0 && req->interp != RT_INTERP_LINEAR && req->interp != RT_INTERP_QUADRATIC)
     return rt_internal_error(RT_ERR_ARG, "rt_submit: interp must be 0, 1 or 2");
+  if (req->iteration != RT_ITER_JACOBI && req->iteration != RT_ITER_GAUSS_SEIDEL)
+    return rt_internal_error(RT_ERR_ARG, "rt_submit: iteration must be 0 or 1");
+  if (req->iteration == RT_ITER_GAUSS_SEIDEL && req->interp == RT_INTERP_QUADRATIC)
+    return rt_internal_error(RT_ERR_ARG, "rt_submit: the Gauss-Seidel iteration takes linear interpolation");
   Request *r = new Request();
   r->desc = req->desc;
   r->interp = req->interp == 0 ? RT_INTERP_LINEAR : req->interp;
@@ -187,6 +193,7 @@ rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
   else r->fw.assign((size_t)req->desc.nfreq, 1.0);
   r->tol = req->tol;
   r->max_iter = req->max_iter;
+  r->iteration = req->iteration;
   r->footprint = fp;
   r->t_submit = Clock::now();
   {

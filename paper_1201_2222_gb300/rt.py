@@ -55,7 +55,7 @@ class rt_server_opts(ctypes.Structure):
 class rt_request(ctypes.Structure):
     _fields_ = [("desc", rt_grid_desc), ("interp", ctypes.c_int), ("chi", ctypes.c_void_p),
                 ("eps", ctypes.c_void_p), ("B", ctypes.c_void_p), ("freq_w", ctypes.c_void_p),
-                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("iteration", ctypes.c_int)]
 
 
 class rt_request_info(ctypes.Structure):
@@ -404,13 +404,15 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, p, prec=MIXED, tol=None, max_iter=1000, interp=INTERP_LINEAR):
+    def submit(self, p, prec=MIXED, tol=None, max_iter=1000, interp=INTERP_LINEAR, iteration=ITER_JACOBI):
         """Queue an ALI solve of the workloads.Problem ``p``; returns its id."""
         if isinstance(interp, str):
             interp = {"linear": INTERP_LINEAR, "quadratic": INTERP_QUADRATIC}[interp.lower()]
+        if isinstance(iteration, str):
+            iteration = {"jacobi": ITER_JACOBI, "gauss_seidel": ITER_GAUSS_SEIDEL}[iteration.lower()]
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.chi, p.eps, p.B, p.freq_w)]
         req = rt_request(_desc_of(p, prec), int(interp), *[a.ctypes.data for a in arrs],
-                         float(p.tol if tol is None else tol), int(max_iter))
+                         float(p.tol if tol is None else tol), int(max_iter), int(iteration))
         rid = ctypes.c_longlong(0)
         _check(load().rt_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
         self._shapes[rid.value] = (p.nf, p.nz, p.ny, p.nx)

@@ -30,15 +30,18 @@ def _mix():
         d = dict(d, shape=shape, eps=max(d["eps"], 0.05))
         prec = "mixed" if i % 3 else "fp64"
         interp = "quadratic" if i % 4 == 3 else "linear"
-        # the second-order mixed path sweeps S itself: float32 rounding limits tol
-        tol = 1e-5 if interp == "quadratic" else 1e-6
-        reqs.append((W.build_request(d, tol=tol), prec, interp))
+        scheme = "gauss_seidel" if i % 4 == 2 else "jacobi"
+        # the second-order and Gauss-Seidel mixed paths sweep S itself: float32
+        # rounding limits tol
+        tol = 1e-5 if (interp == "quadratic" or scheme == "gauss_seidel") else 1e-6
+        reqs.append((W.build_request(d, tol=tol), prec, interp, scheme))
     return reqs
 
 
-def _alone(rt, p, prec, interp):
+def _alone(rt, p, prec, interp, scheme):
     g = rt.Grid.from_problem(p, prec=prec)
     g.set_interpolation(interp)
+    g.set_iteration(scheme)
     g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
     iters, resid, st = g.ali_solve(tol=p.tol, max_iter=3000)
     m = g.moments()
@@ -48,7 +51,8 @@ def _alone(rt, p, prec, interp):
 def test_results_in_the_mix_equal_results_alone(rt):
     reqs = _mix()
     srv = rt.Server(workers=3)
-    ids = [srv.submit(p, prec=prec, interp=interp, max_iter=3000) for p, prec, interp in reqs]
+    ids = [srv.submit(p, prec=prec, interp=interp, iteration=scheme, max_iter=3000)
+           for p, prec, interp, scheme in reqs]
     seen_running = 0
     while True:
         infos = [srv.poll(i) for i in ids]
@@ -57,11 +61,11 @@ def test_results_in_the_mix_equal_results_alone(rt):
             break
         time.sleep(0.002)
     assert seen_running >= 2           # solves overlapped
-    for rid, (p, prec, interp) in zip(ids, reqs):
+    for rid, (p, prec, interp, scheme) in zip(ids, reqs):
         info = srv.wait(rid, timeout=60)
         assert info["status"] == rt.RT_OK and info["resid"] <= p.tol
         J, S, Q, st = srv.fetch(rid)
-        iters, J1, S1, Q1 = _alone(rt, p, prec, interp)
+        iters, J1, S1, Q1 = _alone(rt, p, prec, interp, scheme)
         assert info["iters"] == iters
         np.testing.assert_array_equal(J, J1)
         np.testing.assert_array_equal(S, S1)
@@ -71,11 +75,12 @@ def test_results_in_the_mix_equal_results_alone(rt):
 
 def test_admission_by_footprint(rt):
     reqs = _mix()[:5]
-    fps = [rt.grid_footprint(p, prec) for p, prec, _ in reqs]
-    assert all(f > 8 * 11 * p.chi.size for f, (p, _, _) in zip(fps, reqs))
+    fps = [rt.grid_footprint(p, prec) for p, prec, _, _ in reqs]
+    assert all(f > 8 * 11 * p.chi.size for f, (p, _, _, _) in zip(fps, reqs))
     # a budget below every request: they run one at a time (each alone when nothing else runs)
     srv = rt.Server(workers=3, device_bytes=1)
-    ids = [srv.submit(p, prec=prec, interp=interp, max_iter=3000) for p, prec, interp in reqs]
+    ids = [srv.submit(p, prec=prec, interp=interp, iteration=scheme, max_iter=3000)
+           for p, prec, interp, scheme in reqs]
     while True:
         infos = [srv.poll(i) for i in ids]
         assert sum(x["state"] == rt.REQ_RUNNING for x in infos) <= 1
