@@ -188,10 +188,10 @@ rt_status rt_set_interpolation(rt_grid g, int order);
  *     already see the new S above), and the reverse rays' intensities on that
  *     plane then take the change of the S they read from it (Psi0 dS, and on
  *     the top plane of a bounded V axis Psi- times the ghost layer's change).
- *     The fixed point is the Jacobi one; fewer iterations reach it.  Sweeps
- *     are never incremental (RT_PREC_MIXED grids sweep S itself, so float32
- *     rounding limits tol to about 1e-7 / eps); a medium with eps = 1
- *     everywhere uses the Jacobi test of Eq. 25 on J.  Needs linear
+ *     The fixed point is the Jacobi one; fewer iterations reach it.  As with
+ *     Jacobi, RT_PREC_MIXED grids sweep changes after the first iteration
+ *     (the forward rays' J and the reverse rays' J kept in FP64); a medium with
+ *     eps = 1 everywhere uses the Jacobi test of Eq. 25 on J.  Needs linear
  *     interpolation.  The reverse phase is one cooperative launch whose planes
  *     are separated by grid barriers; a barrier wait that gives up makes the
  *     solve return RT_ERR_CUDA (device error code 60).

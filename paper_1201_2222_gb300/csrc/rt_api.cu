@@ -328,6 +328,8 @@ struct rt_grid_s {
   unsigned *gs_bar = nullptr;
   int *gs_list = nullptr;             // forward groups, then forward rays with mu_V < 0
   size_t gs_list_n = 0;
+  double *gs_acc = nullptr;           // incremental solves: J of the forward and of the reverse
+                                      // rays [2][nf][cells]
 };
 
 namespace {
@@ -774,7 +776,7 @@ rt_status collect_events(std::vector<EventPair> &ev, double *ms_out, int *n_out,
 // correction weights (once per medium and ray set); the reverse kernel's
 // buffers.
 template <typename T>
-rt_status gs_setup(rt_grid g, cudaStream_t s, rtk::GsArgs<T> &G) {
+rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &G) {
   const int V = g->two_d ? 1 : 2;
   std::vector<int> fg, fr;
   int rev_first = -1, nrev = 0, rev0 = 0;
@@ -840,7 +842,15 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, rtk::GsArgs<T> &G) {
   G.Sfs = g->Sfs;
   G.J64 = g->J;
   G.dS = g->Jprev;   // Jprev serves only the eps = 1 test, which Gauss-Seidel leaves to Jacobi
+  G.incremental = incremental ? 1 : 0;
+  G.JF64 = G.JR64 = nullptr;
+  if (incremental) {
+    if (!g->gs_acc) CU(cudaMalloc((void **)&g->gs_acc, 2 * N * sizeof(double)));
+    G.JF64 = g->gs_acc;
+    G.JR64 = g->gs_acc + N;
+  }
   G.gsw = g->gsw;
+  G.SPV = (T *)g->SP[V];
   G.Ir = (T *)g->gsIr;
   G.fmask = g->fmask;
   G.bar = g->gs_bar;
@@ -859,13 +869,12 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   // (the second-order sweep is nonlinear in S -- its clamps -- so it never
   // sweeps increments; it also brings its own Lambda* every iteration)
   const bool gs = g->iteration == RT_ITER_GAUSS_SEIDEL && !g->lte;
-  const int incremental =
-      (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR && !gs) ? 1 : 0;
+  const int incremental = (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR) ? 1 : 0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
   A.incremental = incremental;
   rtk::GsArgs<T> GA{};
   if (gs) {
-    rt_status r = gs_setup<T>(g, s, GA);
+    rt_status r = gs_setup<T>(g, s, incremental != 0, GA);
     if (r != RT_OK) return r;
     A.gs_forward = 1;
     A.gs_axis = GA.V;
@@ -902,9 +911,9 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     for (int i = 0; i < m; ++i) {
       rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
       if (r != RT_OK) return r;
-      if (gs) {   // reverse phase (updates S), then the sweep copies of the new S
+      if (gs) {   // reverse phase (updates S), then the sweep copies of the new S (or dS)
         CU(rtk::launch_gs_reverse<T>(GA, s));
-        CU(rtk::launch_permute<T>(g->d, g->S, L.SP[0], L.SP[1], L.SP[2], s));
+        CU(rtk::launch_permute<T>(g->d, incremental ? GA.dS : g->S, L.SP[0], L.SP[1], L.SP[2], s));
         g->launches += 2;
       } else {
         CU(rtk::launch_ali<T>(L, s));
@@ -936,7 +945,8 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   *converged = hs.converged != 0;
   g->fs_total = hs.fs_count;
   g->last_fs_from_Sfs = !g->lte;
-  g->last_incremental = incremental != 0;
+  // (Gauss-Seidel: the J returned is that of a formal solution of Sfs)
+  g->last_incremental = incremental != 0 && !gs;
   g->sp_is_delta = incremental != 0;
   return RT_OK;
 }
@@ -1202,7 +1212,7 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
                   g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
                   g->Jpart, g->Opart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp,
-                  g->gsw, g->gsIr, g->gs_bar, g->gs_list};
+                  g->gsw, g->gsIr, g->gs_bar, g->gs_list, g->gs_acc};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (g->own) cudaStreamDestroy(g->own);

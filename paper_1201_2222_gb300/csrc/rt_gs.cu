@@ -162,17 +162,27 @@ cudaError_t launch_gs_weights(const Dims &d, int V, const double *chi, const Ray
 // ------------------------------------------------------------------ reverse phase
 // A block takes tiles of TC cells of one plane and frequency; its thread t
 // sweeps reverse ray t / TC at cell t % TC (TC = kGsThreads / nrev).  Per tile:
-// the rays' intensities (upwind plane above), then the cells' updates (one
-// thread per cell, the rays' J terms summed in ray order), then the rays'
-// corrections.  The planes of all frequencies advance together, one grid
-// barrier apart.
+// the cells' inputs that do not depend on this plane's rays, the rays'
+// intensities (upwind plane above), the cells' updates (one thread per cell, the
+// rays' J terms summed in ray order), then the rays' corrections.  The planes of
+// all frequencies advance together, one grid barrier apart.
+//
+// Incremental solves (float32 grids after their first iteration) sweep changes:
+// the reverse rays' intensities at plane k differ from the last iteration's
+// corrected ones by the SC update of (the change of S on the plane above, this
+// iteration's dS; of ghost S read elsewhere, none where the last top-plane
+// correction covered it, else the last iteration's dS; of the lagged ghost
+// intensities, their increments), with no change of S0 yet.  J of the forward
+// and of the reverse rays is kept in FP64 and advanced by the swept changes, so
+// float32 rounding scales with the change, not with J.
 template <typename T>
 __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<T> G) {
   const SweepArgs<T> &A = G.A;
   SolveState *st = A.st;
   if (st->done) return;   // converged earlier in this batch: every block returns
   __shared__ AngleParam<T> P[kGsMaxRev];
-  __shared__ double jr[kGsThreads];
+  __shared__ T jr[kGsThreads];
+  __shared__ T jp0[kGsThreads];
   __shared__ double dsm[kGsThreads];
   __shared__ double rmax_s[kGsThreads / 32];
   __shared__ int fgs[kMaxGroups];
@@ -196,6 +206,8 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
   unsigned nbar = 0;
   const unsigned nblk = gridDim.x;
   double rmax = 0.0;
+  const bool inc = G.incremental && st->iter > 0;    // sweep changes
+  const bool emit = G.incremental && st->iter == 0;  // full sweep that records ghost increments
 
   // S of the previous formal solution (the old S, read where a plane has not
   // been updated yet) -- every cell, before any update
@@ -205,9 +217,21 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
   if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
 
   const int fs = st->fs_count;
-  const T *Gp = A.G[fs & 1];
-  T *Gn = A.G[(fs & 1) ^ 1];
+  const int prev = fs & 1;
+  const T *Gp = A.G[prev];
+  T *Gn = A.G[prev ^ 1];
+  const T *Gsrc = inc ? A.Gd[prev] : Gp;     // inflow: ghost increments or ghosts
+  T *Gdn = G.incremental ? A.Gd[prev ^ 1] : nullptr;
   const bool ghost_fix = !perW || Nw == 1;   // the top plane's ghost layer copies the top plane
+
+  // outflow ghosts of reverse ray p at cell (u, v, w): value I (or its change)
+  auto store_ghosts = [&](const AngleParam<T> &p, int f, int u, int v, int w, T I) {
+    const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
+    if (perU && u == (p.su > 0 ? Nu - 1 : 0)) ghost_store(Gp, Gn, Gdn, gb + plane + (long long)w * Nv + v, I, inc, emit);
+    if (perV && v == (p.sv > 0 ? Nv - 1 : 0))
+      ghost_store(Gp, Gn, Gdn, gb + plane + (long long)Nw * Nv + (long long)w * Nu + u, I, inc, emit);
+    if (perW && w == 0) ghost_store(Gp, Gn, Gdn, gb + (long long)v * Nu + u, I, inc, emit);
+  };
 
   for (int t = 0; t < Nw; ++t) {
     const int w = Nw - 1 - t;
@@ -222,49 +246,26 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
       const int u = live ? (int)(pc % Nu) : 0, v = live ? (int)(pc / Nu) : 0;
       const long long c = (long long)u * csu + (long long)v * csv + (long long)w * csw;
       const long long fc = (long long)f * cells;
-      const double *chf = G.chi + fc;
+      // sweep-precision copies along V ([w][v][u]): chi, and S (dS) -- new on
+      // the planes already updated, old elsewhere
+      const T *chv = A.chiP[G.V] + fc;
+      T *spv = G.SPV + fc;
       T I0 = T(0), psi0 = T(0), psim = T(0);
-      // ---- 1. reverse ray ri at cell (u, v, w)
-      if (ray_thread) {
-        double wj = 0.0;
-        if (live) {
-          const AngleParam<T> &p = P[ri];
-          const T wts[4] = {p.wa, p.wb, p.wc, p.wd};
-          T Im = T(0), Sm = T(0), chim = T(0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int uu = u - ((q & 1) ? p.su : 0), vv = v - ((q & 2) ? p.sv : 0), ww = w + 1;
-            const int mu_ = map_coord(uu, Nu, perU), mv_ = map_coord(vv, Nv, perV), mw_ = map_coord(ww, Nw, perW);
-            const long long mc = (long long)mu_ * csu + (long long)mv_ * csv + (long long)mw_ * csw;
-            const bool in = uu >= 0 && uu < Nu && vv >= 0 && vv < Nv && ww < Nw;
-            T Iv;
-            if (in) Iv = ldcg(Iprv + ((long long)f * nrev + ri) * plane + (long long)vv * Nu + uu);
-            else Iv = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gp, false, uu, vv, ww);
-            // S of the plane above is the new one; a ghost mapped elsewhere reads the old S
-            const T Sv = (T)(mw_ == w + 1 ? ldcg(G.S64 + fc + mc) : G.Sfs[fc + mc]);
-            Im += wts[q] * Iv;
-            Sm += wts[q] * Sv;
-            chim += wts[q] * (T)chf[mc];
-          }
-          const T S0 = (T)G.Sfs[fc + c];
-          const T dtau = (chim + (T)chf[c]) * p.hs;
-          T E, om;
-          seg_weights(dtau, E, psi0, om);
-          I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
-          psim = om - E;
-          wj = (double)(p.wq * I0);
-        }
-        jr[threadIdx.x] = wj;
-      }
-      __syncthreads();
-      // ---- 2. the cell's update with the freshest J
+      // ---- 0. the cell's inputs that do not depend on this plane's rays (the
+      // plane above's dS is final since the barrier), loaded before the rays'
+      // work so that their latency overlaps it
+      const long long i = fc + c;
+      double JF = 0.0, JRp = 0.0, corr = 0.0, S = 0.0, e = 0.0, Bc = 0.0, idn = 0.0;
       if (threadIdx.x < TC && live) {
-        const long long i = fc + c;
+        S = G.Sfs[i];
+        e = G.eps[i];
+        Bc = G.B[i];
+        idn = G.iden[i];
+        if (inc) JRp = G.JR64[i];
         // the forward partials and the correction's 9 weights and changes: all
         // loads issued before any is used (latency, not bandwidth, bounds this)
         const T *jp = A.Jpart + (long long)f * cells + c;
         const long long gstride = (long long)nf * cells;
-        double JF;
         if (sizeof(T) == 4) {   // float partials summed as an exact float pair (TwoSum)
           float hi = 0.f, lo = 0.f;
           for (int q0 = 0; q0 < G.nfg; q0 += 8) {
@@ -282,7 +283,6 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
           }
           JF = (double)hi + (double)lo;
         } else {
-          JF = 0.0;
           for (int q0 = 0; q0 < G.nfg; q0 += 8) {
             double xs[8];
 #pragma unroll
@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
             for (int q = 0; q < 8; ++q) JF += xs[q];
           }
         }
-        double corr = 0.0;
+        if (inc) JF += G.JF64[i];
+        if (G.JF64) G.JF64[i] = JF;
         if (w + 1 < Nw) {
           double cw[9], ds[9];
 #pragma unroll
@@ -304,15 +305,67 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
 #pragma unroll
           for (int q = 0; q < 9; ++q) corr += cw[q] * ds[q];
         }
-        double JR = 0.0;
-        for (int r = 0; r < nrev; ++r) JR += jr[r * TC + threadIdx.x];
+      }
+      // ---- 1. reverse ray ri at cell (u, v, w)
+      if (ray_thread) {
+        T wj = T(0), wp0 = T(0);
+        if (live) {
+          const AngleParam<T> &p = P[ri];
+          const T wts[4] = {p.wa, p.wb, p.wc, p.wd};
+          T Im = T(0), Sm = T(0), chim = T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int uu = u - ((q & 1) ? p.su : 0), vv = v - ((q & 2) ? p.sv : 0), ww = w + 1;
+            const int mu_ = map_coord(uu, Nu, perU), mv_ = map_coord(vv, Nv, perV), mw_ = map_coord(ww, Nw, perW);
+            const long long mp = ((long long)mw_ * Nv + mv_) * Nu + mu_;
+            const bool in = uu >= 0 && uu < Nu && vv >= 0 && vv < Nv && ww < Nw;
+            T Iv;
+            if (in) Iv = ldcg(Iprv + ((long long)f * nrev + ri) * plane + (long long)vv * Nu + uu);
+            else Iv = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, uu, vv, ww);
+            // S of the plane above is the new one.  A ghost mapped elsewhere
+            // reads the old S: on the top plane itself (being updated now) from
+            // the FP64 copy, whose change the last iteration's top-plane
+            // correction already covered; on plane 0 (periodic V, updated last)
+            // from the sweep copy, which still holds the last iteration's dS
+            T Sv;
+            if (mw_ != w) Sv = ldcg(spv + mp);
+            else Sv = inc ? T(0) : (T)G.Sfs[fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)mw_ * csw];
+            Im += wts[q] * Iv;
+            Sm += wts[q] * Sv;
+            chim += wts[q] * chv[mp];
+          }
+          const long long pown = ((long long)w * Nv + v) * Nu + u;
+          const T S0 = inc ? T(0) : spv[pown];
+          const T dtau = (chim + chv[pown]) * p.hs;
+          T E, om;
+          seg_weights(dtau, E, psi0, om);
+          I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
+          psim = om - E;
+          wj = p.wq * I0;
+          wp0 = p.wq * psi0;
+        }
+        jr[threadIdx.x] = wj;
+        jp0[threadIdx.x] = wp0;
+      }
+      __syncthreads();
+      // ---- 2. the cell's update with the freshest J
+      if (threadIdx.x < TC && live) {
+        T jrs = T(0), wps = T(0);   // the reverse rays' J terms, in ray order
+        for (int r = 0; r < nrev; ++r) {
+          jrs += jr[r * TC + threadIdx.x];
+          wps += jp0[r * TC + threadIdx.x];
+        }
+        const double JR = JRp + (double)jrs, WP = (double)wps;
         const double J = JF + corr + JR;
-        const double S = G.Sfs[i], e = G.eps[i];
-        const double dS = ((1.0 - e) * J + e * G.B[i] - S) * G.iden[i];
+        const double dS = ((1.0 - e) * J + e * Bc - S) * idn;
         const double Sn = S + dS;
         G.S64[i] = Sn;
         G.J64[i] = J;
         G.dS[i] = dS;
+        spv[((long long)w * Nv + v) * Nu + u] = (T)(inc ? dS : Sn);
+        // the reverse rays' J once their intensities take this dS (the top plane
+        // of a bounded V axis adds its ghost-layer term in the pass below)
+        if (G.JR64) G.JR64[i] = JR + WP * dS;
         dsm[threadIdx.x] = dS;
         const double ad = fabs(dS), as = fabs(Sn);
         const double r = (sizeof(T) == 4 && as > 1e-30 && as < 1e30 && ad < 1e30)
@@ -331,11 +384,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
         } else {
           const T I = I0 + psi0 * (T)dsm[cs];
           Icur[o] = I;
-          const AngleParam<T> &p = P[ri];
-          const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
-          if (perU && u == (p.su > 0 ? Nu - 1 : 0)) Gn[gb + plane + (long long)w * Nv + v] = I;
-          if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) Gn[gb + plane + (long long)Nw * Nv + (long long)w * Nu + u] = I;
-          if (perW && w == 0) Gn[gb + (long long)v * Nu + u] = I;
+          store_ghosts(P[ri], f, u, v, w, I);
         }
       }
       __syncthreads();
@@ -343,34 +392,39 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
     if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
     if (fix) {
       // top plane of a bounded V axis: the upwind S of the ghost layer was this
-      // plane's; add Psi- times its change, then store the outflow ghosts
-      const long long n = (long long)nf * nrev * plane;
+      // plane's; add Psi- times its change, then store the outflow ghosts.  One
+      // thread per cell, the rays in order (their J term in a fixed order).
+      const long long n = (long long)nf * plane;
       for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
            j += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(j / ((long long)nrev * plane));
-        const int r = (int)((j / plane) % nrev);
+        const int f = (int)(j / plane);
         const long long pc = j % plane;
         if (G.fmask && G.fmask[f]) continue;
         const int u = (int)(pc % Nu), v = (int)(pc / Nu);
         const long long fc = (long long)f * cells;
-        const AngleParam<T> &p = P[r];
-        const T wts[4] = {p.wa, p.wb, p.wc, p.wd};
-        double gsum = 0.0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int uu = u - ((q & 1) ? p.su : 0), vv = v - ((q & 2) ? p.sv : 0), ww = w + 1;
-          const int mw_ = map_coord(ww, Nw, perW);
-          if (wts[q] == T(0) || mw_ != w) continue;
-          const int mu_ = map_coord(uu, Nu, perU), mv_ = map_coord(vv, Nv, perV);
-          gsum += (double)wts[q] * ldcg(G.dS + fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)w * csw);
-        }
         const long long c = (long long)u * csu + (long long)v * csv + (long long)w * csw;
-        const T I = Icur[j] + Psz[j] * (T)ldcg(G.dS + fc + c) + Psm[j] * (T)gsum;
-        Icur[j] = I;
-        const long long gb = ((long long)f * A.na + p.angle) * A.d.gsize;
-        if (perU && u == (p.su > 0 ? Nu - 1 : 0)) Gn[gb + plane + (long long)w * Nv + v] = I;
-        if (perV && v == (p.sv > 0 ? Nv - 1 : 0)) Gn[gb + plane + (long long)Nw * Nv + (long long)w * Nu + u] = I;
-        if (perW && w == 0) Gn[gb + (long long)v * Nu + u] = I;
+        const T dSc = (T)ldcg(G.dS + fc + c);
+        double extra = 0.0;   // the ghost-layer term of the reverse rays' J
+        for (int r = 0; r < nrev; ++r) {
+          const AngleParam<T> &p = P[r];
+          const T wts[4] = {p.wa, p.wb, p.wc, p.wd};
+          double gsum = 0.0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int uu = u - ((q & 1) ? p.su : 0), vv = v - ((q & 2) ? p.sv : 0), ww = w + 1;
+            const int mw_ = map_coord(ww, Nw, perW);
+            if (wts[q] == T(0) || mw_ != w) continue;
+            const int mu_ = map_coord(uu, Nu, perU), mv_ = map_coord(vv, Nv, perV);
+            gsum += (double)wts[q] * ldcg(G.dS + fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)w * csw);
+          }
+          const long long o = ((long long)f * nrev + r) * plane + pc;
+          const T gterm = Psm[o] * (T)gsum;
+          const T I = Icur[o] + Psz[o] * dSc + gterm;
+          Icur[o] = I;
+          extra += (double)(p.wq * gterm);
+          store_ghosts(p, f, u, v, w, I);
+        }
+        if (G.JR64) G.JR64[fc + c] += extra;
       }
       if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
     }

@@ -68,9 +68,16 @@ struct GsArgs {
   const int *fgroups;        // the forward groups (their J partials are summed)
   int nfg;
   const double *chi, *eps, *B, *iden;
-  double *S64, *Sfs, *J64, *dS;
+  double *S64, *Sfs, *J64;
+  double *dS;                // [nf][cells] this iteration's change of S
   const double *gsw;         // [nf][9][cells] first-order correction weights
-  T *Ir;                     // [4][nf][nrev][plane]: intensities (2 planes), Psi0, Psi-
+  int incremental;           // after the first iteration, sweep increments (float32 grids):
+  double *JF64, *JR64;       //   J of the forward rays and (corrected) of the reverse rays,
+                             //   accumulated in FP64 from the swept increments
+  T *SPV;                    // sweep copy of S (or dS) along V, [nf][w][v][u]: read for the
+                             // plane above and rewritten plane by plane with the new values
+  T *Ir;                     // [4][nf][nrev][plane]: intensities or their increments
+                             // (2 planes), Psi0, Psi-
   const unsigned char *fmask;
   unsigned *bar;             // grid-barrier counter, zero at launch
 };

@@ -2,8 +2,9 @@
 
 * Iteration by iteration: S after 1, 2 and 4 iterations (tol 0, the solve stops
   on max_iter) equals the oracle's Gauss-Seidel S: FP64 to 1e-11 relative, the
-  mixed path (float32 sweeps of S itself) within float32 rounding amplified by
-  the update (2e-4 relative, floor 1e-6 of the bin's largest S).
+  mixed path (float32 sweeps, of changes after the first iteration) within
+  float32 rounding amplified by the update (2e-4 relative, floor 1e-6 of the
+  bin's largest S).
 * Converged: same iteration count (FP64; within one for mixed), S and J of the
   final formal solution within the FP64 tolerance, and fewer iterations than
   the library's own Jacobi solve.
@@ -77,7 +78,7 @@ def test_iterations_match_the_oracle(rt, case, prec):
 @pytest.mark.parametrize("case", ["atmosphere", "periodic_lq6", "two_d"])
 def test_converged_solve(rt, case, prec):
     p = CASES[case]()
-    tol = 1e-9 if prec == "fp64" else 1e-5
+    tol = 1e-9 if prec == "fp64" else 1e-6
     og = O.Grid.from_problem(p)
     ref = O.ali_solve(og, p.chi, p.eps, p.B, p.freq_w, tol=tol, max_iter=5000, moments=True,
                       method="gauss_seidel", nthreads=O.max_threads())
@@ -124,3 +125,15 @@ def test_switching_schemes_and_validation(rt):
     g.set_interpolation("quadratic")
     with pytest.raises(rt.RTError):
         g.set_iteration("gauss_seidel")
+
+
+def test_mixed_sweeps_changes_and_reaches_tight_tolerances(rt):
+    # float32 sweeps of S itself stall near 1e-7 / eps; sweeping changes does not
+    p = W.stratified_atmosphere(16, eps=1e-3, n_mu=4, nxy=8)
+    g = _gpu(rt, p, "mixed")
+    iters, resid, st = g.ali_solve(tol=1e-7, max_iter=20000)
+    assert st == rt.RT_OK and resid <= 1e-7
+    ref = _gpu(rt, p, "fp64")
+    it64, _, _ = ref.ali_solve(tol=1e-7, max_iter=20000)
+    assert abs(iters - it64) <= max(2, it64 // 100), (iters, it64)
+    assert _binwise_ok(g.get_S(), ref.get_S(), 1e-4, 1e-7)

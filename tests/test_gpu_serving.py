@@ -31,9 +31,8 @@ def _mix():
         prec = "mixed" if i % 3 else "fp64"
         interp = "quadratic" if i % 4 == 3 else "linear"
         scheme = "gauss_seidel" if i % 4 == 2 else "jacobi"
-        # the second-order and Gauss-Seidel mixed paths sweep S itself: float32
-        # rounding limits tol
-        tol = 1e-5 if (interp == "quadratic" or scheme == "gauss_seidel") else 1e-6
+        # the second-order mixed path sweeps S itself: float32 rounding limits tol
+        tol = 1e-5 if interp == "quadratic" else 1e-6
         reqs.append((W.build_request(d, tol=tol), prec, interp, scheme))
     return reqs
 
