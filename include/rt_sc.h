@@ -133,12 +133,18 @@ rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I);
 rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out,
                           int on_device, const rt_solve_opts *opts);
 
-/* Jacobi ALI to max|dS|/S <= opts->tol (Eqs. 24-25).  S_init [nf][nz][ny][nx]
- * (device or host per on_device) or NULL to start from S = B.  Periodic ghosts
- * start as the image cells' S.  When every eps == 1 the stopping test uses the
- * change of J between consecutive formal solutions.  iters_out: formal
- * solutions performed; resid_out: the last max relative change.  Returns
- * RT_ERR_NOT_CONVERGED (state kept) if max_iter is reached first. */
+/* Jacobi ALI to max|dS|/S <= opts->tol (Eqs. 24-25) (or Gauss-Seidel, see
+ * rt_set_iteration).  S_init [nf][nz][ny][nx] (device or host per on_device) or
+ * NULL to start from S = B.  Periodic ghosts start as the image cells' S.  When
+ * every eps == 1 the stopping test uses the change of J between consecutive
+ * formal solutions.  iters_out: formal solutions performed; resid_out: the last
+ * max relative change.  Iterations are enqueued in batches (opts->check_every,
+ * or 4 doubling to 64) with one host check per batch; after the first batch of
+ * a solve, a batch's launches are captured once as a CUDA graph and replayed
+ * (not while timing is enabled, whose events need direct launches; a stream
+ * that cannot be captured, such as the legacy default stream, keeps direct
+ * launches).  Returns RT_ERR_NOT_CONVERGED (state kept) if max_iter is reached
+ * first. */
 rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
                        int *iters_out, double *resid_out);
 
@@ -224,7 +230,8 @@ rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opt
  * duration of the formal-solution kernel launches that did work; sweep_launches:
  * how many; total_ms: the whole solve; kernel_launches: all kernels this grid has
  * launched since it was created (cumulative); updates: cell * ray * frequency
- * updates of the latest call. */
+ * updates of the latest call; graph_launches: ALI batches replayed as CUDA
+ * graphs since the grid was created. */
 typedef struct {
   int iters;
   double resid;
@@ -233,6 +240,7 @@ typedef struct {
   double total_ms;
   long long kernel_launches;
   long long updates;       /* cell * ray * frequency updates performed */
+  long long graph_launches; /* ALI batches replayed as CUDA graphs (cumulative) */
 } rt_stats;
 rt_status rt_enable_timing(rt_grid g, int enable);
 rt_status rt_get_stats(rt_grid g, rt_stats *out);

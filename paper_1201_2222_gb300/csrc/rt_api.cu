@@ -330,6 +330,19 @@ struct rt_grid_s {
   size_t gs_list_n = 0;
   double *gs_acc = nullptr;           // incremental solves: J of the forward and of the reverse
                                       // rays [2][nf][cells]
+
+  // CUDA graphs of ALI batches (the launches of m iterations, replayed as one
+  // graph); keyed by m, the scheme and the generation of the captured arguments
+  struct Graph {
+    long long gen;
+    int m, gs, inc;
+    long long nlaunch;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  long long gen = 0;                  // bumped whenever a captured pointer or plan may change
+  bool graphs_ok = true;              // false once a capture failed on this grid
+  long long graph_launches = 0;
 };
 
 namespace {
@@ -563,6 +576,7 @@ void plan_groups(rt_grid g) {
 
 template <typename T>
 rt_status upload_plan(rt_grid g) {
+  g->gen++;
   std::vector<AngleParam<T>> ap(g->group_angles.size());
   for (size_t gi = 0; gi < g->groups.size(); ++gi) {
     const GroupParam &gp = g->groups[gi];
@@ -803,6 +817,7 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   std::vector<int> list(fg);
   list.insert(list.end(), fr.begin(), fr.end());
   if (list.size() > g->gs_list_n) {
+    g->gen++;
     if (g->gs_list) cudaFree(g->gs_list);
     g->gs_list = nullptr;
     g->gs_list_n = 0;
@@ -811,6 +826,7 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   }
   CU(cudaMemcpyAsync(g->gs_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   const size_t N = (size_t)N_of(g);
+  if (!g->gsw || !g->gs_bar) g->gen++;
   if (!g->gsw) CU(cudaMalloc((void **)&g->gsw, 9 * N * sizeof(double)));
   if (!g->gs_bar) CU(cudaMalloc((void **)&g->gs_bar, sizeof(unsigned)));
   int cax[3];
@@ -818,6 +834,7 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   const size_t plane = (size_t)g->d.n[cax[0]] * g->d.n[cax[1]];
   const size_t irb = 4 * (size_t)g->d.nf * nrev * plane * sizeof(T);
   if (irb > g->gsIr_bytes) {
+    g->gen++;
     if (g->gsIr) cudaFree(g->gsIr);
     g->gsIr = nullptr;
     g->gsIr_bytes = 0;
@@ -845,7 +862,10 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   G.incremental = incremental ? 1 : 0;
   G.JF64 = G.JR64 = nullptr;
   if (incremental) {
-    if (!g->gs_acc) CU(cudaMalloc((void **)&g->gs_acc, 2 * N * sizeof(double)));
+    if (!g->gs_acc) {
+      g->gen++;
+      CU(cudaMalloc((void **)&g->gs_acc, 2 * N * sizeof(double)));
+    }
     G.JF64 = g->gs_acc;
     G.JR64 = g->gs_acc + N;
   }
@@ -906,8 +926,9 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   }
   int enqueued = 0, batch = opts && opts->check_every > 0 ? opts->check_every : 4;
   rtk::SolveState hs{};
-  while (true) {
-    const int m = std::min(batch, max_iter - enqueued);
+  // the launches of m iterations (every later kernel of a batch does nothing
+  // once the solve has converged)
+  auto enqueue_batch = [&](int m) -> rt_status {
     for (int i = 0; i < m; ++i) {
       rt_status r = enqueue_sweep<T>(g, A, false, s, g->timing ? &ev : nullptr);
       if (r != RT_OK) return r;
@@ -921,6 +942,53 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
       }
       CU(rtk::launch_finish(g->st, s));
       g->launches++;
+    }
+    return RT_OK;
+  };
+  // after the first batch (which also performs every kernel's one-time set-up),
+  // batches are captured once as CUDA graphs and replayed: one launch per batch
+  auto graph_for = [&](int m) -> const rt_grid_s::Graph * {
+    for (auto it = g->graphs.begin(); it != g->graphs.end();) {
+      if (it->gen != g->gen) {   // arguments of another plan or buffer set
+        cudaGraphExecDestroy(it->exec);
+        it = g->graphs.erase(it);
+        continue;
+      }
+      if (it->m == m && it->gs == (gs ? 1 : 0) && it->inc == incremental) return &*it;
+      ++it;
+    }
+    const long long l0 = g->launches;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g->graphs_ok = false;
+      return nullptr;
+    }
+    const rt_status r = enqueue_batch(m);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    const long long n = g->launches - l0;
+    g->launches = l0;
+    cudaGraphExec_t exec = nullptr;
+    if (r != RT_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();   // not capturable here: launch directly from now on
+      if (graph) cudaGraphDestroy(graph);
+      g->graphs_ok = false;
+      return nullptr;
+    }
+    cudaGraphDestroy(graph);
+    g->graphs.push_back(rt_grid_s::Graph{g->gen, m, gs ? 1 : 0, incremental, n, exec});
+    return &g->graphs.back();
+  };
+  while (true) {
+    const int m = std::min(batch, max_iter - enqueued);
+    const rt_grid_s::Graph *gr = (enqueued > 0 && !g->timing && g->graphs_ok) ? graph_for(m) : nullptr;
+    if (gr) {
+      CU(cudaGraphLaunch(gr->exec, s));
+      g->launches += gr->nlaunch;
+      g->graph_launches++;
+    } else {
+      rt_status r = enqueue_batch(m);
+      if (r != RT_OK) return r;
     }
     enqueued += m;
     CU(cudaMemcpyAsync(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost, s));
@@ -1215,6 +1283,7 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->gsw, g->gsIr, g->gs_bar, g->gs_list, g->gs_acc};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (auto &e : g->graphs) cudaGraphExecDestroy(e.exec);
   if (g->own) cudaStreamDestroy(g->own);
   delete g;
   return RT_OK;
@@ -1318,6 +1387,7 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
     if ((r = fill_bc_any(g, f, s)) != RT_OK) return r;
   if (g->desc.prec == RT_PREC_MIXED && (r = plan_precision(g)) != RT_OK) return r;
   g->gs_ready = false;
+  g->gen++;
   g->have_medium = true;
   return RT_OK;
 }
@@ -1717,6 +1787,7 @@ rt_status rt_get_stats(rt_grid g, rt_stats *out) {
   if (!g || !out) return fail(RT_ERR_ARG, "NULL argument");
   *out = g->stats;
   out->kernel_launches = g->launches;
+  out->graph_launches = g->graph_launches;
   return RT_OK;
 }
 

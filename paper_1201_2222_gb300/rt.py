@@ -45,7 +45,8 @@ class rt_solve_opts(ctypes.Structure):
 class rt_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("resid", ctypes.c_double), ("sweep_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_int), ("total_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong),
+                ("graph_launches", ctypes.c_longlong)]
 
 
 class rt_server_opts(ctypes.Structure):

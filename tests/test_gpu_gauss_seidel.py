@@ -137,3 +137,22 @@ def test_mixed_sweeps_changes_and_reaches_tight_tolerances(rt):
     it64, _, _ = ref.ali_solve(tol=1e-7, max_iter=20000)
     assert abs(iters - it64) <= max(2, it64 // 100), (iters, it64)
     assert _binwise_ok(g.get_S(), ref.get_S(), 1e-4, 1e-7)
+
+
+def test_batches_replay_as_graphs_with_the_same_result(rt):
+    # a solve of several batches replays graphs after its first batch; the
+    # result equals that of a solve whose batches all launch directly (timing on)
+    p = W.stratified_atmosphere(12, n_mu=4, nxy=8)
+    res = {}
+    for scheme in ("jacobi", "gauss_seidel"):
+        for timing in (False, True):
+            g = _gpu(rt, p, "mixed", scheme)
+            g.enable_timing(timing)
+            it, _, st = g.ali_solve(tol=1e-7, max_iter=5000, check_every=4)
+            assert st == rt.RT_OK and it > 8
+            res[scheme, timing] = (it, g.get_S(), g.stats()["graph_launches"])
+        it0, S0, n0 = res[scheme, False]
+        it1, S1, n1 = res[scheme, True]
+        assert n0 > 0 and n1 == 0
+        assert it0 == it1
+        np.testing.assert_array_equal(S0, S1)
