@@ -828,7 +828,7 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   const size_t N = (size_t)N_of(g);
   if (!g->gsw || !g->gs_bar) g->gen++;
   if (!g->gsw) CU(cudaMalloc((void **)&g->gsw, 9 * N * sizeof(double)));
-  if (!g->gs_bar) CU(cudaMalloc((void **)&g->gs_bar, sizeof(unsigned)));
+  if (!g->gs_bar) CU(cudaMalloc((void **)&g->gs_bar, rtk::kGsBarWords * sizeof(unsigned)));
   int cax[3];
   rtk::plane_axes(V, cax);
   const size_t plane = (size_t)g->d.n[cax[0]] * g->d.n[cax[1]];

@@ -47,15 +47,24 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
 }
 
 // Grid barrier of a cooperative launch: the n-th call returns once every block
-// has made it.  Returns false (and records the timeout) if a wait gave up or
-// another block already did; the caller then returns.
-__device__ bool grid_sync(unsigned *bar, unsigned target, SolveState *st) {
+// has made it.  Arrivals are counted in two levels (blocks in groups of
+// kGsBarGroup on their own counters, bar[1 + group]; the last block of a group
+// adds the group to bar[0]) so that no counter takes more than a few dozen
+// atomics per barrier.  Returns false (and records the timeout) if a wait gave
+// up or another block already did; the caller then returns.
+__device__ bool grid_sync(unsigned *bar, unsigned epoch, SolveState *st) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
+    const unsigned grp = blockIdx.x / kGsBarGroup, ngrp = (gridDim.x + kGsBarGroup - 1) / kGsBarGroup;
+    const unsigned gsize = min((unsigned)kGsBarGroup, gridDim.x - grp * kGsBarGroup);
     __threadfence();
-    atomicAdd(bar, 1u);
+    if (atomicAdd(&bar[1 + grp], 1u) + 1 == epoch * gsize) {   // the group is complete
+      __threadfence();
+      atomicAdd(&bar[0], 1u);
+    }
+    const unsigned target = epoch * ngrp;
     long long polls = 0;
     while (ld_relaxed(bar) < target) {   // the fence below orders what follows
       if (*(volatile int *)&st->err == kGsBarrierTimeout || ++polls > (1LL << 22)) {
@@ -204,7 +213,6 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
   const bool ray_thread = ri < nrev;
   const long long IrPlane = (long long)nf * nrev * plane;   // one of the four blocks of Ir
   unsigned nbar = 0;
-  const unsigned nblk = gridDim.x;
   double rmax = 0.0;
   const bool inc = G.incremental && st->iter > 0;    // sweep changes
   const bool emit = G.incremental && st->iter == 0;  // full sweep that records ghost increments
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells * nf;
        i += (long long)gridDim.x * blockDim.x)
     G.Sfs[i] = G.S64[i];
-  if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
+  if (!grid_sync(G.bar, ++nbar, st)) return;
 
   const int fs = st->fs_count;
   const int prev = fs & 1;
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
       }
       __syncthreads();
     }
-    if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
+    if (!grid_sync(G.bar, ++nbar, st)) return;
     if (fix) {
       // top plane of a bounded V axis: the upwind S of the ghost layer was this
       // plane's; add Psi- times its change, then store the outflow ghosts.  One
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
         }
         if (G.JR64) G.JR64[fc + c] += extra;
       }
-      if (!grid_sync(G.bar, nblk * ++nbar, st)) return;
+      if (!grid_sync(G.bar, ++nbar, st)) return;
     }
   }
   // residual: block maximum, then one atomic per block
@@ -458,8 +466,9 @@ cudaError_t launch_gs_reverse(const GsArgs<T> &G, cudaStream_t s) {
   const long long plane = (long long)G.A.d.n[cax[0]] * G.A.d.n[cax[1]];
   const int TC = kGsThreads / G.nrev;
   const long long tiles = (plane + TC - 1) / TC * G.A.d.nf;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)bps * sms));
-  if ((e = cudaMemsetAsync(G.bar, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  const long long cap = std::min<long long>((long long)bps * sms, (long long)(kGsBarWords - 1) * kGsBarGroup);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, cap));
+  if ((e = cudaMemsetAsync(G.bar, 0, kGsBarWords * sizeof(unsigned), s)) != cudaSuccess) return e;
   GsArgs<T> arg = G;
   void *params[] = {&arg};
   return cudaLaunchCooperativeKernel((const void *)gs_reverse_kernel<T>, dim3(grid), dim3(kGsThreads),

@@ -58,6 +58,8 @@ struct AliArgs {
 constexpr int kGsMaxRev = 64;          // reverse rays per frequency
 constexpr int kGsThreads = 256;
 constexpr int kGsBarrierTimeout = 60;
+constexpr int kGsBarGroup = 16;         // blocks per first-level barrier counter
+constexpr int kGsBarWords = 1 + 256;    // barrier counters (grids of up to 4096 blocks)
 
 template <typename T>
 struct GsArgs {
