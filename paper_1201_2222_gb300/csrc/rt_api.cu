@@ -342,6 +342,12 @@ struct rt_grid_s {
   std::vector<Graph> graphs;
   long long gen = 0;                  // bumped whenever a captured pointer or plan may change
   bool graphs_ok = true;              // false once a capture failed on this grid
+  // FP64 grids, one-cell-per-thread sweep: E and Psi0 per ray slot and cell,
+  // [2][slots][nf][cells], tabulated for the medium and plan of generation wt_gen
+  void *wt = nullptr;
+  size_t wt_bytes = 0;
+  long long wt_gen = -1;
+  bool wt_off = false;                // the table did not fit in device memory
   long long graph_launches = 0;
 };
 
@@ -728,7 +734,43 @@ rtk::SweepArgs<T> sweep_args(rt_grid g) {
   A.write_ghosts = 1;
   A.skip_if_done = 1;
   A.cluster = g->cluster;
+  const bool wt = g->wt && g->wt_gen == g->gen && g->variant == 1 && g->interp == RT_INTERP_LINEAR;
+  const size_t half = g->wt_bytes / 2;
+  A.WE = wt ? (const T *)g->wt : nullptr;
+  A.WP = wt ? (const T *)((const char *)g->wt + half) : nullptr;
   return A;
+}
+
+// The one-cell-per-thread sweep of FP64 grids reads its segment weights E, Psi0
+// (functions of chi alone) from a table filled once per medium and plan: the
+// FP64 exponential and divide are then paid once, not every formal solution.
+// Without the memory for it, the sweep computes them as before.
+template <typename T>
+rt_status ensure_seg_table(rt_grid g, cudaStream_t s) {
+  if (sizeof(T) != 8 || g->variant != 1 || g->interp != RT_INTERP_LINEAR || g->wt_off) return RT_OK;
+  if (g->wt && g->wt_gen == g->gen) return RT_OK;
+  const size_t need = 2 * g->group_angles.size() * (size_t)N_of(g) * sizeof(T);
+  if (need > g->wt_bytes) {
+    if (g->wt) cudaFree(g->wt);
+    g->wt = nullptr;
+    g->wt_bytes = 0;
+    if (cudaMalloc(&g->wt, need) != cudaSuccess) {
+      cudaGetLastError();
+      g->wt = nullptr;
+      g->wt_off = true;
+      return RT_OK;
+    }
+    g->wt_bytes = need;
+    g->gen++;   // a new buffer: captured graphs must not replay the old pointers
+  }
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  T *WE = (T *)g->wt, *WP = (T *)((char *)g->wt + g->wt_bytes / 2);
+  for (size_t gi = 0; gi < g->groups.size(); ++gi) {
+    CU(rtk::launch_seg_table<T>(A, (int)gi, g->groups[gi].na, WE, WP, s));
+    g->launches++;
+  }
+  g->wt_gen = g->gen;
+  return RT_OK;
 }
 
 struct EventPair {
@@ -890,12 +932,18 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   // sweeps increments; it also brings its own Lambda* every iteration)
   const bool gs = g->iteration == RT_ITER_GAUSS_SEIDEL && !g->lte;
   const int incremental = (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR) ? 1 : 0;
-  rtk::SweepArgs<T> A = sweep_args<T>(g);
-  A.incremental = incremental;
   rtk::GsArgs<T> GA{};
   if (gs) {
     rt_status r = gs_setup<T>(g, s, incremental != 0, GA);
     if (r != RT_OK) return r;
+  }
+  {
+    rt_status r = ensure_seg_table<T>(g, s);
+    if (r != RT_OK) return r;
+  }
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  A.incremental = incremental;
+  if (gs) {
     A.gs_forward = 1;
     A.gs_axis = GA.V;
     GA.A = A;
@@ -1021,6 +1069,8 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
 
 template <typename T>
 rt_status formal_once(rt_grid g, cudaStream_t s) {
+  rt_status r0 = ensure_seg_table<T>(g, s);
+  if (r0 != RT_OK) return r0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
   A.skip_if_done = 0;
   std::vector<EventPair> ev;
@@ -1055,6 +1105,8 @@ rt_status moments_sweep(rt_grid g, cudaStream_t s) {
     CU(cudaMalloc(&g->Mpart, need * 9 * (size_t)N_of(g) * sizeof(T)));
     g->mpart_groups = need;
   }
+  rt_status r0 = ensure_seg_table<T>(g, s);
+  if (r0 != RT_OK) return r0;
   rtk::SweepArgs<T> A = sweep_args<T>(g);
   A.parity_offset = -1;
   A.write_ghosts = 0;
@@ -1280,7 +1332,7 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
                   g->user_bc[0], g->user_bc[1], g->user_bc[2], g->user_bc[3], g->user_bc[4], g->user_bc[5],
                   g->Jpart, g->Opart, g->Mpart, g->angp, g->grp, g->rays_d, g->st, g->counts, g->tmp,
-                  g->gsw, g->gsIr, g->gs_bar, g->gs_list, g->gs_acc};
+                  g->gsw, g->gsIr, g->gs_bar, g->gs_list, g->gs_acc, g->wt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &e : g->graphs) cudaGraphExecDestroy(e.exec);
@@ -1307,6 +1359,7 @@ rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes) {
               + 6 * D.nfreq * na * gsize * ts  // ghosts (two parities, increments) and inflow faces
               + groups * N * ts * 11           // J, Lambda* and moment partials
               + 8 * (16 * N + cells);          // moments outputs
+  if (D.prec == RT_PREC_FP64) b += 2 * na * N * 8;   // tabulated segment weights (one-cell sweep)
   *bytes = b;
   return RT_OK;
 }
@@ -1924,6 +1977,7 @@ extern "C" rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const dou
   }
   // the size limit is checked before any pointer is touched
   rt_grid_s g;
+  g.wt_off = true;   // no segment-weight table: this entry point allocates nothing
   g.desc = D;
   g.two_d = D.nz == 1;
   if (g.two_d) {

@@ -129,8 +129,6 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
           const long long iB = pbase + (long long)v * Nu + um;
           const long long iC = pbase + (long long)vm * Nu + u;
           const long long iD = pbase + (long long)vm * Nu + um;
-          const T cA = chiP[RT_IDX(iA, cells, 3)], cB = chiP[RT_IDX(iB, cells, 3)];
-          const T cC = chiP[RT_IDX(iC, cells, 3)], cD = chiP[RT_IDX(iD, cells, 3)];
           const T sA = SP[RT_IDX(iA, cells, 4)], sB = SP[RT_IDX(iB, cells, 4)];
           const T sC = SP[RT_IDX(iC, cells, 4)], sD = SP[RT_IDX(iD, cells, 4)];
           T IA, IB, IC, ID;
@@ -162,12 +160,21 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
             IC = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, u, vb, wp);
             ID = ghost_I<T>(A, cax, Nu, Nv, Nw, f, p.angle, Gsrc, inc, ua, vb, wp);
           }
-          const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
           const T Sm = p.wa * sA + p.wb * sB + p.wc * sC + p.wd * sD;
           const T Im = p.wa * IA + p.wb * IB + p.wc * IC + p.wd * ID;
-          const T dtau = (chim + chi0) * p.hs;
-          T E, psi0, om;
-          seg_weights(dtau, E, psi0, om);
+          T E, psi0;
+          if (A.WE) {   // the medium's segment weights, tabulated once
+            const long long wi = ((long long)(gp.a0 + a) * A.d.nf + f) * cells + pidx;
+            E = A.WE[wi];
+            psi0 = A.WP[wi];
+          } else {
+            const T cA = chiP[RT_IDX(iA, cells, 3)], cB = chiP[RT_IDX(iB, cells, 3)];
+            const T cC = chiP[RT_IDX(iC, cells, 3)], cD = chiP[RT_IDX(iD, cells, 3)];
+            const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
+            const T dtau = (chim + chi0) * p.hs;
+            T om;
+            seg_weights(dtau, E, psi0, om);
+          }
           const T I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
           cur[RT_IDX((a * Rmax + lv) * Nu + u, smem_n, 7)] = I0;
           const T wI = p.wq * I0;
@@ -473,6 +480,59 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_tiled_kernel(
     if (C > 1) cluster.sync();
     else __syncthreads();
   }
+}
+
+// Segment weights of the one-cell-per-thread sweep, tabulated per medium: for
+// each ray of group gi (slots gp.a0 ...) and cell (in the group's [w][v][u]
+// layout) the E and Psi0 that sc_sweep_kernel would compute there -- the same
+// upwind vertices (periodic image or the cell's own row/column/plane at a
+// bounded face) and the same expressions.
+template <typename T>
+__global__ void __launch_bounds__(256) seg_table_kernel(const SweepArgs<T> A, int gi, T *WE, T *WP) {
+  const GroupParam gp = A.grp[gi];
+  int cax[3];
+  plane_axes(gp.axis, cax);
+  const int Nu = pick3(A.d.n, cax[0]), Nv = pick3(A.d.n, cax[1]), Nw = pick3(A.d.n, cax[2]);
+  const int perU = pick3(A.d.periodic, cax[0]), perV = pick3(A.d.periodic, cax[1]),
+            perW = pick3(A.d.periodic, cax[2]);
+  const long long cells = A.d.cells, plane = (long long)Nu * Nv;
+  const long long n = (long long)gp.na * A.d.nf * cells;
+  const int sa = gp.sa;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(k / ((long long)A.d.nf * cells));
+    const int f = (int)((k / cells) % A.d.nf);
+    const long long pidx = k % cells;
+    const int u = (int)(pidx % Nu), v = (int)((pidx / Nu) % Nv), w = (int)(pidx / plane);
+    const AngleParam<T> p = A.ang[gp.a0 + a];
+    const T *chiP = A.chiP[gp.axis] + (long long)f * cells;
+    const int wp = w - sa;
+    const bool wp_in = (unsigned)wp < (unsigned)Nw;
+    const int wpm = wp_in ? wp : (perW ? (wp < 0 ? wp + Nw : wp - Nw) : w);
+    const long long pbase = (long long)wpm * plane;
+    const int ua = u - p.su, vb = v - p.sv;
+    const bool ua_in = (unsigned)ua < (unsigned)Nu;
+    const bool vb_in = (unsigned)vb < (unsigned)Nv;
+    const int um = ua_in ? ua : (perU ? (ua < 0 ? ua + Nu : ua - Nu) : u);
+    const int vm = vb_in ? vb : (perV ? (vb < 0 ? vb + Nv : vb - Nv) : v);
+    const T cA = chiP[pbase + (long long)v * Nu + u], cB = chiP[pbase + (long long)v * Nu + um];
+    const T cC = chiP[pbase + (long long)vm * Nu + u], cD = chiP[pbase + (long long)vm * Nu + um];
+    const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
+    const T dtau = (chim + chiP[pidx]) * p.hs;
+    T E, psi0, om;
+    seg_weights(dtau, E, psi0, om);
+    const long long wi = ((long long)(gp.a0 + a) * A.d.nf + f) * cells + pidx;
+    WE[wi] = E;
+    WP[wi] = psi0;
+  }
+}
+
+template <typename T>
+cudaError_t launch_seg_table(const SweepArgs<T> &A, int gi, int nslots, T *WE, T *WP, cudaStream_t s) {
+  const long long n = (long long)nslots * A.d.nf * A.d.cells;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 32);
+  seg_table_kernel<T><<<grid, 256, 0, s>>>(A, gi, WE, WP);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ pipelined sweep
@@ -1745,6 +1805,7 @@ cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, c
 
 #define RT_INSTANTIATE(T)                                                                          \
   template cudaError_t launch_sweep<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template cudaError_t launch_seg_table<T>(const SweepArgs<T> &, int, int, T *, T *, cudaStream_t);   \
   template cudaError_t launch_sweep_tiled<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
   template cudaError_t launch_sweep_pipe<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
   template int sweep_max_active_clusters<T>(int, int, int, int, size_t);                          \

@@ -29,6 +29,8 @@ struct SweepArgs {
   int cluster;               // CTAs per cluster = strips per plane
   int incremental;           // ALI solve sweeping increments after its first formal solution
   int ray_slots;             // shared-memory planes per ray slot (>= rays of any group)
+  const T *WE, *WP;          // one-cell-per-thread sweep: E and Psi0 per ray slot and cell,
+                             // [slot][nf][w][v][u] of the slot's group (NULL: computed)
   int gs_forward;            // 1: Gauss-Seidel forward phase -- groups crossing the
   int gs_axis;               //    gs_axis face with mu < 0 (the reverse rays) do nothing
 };
@@ -102,6 +104,10 @@ cudaError_t prepare_kernel(const void *fn);
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                          cudaStream_t s);
+// E and Psi0 of every ray of group gi at every cell, as the one-cell-per-thread
+// sweep computes them (they depend on chi only), into A.WE / A.WP
+template <typename T>
+cudaError_t launch_seg_table(const SweepArgs<T> &A, int gi, int nslots, T *WE, T *WP, cudaStream_t s);
 // cells per thread of the tiled sweeps
 constexpr int kSweepSeg = 4;
 // threads per CTA of the tiled and pipelined sweeps: FP64 keeps 256 so that its
