@@ -321,12 +321,18 @@ def test_degenerate_shapes(rt, shape):
 
 # ------------------------------------------------------------ full-size sample
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_turbulent_box_128_formal_solution(rt, prec):
-    """The 128^3, 80-ray box in the launch configuration the benchmark uses: one
-    formal solution against the oracle at full size (oracle on all host cores)."""
+@pytest.mark.parametrize("prec,plan", [("mixed", None), ("fp64", None),
+                                       ("mixed", dict(angles_per_group=7, cluster_ctas=10, threads=512, variant=3))])
+def test_turbulent_box_128_formal_solution(rt, prec, plan):
+    """The 128^3, 80-ray box in the launch configurations the benchmark uses (the
+    planner's, and the plan its autotuner picks and its profiles were taken with:
+    pipelined, 7 rays per group, clusters of 10, 512 threads): one formal solution
+    against the oracle at full size (oracle on all host cores)."""
     p = W.turbulent_box(128, n_mu=8)
-    g = make(rt, p, prec)
+    g = make(rt, p, prec, **(plan or {}))
+    if plan:
+        got = g.sweep_plan()
+        assert (got["variant"], got["rays_per_group"], got["cluster"], got["threads"]) == (3, 7, 10, 512)
     J = g.formal_solve(p.B)
     og = O.Grid.from_problem(p)
     ref = O.formal_solution(og, p.chi[0], p.B[0], p.B[0], nthreads=O.max_threads())
