@@ -181,3 +181,17 @@ def test_rejects_second_order_and_unknown_methods():
         O.ali_solve(g, p.chi, p.eps, p.B, method="gauss_seidel", interp="quadratic")
     with pytest.raises(ValueError):
         O.ali_solve(g, p.chi, p.eps, p.B, method="sor")
+
+
+def test_paper_comparison_setting():
+    # the paper's comparison of the two schemes (Sec. 5.1): a scattering
+    # atmosphere with eps = 1e-6, nine zones per decade of optical depth, started
+    # from LTE; with two-stream rays (every downward ray swept in reverse) the
+    # Gauss-Seidel scheme needs nearly half the iterations
+    p = W.stratified_atmosphere(63, eps=1e-6, n_mu=2, nxy=2)
+    g = O.Grid.from_problem(p)
+    rj = O.ali_solve(g, p.chi, p.eps, p.B, p.freq_w, tol=1e-6, max_iter=20000, moments=False)
+    rg = O.ali_solve(g, p.chi, p.eps, p.B, p.freq_w, tol=1e-6, max_iter=20000, moments=False,
+                     method="gauss_seidel")
+    assert rj["converged"] and rg["converged"]
+    assert 1.6 <= rj["iters"] / rg["iters"] <= 2.2, (rj["iters"], rg["iters"])
