@@ -187,7 +187,7 @@ def test_paper_comparison_setting():
     # the paper's comparison of the two schemes (Sec. 5.1): a scattering
     # atmosphere with eps = 1e-6, nine zones per decade of optical depth, started
     # from LTE; with two-stream rays (every downward ray swept in reverse) the
-    # Gauss-Seidel scheme needs nearly half the iterations
+    # Gauss-Seidel scheme needs close to half the iterations
     p = W.stratified_atmosphere(63, eps=1e-6, n_mu=2, nxy=2)
     g = O.Grid.from_problem(p)
     rj = O.ali_solve(g, p.chi, p.eps, p.B, p.freq_w, tol=1e-6, max_iter=20000, moments=False)
