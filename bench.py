@@ -39,7 +39,11 @@ UNIT = "updates/s"
 N_BOX = 128
 N_MU = 8
 TOL = 1e-6
-FLOPS_PER_UPDATE = 36        # algorithmic FP32 operations of one cell*ray update
+# algorithmic FP32 operations of one cell*ray update: three bilinear interpolants
+# (chi-, S-, I-: 4 multiplies + 3 adds each), dtau (add, multiply), Psi0 (divide,
+# subtract), the update (3 multiplies + 2 adds), the J accumulation (multiply, add);
+# the exponential is counted apart
+FLOPS_PER_UPDATE = 36
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
