@@ -39,11 +39,12 @@ UNIT = "updates/s"
 N_BOX = 128
 N_MU = 8
 TOL = 1e-6
-# algorithmic FP32 operations of one cell*ray update: three bilinear interpolants
-# (chi-, S-, I-: 4 multiplies + 3 adds each), dtau (add, multiply), Psi0 (divide,
-# subtract), the update (3 multiplies + 2 adds), the J accumulation (multiply, add);
-# the exponential is counted apart
-FLOPS_PER_UPDATE = 36
+# algorithmic FP32 operations of one cell*ray update (Eq. 20 with linear
+# interpolation): three bilinear interpolants (chi-, S-, I-: 4 multiplies + 3 adds
+# each, 21), dtau = (chi- + chi0) s/2 (add, multiply), e0 = 1 - E, e1 = dtau - e0,
+# Psi0 = e1 / dtau, Psi- = e0 - Psi0 (4), I0 = I- E + Psi- S- + Psi0 S0 (3 multiplies
+# + 2 adds), the J accumulation (multiply, add); the exponential is counted apart
+FLOPS_PER_UPDATE = 34
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
