@@ -340,13 +340,20 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
             else Sv = inc ? T(0) : (T)G.Sfs[fc + (long long)mu_ * csu + (long long)mv_ * csv + (long long)mw_ * csw];
             Im += wts[q] * Iv;
             Sm += wts[q] * Sv;
-            chim += wts[q] * chv[mp];
+            if (!A.WE) chim += wts[q] * chv[mp];
           }
           const long long pown = ((long long)w * Nv + v) * Nu + u;
           const T S0 = inc ? T(0) : spv[pown];
-          const T dtau = (chim + chv[pown]) * p.hs;
           T E, om;
-          seg_weights(dtau, E, psi0, om);
+          if (A.WE) {   // the medium's segment weights (FP64 grids), tabulated once
+            const long long wi = ((long long)(G.rev0 + ri) * nf + f) * cells + pown;
+            E = A.WE[wi];
+            psi0 = A.WP[wi];
+            om = T(1) - psi0;
+          } else {
+            const T dtau = (chim + chv[pown]) * p.hs;
+            seg_weights(dtau, E, psi0, om);
+          }
           I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
           psim = om - E;
           wj = p.wq * I0;
