@@ -20,6 +20,10 @@ Follows Davis, Stone & Jiang (2012):
     its plane-wavefront form (``gs_reverse_rays``, ``gs_reverse`` and
     ``orc_gs_reverse`` in sc_oracle.c): forward rays from the old S, then the
     reverse sweep updating S plane by plane with the freshest J.
+  * ``slab_ali_solve``   - the same Jacobi ALI on z slabs (the paper's domain
+    decomposition, Sec. 3.5): each slab sweeps alone with a one-cell ghost layer
+    on its subdomain faces holding the neighbour's chi and S and, lagged by one
+    iteration, its intensities (``formal_solution(..., ext=...)``).
   * ``heating_rate``     - Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu) (Sec. 4, Q^int).
   * ``heating_rate_dif`` - Q^dif = -4 pi sum_nu w_nu div H_nu (Sec. 4), div H by
     centred differences of the cell-centred H (one-sided at non-periodic faces).
@@ -38,7 +42,7 @@ import numpy as np
 from . import build as _build
 from .quadrature import level_symmetric
 
-PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
+PERIODIC, VACUUM, THERMAL, FIXED, EXTERNAL = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -63,6 +67,8 @@ def _load():
         lib.orc_gs_is_reverse.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double]
         lib.orc_gs_is_reverse.restype = ctypes.c_int
+        lib.orc_formal_solution_ext.argtypes = lib.orc_formal_solution.argtypes + [d, d, d, d, d, d, d, d]
+        lib.orc_formal_solution_ext.restype = ctypes.c_int
         lib.orc_bezier_weights.argtypes = [ctypes.c_double, d]
         lib.orc_bezier_weights.restype = None
         lib.orc_max_threads.restype = ctypes.c_int
@@ -155,7 +161,7 @@ def _ray_subset_fixed(grid: Grid, I_fixed, rays):
 
 
 def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=False,
-                    nthreads=1, interp="linear", rays=None):
+                    nthreads=1, interp="linear", rays=None, ext=None):
     """One formal solution for one frequency.
 
     ``interp``: "linear" (bilinear face interpolation, linear S along the segment)
@@ -167,6 +173,10 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     ([6][na][face cells], faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi).
     ``rays``: indices of the rays to solve (default all); J, lstar, H, K then
     sum over those rays only and G_next holds their rows only.
+    ``ext`` (linear only): the ghost layers of EXTERNAL z faces, a dict with
+    "lo" and/or "hi" entries (chi [ny][nx], S [ny][nx], I [na][ny][nx]); the
+    result then also holds I_zlo and I_zhi, every ray's intensity on the first
+    and last z plane [na][ny][nx].
     Returns a dict with J, lstar, G_next (and H [3], K [6] when ``moments``)."""
     lib = _load()
     C = grid.cells
@@ -199,14 +209,32 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     mu = np.ascontiguousarray(mu).reshape(-1)
     wq = np.ascontiguousarray(wq)
     fn = {"linear": lib.orc_formal_solution, "quadratic": lib.orc_formal_solution_quad}[interp]
-    rc = fn(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
+    args = (grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1],
             grid.d[2], bl, bh, na, _ptr(mu), _ptr(wq),
             _ptr(chi), _ptr(S), _ptr(B), _ptr(I_fixed), _ptr(G_prev),
             _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
             int(nthreads))
+    Izlo = Izhi = None
+    if ext is not None:
+        if interp != "linear":
+            raise ValueError("external faces are supported with linear interpolation")
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        side = {}
+        for key in ("lo", "hi"):
+            side[key] = tuple(f64(a) for a in ext[key]) if key in ext else (None, None, None)
+        nface = grid.n[0] * grid.n[1]
+        Izlo = np.empty(na * nface)
+        Izhi = np.empty(na * nface)
+        rc = lib.orc_formal_solution_ext(*args, *[_ptr(a) for a in side["lo"]],
+                                         *[_ptr(a) for a in side["hi"]], _ptr(Izlo), _ptr(Izhi))
+    else:
+        rc = fn(*args)
     if rc != 0:
         raise RuntimeError(f"oracle formal solution failed ({rc})")
     out = dict(J=J.reshape(grid.shape), lstar=L.reshape(grid.shape), G_next=G_next)
+    if ext is not None:
+        out["I_zlo"] = Izlo.reshape(na, grid.n[1], grid.n[0])
+        out["I_zhi"] = Izhi.reshape(na, grid.n[1], grid.n[0])
     if moments:
         H = H.reshape((3,) + grid.shape)
         K = K.reshape((6,) + grid.shape)
@@ -444,6 +472,85 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
         with np.errstate(divide="ignore", invalid="ignore"):
             out["f"] = K / J[:, None]
     return out
+
+
+def slab_ali_solve(grid: Grid, chi, eps, B, nslab, freq_w=None, tol=1e-6, max_iter=1000, nthreads=1):
+    """Jacobi ALI (Eqs. 24-25) with the z axis split into ``nslab`` slabs (the
+    paper's domain decomposition, Sec. 3.5).
+
+    Every slab is solved as a grid of its own.  A face between two slabs (and,
+    on a periodic z axis, the wrap) is an EXTERNAL face: its one-cell ghost
+    layer holds the neighbour's chi and current S on the adjacent plane and,
+    for the rays entering through it, the neighbour's intensities there from
+    the previous iteration (before the first, its S, as for periodic ghosts);
+    the other faces keep the grid's boundaries.  Lambda* comes from each slab's
+    first formal solution, the stopping rule is the global max |dS|/S.
+    Returns dict(S, J, iters, resid, converged, history) with J that of the
+    last formal solution.  3D grids (nz >= nslab)."""
+    chi = np.asarray(chi, dtype=np.float64).reshape((-1,) + grid.shape)
+    eps = np.asarray(eps, dtype=np.float64).reshape(chi.shape)
+    B = np.asarray(B, dtype=np.float64).reshape(chi.shape)
+    nf = chi.shape[0]
+    nx, ny, nz = grid.n
+    if grid.two_d or not (1 <= nslab <= nz):
+        raise ValueError("slabs split the z axis of a 3D grid into 1..nz parts")
+    per_z = grid.bc_lo[2] == PERIODIC
+    z0 = [(d * nz) // nslab for d in range(nslab + 1)]
+    n_mu = {8: 2, 24: 4, 48: 6, 80: 8, 120: 10, 168: 12}[grid.na]
+    slabs = []
+    for d in range(nslab):
+        lo = EXTERNAL if (d > 0 or per_z) else grid.bc_lo[2]
+        hi = EXTERNAL if (d < nslab - 1 or per_z) else grid.bc_hi[2]
+        slabs.append(Grid(nx, ny, z0[d + 1] - z0[d], n_mu, bc_lo=(grid.bc_lo[0], grid.bc_lo[1], lo),
+                          bc_hi=(grid.bc_hi[0], grid.bc_hi[1], hi), dx=grid.d[0], dy=grid.d[1], dz=grid.d[2]))
+    S = B.copy()
+    lte = bool(np.all(eps == 1.0))
+    # incoming intensities of each slab's z faces: [f][d] -> [na][ny][nx]
+    below = lambda d: (z0[d] - 1) % nz      # global plane under slab d
+    above = lambda d: z0[d + 1] % nz        # global plane over slab d
+    I_lo = [[np.repeat(S[f, below(d)][None], grid.na, axis=0) for d in range(nslab)] for f in range(nf)]
+    I_hi = [[np.repeat(S[f, above(d)][None], grid.na, axis=0) for d in range(nslab)] for f in range(nf)]
+    G = [[init_ghosts(slabs[d], S[f, z0[d]:z0[d + 1]]) for d in range(nslab)] for f in range(nf)]
+    lstar = np.empty_like(chi)
+    J = np.empty_like(chi)
+    J_prev = None
+    history = []
+    r = math.inf
+    it = 0
+    for it in range(1, max_iter + 1):
+        out_lo, out_hi = [[None] * nslab for _ in range(nf)], [[None] * nslab for _ in range(nf)]
+        for f in range(nf):
+            for d in range(nslab):
+                g = slabs[d]
+                sl = slice(z0[d], z0[d + 1])
+                ext = {}
+                if g.bc_lo[2] == EXTERNAL:
+                    ext["lo"] = (chi[f, below(d)], S[f, below(d)], I_lo[f][d])
+                if g.bc_hi[2] == EXTERNAL:
+                    ext["hi"] = (chi[f, above(d)], S[f, above(d)], I_hi[f][d])
+                res = formal_solution(g, chi[f, sl], S[f, sl], B[f, sl], G[f][d], nthreads=nthreads, ext=ext)
+                J[f, sl] = res["J"]
+                if it == 1:
+                    lstar[f, sl] = res["lstar"]
+                G[f][d] = res["G_next"]
+                out_lo[f][d], out_hi[f][d] = res["I_zlo"], res["I_zhi"]
+        # the neighbours' intensities for the next iteration: slab d's top plane
+        # feeds the slab above's lower ghost layer, its bottom plane the slab below's
+        for f in range(nf):
+            for d in range(nslab):
+                I_lo[f][d] = out_hi[f][(d - 1) % nslab]
+                I_hi[f][d] = out_lo[f][(d + 1) % nslab]
+        if lte:
+            r = math.inf if J_prev is None else max_relative_change(J - J_prev, J)
+        else:
+            dS = ((1.0 - eps) * J + eps * B - S) / (1.0 - (1.0 - eps) * lstar)
+            S = S + dS
+            r = max_relative_change(dS, S)
+        J_prev = J.copy()
+        history.append(r)
+        if r <= tol:
+            break
+    return dict(S=S, J=J.copy(), iters=it, resid=r, converged=r <= tol, history=history)
 
 
 def solve_problem(p, **kw):

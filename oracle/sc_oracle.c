@@ -45,7 +45,7 @@
 #include <omp.h>
 #endif
 
-enum { BC_PERIODIC = 0, BC_VACUUM = 1, BC_THERMAL = 2, BC_FIXED = 3 };
+enum { BC_PERIODIC = 0, BC_VACUUM = 1, BC_THERMAL = 2, BC_FIXED = 3, BC_EXTERNAL = 4 };
 
 typedef struct {
   int n[3];
@@ -56,6 +56,10 @@ typedef struct {
   long face[3];     /* cells on a face normal to axis a */
   long goff[3];     /* offset of each face inside one angle's ghost block */
   long gsize;       /* ghost block per angle */
+  /* z faces of kind BC_EXTERNAL (a subdomain face, Sec. 3.5): the ghost layer's
+     chi and S [ny][nx] and each ray's intensity there [na][ny][nx], supplied by
+     the caller (lo = 0, hi = 1); NULL elsewhere */
+  const double *xchi[2], *xS[2], *xI[2];
 } geom;
 
 static long cell_index(const geom *g, int i, int j, int k) {
@@ -100,6 +104,8 @@ static double ghost_I(const geom *g, const int c[3], int angle, int na,
     int bc = fixed_side ? g->bc_hi[fixed_axis] : g->bc_lo[fixed_axis];
     if (bc == BC_VACUUM) return 0.0;
     if (bc == BC_THERMAL) return B[cell_index(g, m[0], m[1], m[2])];
+    if (bc == BC_EXTERNAL)   /* z faces only */
+      return g->xI[fixed_side][(long)angle * g->face[2] + face_index(g, 2, m[0], m[1], m[2])];
     /* BC_FIXED */
     long off = 0;
     for (int f = 0; f < 2 * fixed_axis + fixed_side; ++f) off += (long)na * g->face[f / 2];
@@ -126,19 +132,48 @@ static int map_field(const geom *g, const int c[3]) {
   return (int)cell_index(g, m[0], m[1], m[2]);
 }
 
+/* chi (which = 0) or S (1) at vertex c[]: beyond an external z face, the
+   supplied ghost layer at the mapped (x, y); elsewhere the field at map_field */
+static double field_value(const geom *g, const int c[3], const double *f, int which) {
+  for (int side = 0; side < 2; ++side) {
+    const double *const *x = which ? g->xS : g->xchi;
+    if (!x[side] || (side ? c[2] < g->n[2] : c[2] >= 0)) continue;
+    int m[3] = {c[0], c[1], 0};
+    for (int a = 0; a < 2; ++a) {
+      if (c[a] < 0) m[a] = (g->bc_lo[a] == BC_PERIODIC) ? c[a] + g->n[a] : 0;
+      else if (c[a] >= g->n[a]) m[a] = (g->bc_hi[a] == BC_PERIODIC) ? c[a] - g->n[a] : g->n[a] - 1;
+    }
+    return x[side][face_index(g, 2, m[0], m[1], 0)];
+  }
+  return f[map_field(g, c)];
+}
+
 /*
  * One formal solution for one frequency.  Returns 0 on success, -1 on bad input.
  * J, lstar, H, K are overwritten (lstar, H, K may be NULL).  G_next may be NULL.
  * nthreads > 1 splits the angles over OpenMP threads, each with its own
  * accumulators, summed afterwards in thread order.
  */
-int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
-                        const int *bc_lo, const int *bc_hi,
-                        int na, const double *mu, const double *wq,
-                        const double *chi, const double *S, const double *B,
-                        const double *I_fixed, const double *G_prev, double *G_next,
-                        double *J, double *lstar, double *H, double *K, int nthreads) {
+int orc_formal_solution_ext(int nx, int ny, int nz, double dx, double dy, double dz,
+                            const int *bc_lo, const int *bc_hi,
+                            int na, const double *mu, const double *wq,
+                            const double *chi, const double *S, const double *B,
+                            const double *I_fixed, const double *G_prev, double *G_next,
+                            double *J, double *lstar, double *H, double *K, int nthreads,
+                            const double *xchi_lo, const double *xS_lo, const double *xI_lo,
+                            const double *xchi_hi, const double *xS_hi, const double *xI_hi,
+                            double *I_zlo, double *I_zhi) {
   geom g;
+  memset(&g, 0, sizeof g);
+  g.xchi[0] = xchi_lo; g.xS[0] = xS_lo; g.xI[0] = xI_lo;
+  g.xchi[1] = xchi_hi; g.xS[1] = xS_hi; g.xI[1] = xI_hi;
+  for (int side = 0; side < 2; ++side) {
+    const int bc = side ? bc_hi[2] : bc_lo[2];
+    if ((bc == BC_EXTERNAL) != (g.xchi[side] && g.xS[side] && g.xI[side])) return -1;
+  }
+  if (bc_lo[0] == BC_EXTERNAL || bc_hi[0] == BC_EXTERNAL || bc_lo[1] == BC_EXTERNAL ||
+      bc_hi[1] == BC_EXTERNAL)
+    return -1;   /* subdomain faces are z faces */
   g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
   g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
   g.two_d = (nz == 1);
@@ -214,9 +249,8 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
               c[b2] = c0[b2] - d2 * sgn[b2];
               const int inside = c[0] >= 0 && c[0] < nx && c[1] >= 0 && c[1] < ny &&
                                  c[2] >= 0 && c[2] < nz;
-              const int fi = map_field(&g, c);
-              chim += wv * chi[fi];
-              Sm += wv * S[fi];
+              chim += wv * field_value(&g, c, chi, 0);
+              Sm += wv * field_value(&g, c, S, 1);
               Im += wv * (inside ? I[cell_index(&g, c[0], c[1], c[2])]
                                  : ghost_I(&g, c, k, na, B, I_fixed, G_prev));
             }
@@ -233,6 +267,8 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
           const double psim = e0 - psi0;
           const double I0 = Im * E + psim * Sm + psi0 * S[ci];
           I[ci] = I0;
+          if (I_zlo && iz == 0) I_zlo[(long)k * g.face[2] + face_index(&g, 2, ix, iy, 0)] = I0;
+          if (I_zhi && iz == nz - 1) I_zhi[(long)k * g.face[2] + face_index(&g, 2, ix, iy, 0)] = I0;
           accJ[ci] += w * I0;
           accL[ci] += w * psi0;
           if (want_mom) {
@@ -278,6 +314,17 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
   free(acc);
   free(Iw);
   return 0;
+}
+
+int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
+                        const int *bc_lo, const int *bc_hi,
+                        int na, const double *mu, const double *wq,
+                        const double *chi, const double *S, const double *B,
+                        const double *I_fixed, const double *G_prev, double *G_next,
+                        double *J, double *lstar, double *H, double *K, int nthreads) {
+  return orc_formal_solution_ext(nx, ny, nz, dx, dy, dz, bc_lo, bc_hi, na, mu, wq, chi, S, B,
+                                 I_fixed, G_prev, G_next, J, lstar, H, K, nthreads,
+                                 NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------
@@ -365,6 +412,7 @@ int orc_formal_solution_quad(int nx, int ny, int nz, double dx, double dy, doubl
                              const double *I_fixed, const double *G_prev, double *G_next,
                              double *J, double *lstar, double *H, double *K, int nthreads) {
   geom g;
+  memset(&g, 0, sizeof g);
   g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
   g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
   g.two_d = (nz == 1);
@@ -617,6 +665,7 @@ static int plane_of(const geom *g, long fi, int V) {
 /* 1 if ray k is a reverse ray of the Gauss-Seidel iteration */
 int orc_gs_is_reverse(int nz, const double *mu, int k, double dx, double dy, double dz) {
   geom g;
+  memset(&g, 0, sizeof g);
   g.two_d = (nz == 1);
   g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
   const int V = g.two_d ? 1 : 2;
@@ -634,6 +683,7 @@ int orc_gs_reverse(int nx, int ny, int nz, double dx, double dy, double dz,
                    const double *G_prev, double *G_next,
                    double *J_out, double *dS_out, double *C_out) {
   geom g;
+  memset(&g, 0, sizeof g);
   g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
   g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
   g.two_d = (nz == 1);
