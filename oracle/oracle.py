@@ -67,7 +67,7 @@ def _load():
         lib.orc_gs_is_reverse.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double]
         lib.orc_gs_is_reverse.restype = ctypes.c_int
-        lib.orc_formal_solution_ext.argtypes = lib.orc_formal_solution.argtypes + [d, d, d, d, d, d, d, d]
+        lib.orc_formal_solution_ext.argtypes = lib.orc_formal_solution.argtypes + [d] * 10
         lib.orc_formal_solution_ext.restype = ctypes.c_int
         lib.orc_bezier_weights.argtypes = [ctypes.c_double, d]
         lib.orc_bezier_weights.restype = None
@@ -174,7 +174,10 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     ``rays``: indices of the rays to solve (default all); J, lstar, H, K then
     sum over those rays only and G_next holds their rows only.
     ``ext`` (linear only): the ghost layers of EXTERNAL z faces, a dict with
-    "lo" and/or "hi" entries (chi [ny][nx], S [ny][nx], I [na][ny][nx]); the
+    "lo" and/or "hi" entries (chi [ny][nx], S [ny][nx], I [na][ny][nx],
+    B [ny][nx]); past such a face an out-of-range non-periodic x or y face
+    decides the ghost intensity (thermal: the ghost layer's B), as in the
+    undecomposed domain, and otherwise the layer's I applies; the
     result then also holds I_zlo and I_zhi, every ray's intensity on the first
     and last z plane [na][ny][nx].
     Returns a dict with J, lstar, G_next (and H [3], K [6] when ``moments``)."""
@@ -221,7 +224,7 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
         side = {}
         for key in ("lo", "hi"):
-            side[key] = tuple(f64(a) for a in ext[key]) if key in ext else (None, None, None)
+            side[key] = tuple(f64(a) for a in ext[key]) if key in ext else (None, None, None, None)
         nface = grid.n[0] * grid.n[1]
         Izlo = np.empty(na * nface)
         Izhi = np.empty(na * nface)
@@ -494,6 +497,8 @@ def slab_ali_solve(grid: Grid, chi, eps, B, nslab, freq_w=None, tol=1e-6, max_it
     nx, ny, nz = grid.n
     if grid.two_d or not (1 <= nslab <= nz):
         raise ValueError("slabs split the z axis of a 3D grid into 1..nz parts")
+    if nslab > 1 and FIXED in tuple(grid.bc_lo[:2]) + tuple(grid.bc_hi[:2]):
+        raise ValueError("slabs need x and y faces without fixed incident intensities")
     per_z = grid.bc_lo[2] == PERIODIC
     z0 = [(d * nz) // nslab for d in range(nslab + 1)]
     n_mu = {8: 2, 24: 4, 48: 6, 80: 8, 120: 10, 168: 12}[grid.na]
@@ -525,9 +530,9 @@ def slab_ali_solve(grid: Grid, chi, eps, B, nslab, freq_w=None, tol=1e-6, max_it
                 sl = slice(z0[d], z0[d + 1])
                 ext = {}
                 if g.bc_lo[2] == EXTERNAL:
-                    ext["lo"] = (chi[f, below(d)], S[f, below(d)], I_lo[f][d])
+                    ext["lo"] = (chi[f, below(d)], S[f, below(d)], I_lo[f][d], B[f, below(d)])
                 if g.bc_hi[2] == EXTERNAL:
-                    ext["hi"] = (chi[f, above(d)], S[f, above(d)], I_hi[f][d])
+                    ext["hi"] = (chi[f, above(d)], S[f, above(d)], I_hi[f][d], B[f, above(d)])
                 res = formal_solution(g, chi[f, sl], S[f, sl], B[f, sl], G[f][d], nthreads=nthreads, ext=ext)
                 J[f, sl] = res["J"]
                 if it == 1:

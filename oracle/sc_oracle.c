@@ -57,9 +57,9 @@ typedef struct {
   long goff[3];     /* offset of each face inside one angle's ghost block */
   long gsize;       /* ghost block per angle */
   /* z faces of kind BC_EXTERNAL (a subdomain face, Sec. 3.5): the ghost layer's
-     chi and S [ny][nx] and each ray's intensity there [na][ny][nx], supplied by
-     the caller (lo = 0, hi = 1); NULL elsewhere */
-  const double *xchi[2], *xS[2], *xI[2];
+     chi, S and B [ny][nx] and each ray's intensity there [na][ny][nx], supplied
+     by the caller (lo = 0, hi = 1); NULL elsewhere */
+  const double *xchi[2], *xS[2], *xI[2], *xB[2];
 } geom;
 
 static long cell_index(const geom *g, int i, int j, int k) {
@@ -93,20 +93,33 @@ static double ghost_I(const geom *g, const int c[3], int angle, int na,
       }
     }
   }
+  /* A vertex past a subdomain (EXTERNAL) z face lies inside the undecomposed
+     domain's z range, so there the z axis does not decide: the x and y faces do
+     (as they would in the undecomposed domain), and only when neither of them is
+     an out-of-range non-periodic face does the neighbour's intensity apply. */
+  int ext_side = -1;
+  if (oor[2]) {
+    int side = c[2] < 0 ? 0 : 1;
+    if ((side ? g->bc_hi[2] : g->bc_lo[2]) == BC_EXTERNAL) ext_side = side;
+  }
   /* first non-periodic out-of-range axis in the order z, y, x */
   for (int a = 2; a >= 0; --a) {
-    if (!oor[a]) continue;
+    if (!oor[a] || (a == 2 && ext_side >= 0)) continue;
     int side = c[a] < 0 ? 0 : 1;
     int bc = side ? g->bc_hi[a] : g->bc_lo[a];
     if (bc != BC_PERIODIC) { fixed_axis = a; fixed_side = side; break; }
   }
+  if (fixed_axis < 0 && ext_side >= 0)
+    return g->xI[ext_side][(long)angle * g->face[2] + face_index(g, 2, m[0], m[1], m[2])];
   if (fixed_axis >= 0) {
     int bc = fixed_side ? g->bc_hi[fixed_axis] : g->bc_lo[fixed_axis];
     if (bc == BC_VACUUM) return 0.0;
-    if (bc == BC_THERMAL) return B[cell_index(g, m[0], m[1], m[2])];
-    if (bc == BC_EXTERNAL)   /* z faces only */
-      return g->xI[fixed_side][(long)angle * g->face[2] + face_index(g, 2, m[0], m[1], m[2])];
-    /* BC_FIXED */
+    if (bc == BC_THERMAL) {
+      /* B of the adjacent layer: past an external z face, the neighbour's plane */
+      if (ext_side >= 0) return g->xB[ext_side][face_index(g, 2, m[0], m[1], m[2])];
+      return B[cell_index(g, m[0], m[1], m[2])];
+    }
+    /* BC_FIXED (rejected together with an external z face) */
     long off = 0;
     for (int f = 0; f < 2 * fixed_axis + fixed_side; ++f) off += (long)na * g->face[f / 2];
     return I_fixed[off + (long)angle * g->face[fixed_axis] +
@@ -161,19 +174,24 @@ int orc_formal_solution_ext(int nx, int ny, int nz, double dx, double dy, double
                             const double *I_fixed, const double *G_prev, double *G_next,
                             double *J, double *lstar, double *H, double *K, int nthreads,
                             const double *xchi_lo, const double *xS_lo, const double *xI_lo,
+                            const double *xB_lo,
                             const double *xchi_hi, const double *xS_hi, const double *xI_hi,
+                            const double *xB_hi,
                             double *I_zlo, double *I_zhi) {
   geom g;
   memset(&g, 0, sizeof g);
-  g.xchi[0] = xchi_lo; g.xS[0] = xS_lo; g.xI[0] = xI_lo;
-  g.xchi[1] = xchi_hi; g.xS[1] = xS_hi; g.xI[1] = xI_hi;
+  g.xchi[0] = xchi_lo; g.xS[0] = xS_lo; g.xI[0] = xI_lo; g.xB[0] = xB_lo;
+  g.xchi[1] = xchi_hi; g.xS[1] = xS_hi; g.xI[1] = xI_hi; g.xB[1] = xB_hi;
   for (int side = 0; side < 2; ++side) {
     const int bc = side ? bc_hi[2] : bc_lo[2];
-    if ((bc == BC_EXTERNAL) != (g.xchi[side] && g.xS[side] && g.xI[side])) return -1;
+    if ((bc == BC_EXTERNAL) != (g.xchi[side] && g.xS[side] && g.xI[side] && g.xB[side])) return -1;
   }
   if (bc_lo[0] == BC_EXTERNAL || bc_hi[0] == BC_EXTERNAL || bc_lo[1] == BC_EXTERNAL ||
       bc_hi[1] == BC_EXTERNAL)
     return -1;   /* subdomain faces are z faces */
+  if ((bc_lo[2] == BC_EXTERNAL || bc_hi[2] == BC_EXTERNAL) &&
+      (bc_lo[0] == BC_FIXED || bc_hi[0] == BC_FIXED || bc_lo[1] == BC_FIXED || bc_hi[1] == BC_FIXED))
+    return -1;   /* a fixed x/y face would need the neighbour's incident intensities */
   g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
   g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
   g.two_d = (nz == 1);
@@ -324,7 +342,7 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
                         double *J, double *lstar, double *H, double *K, int nthreads) {
   return orc_formal_solution_ext(nx, ny, nz, dx, dy, dz, bc_lo, bc_hi, na, mu, wq, chi, S, B,
                                  I_fixed, G_prev, G_next, J, lstar, H, K, nthreads,
-                                 NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+                                 NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------

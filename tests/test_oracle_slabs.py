@@ -64,6 +64,27 @@ def test_periodic_slabs_converge_to_the_single_domain(nslab):
     np.testing.assert_allclose(rs["S"], ref["S"], rtol=50 * tol)
 
 
+@pytest.mark.parametrize("nslab", [2, 3])
+def test_slabs_with_bounded_side_faces_converge_to_the_single_domain(nslab):
+    # vacuum and thermal x and y faces: a ghost vertex past a slab face and past
+    # one of them takes that face's rule, as in the undecomposed domain
+    tol = 1e-9
+    T, V = O.THERMAL, O.VACUUM
+    p = W.random_box(5, 6, 9, seed=33, n_mu=4, bc_lo=(T, V, T), bc_hi=(V, T, V))
+    g, ref = _single(p, tol)
+    rs = O.slab_ali_solve(g, p.chi, p.eps, p.B, nslab, tol=tol, max_iter=5000)
+    assert rs["converged"]
+    np.testing.assert_allclose(rs["S"], ref["S"], rtol=50 * tol)
+    np.testing.assert_allclose(rs["J"], ref["J"], rtol=50 * tol)
+
+
+def test_slabs_reject_fixed_side_faces():
+    p = W.random_box(4, 4, 6, seed=3, n_mu=4, bc_lo=(O.FIXED, P, O.THERMAL), bc_hi=(O.FIXED, P, O.VACUUM))
+    g = O.Grid.from_problem(p)
+    with pytest.raises(ValueError):
+        O.slab_ali_solve(g, p.chi, p.eps, p.B, 2)
+
+
 def test_constant_fields_stay_exact_across_slab_faces():
     p = W.uniform_box(6, chi=0.7, eps=0.3, B=2.0, n_mu=6)
     g = O.Grid.from_problem(p)
