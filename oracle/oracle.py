@@ -67,7 +67,16 @@ def _load():
         lib.orc_gs_is_reverse.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double]
         lib.orc_gs_is_reverse.restype = ctypes.c_int
-        lib.orc_formal_solution_ext.argtypes = lib.orc_formal_solution.argtypes + [d] * 10
+        geo = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+               ctypes.c_double, ip, ip]
+        lib.orc_gs_cell_is_reverse.argtypes = lib.orc_gs_is_reverse.argtypes
+        lib.orc_gs_cell_is_reverse.restype = ctypes.c_int
+        lib.orc_gs_cell_weights.argtypes = geo + [ctypes.c_int, d, d, ip, d, d]
+        lib.orc_gs_cell_weights.restype = ctypes.c_int
+        lib.orc_gs_cell_reverse.argtypes = geo + [ctypes.c_int, d, d, ip, d, d, d, d, d, d, d, d,
+                                                  d, d, ctypes.c_int, d, d, d, d]
+        lib.orc_gs_cell_reverse.restype = ctypes.c_int
+        lib.orc_formal_solution_ext.argtypes = lib.orc_formal_solution.argtypes + [d] * 11
         lib.orc_formal_solution_ext.restype = ctypes.c_int
         lib.orc_bezier_weights.argtypes = [ctypes.c_double, d]
         lib.orc_bezier_weights.restype = None
@@ -161,7 +170,7 @@ def _ray_subset_fixed(grid: Grid, I_fixed, rays):
 
 
 def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=False,
-                    nthreads=1, interp="linear", rays=None, ext=None):
+                    nthreads=1, interp="linear", rays=None, ext=None, S_ghost=None):
     """One formal solution for one frequency.
 
     ``interp``: "linear" (bilinear face interpolation, linear S along the segment)
@@ -180,6 +189,8 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     undecomposed domain, and otherwise the layer's I applies; the
     result then also holds I_zlo and I_zhi, every ray's intensity on the first
     and last z plane [na][ny][nx].
+    ``S_ghost`` (linear only): S at ghost vertices is read from this array
+    (the cell it copies or images) instead of from S.
     Returns a dict with J, lstar, G_next (and H [3], K [6] when ``moments``)."""
     lib = _load()
     C = grid.cells
@@ -218,6 +229,8 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
             _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
             int(nthreads))
     Izlo = Izhi = None
+    if S_ghost is not None and ext is None:
+        ext = {}
     if ext is not None:
         if interp != "linear":
             raise ValueError("external faces are supported with linear interpolation")
@@ -228,14 +241,16 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
         nface = grid.n[0] * grid.n[1]
         Izlo = np.empty(na * nface)
         Izhi = np.empty(na * nface)
+        Sg = None if S_ghost is None else np.ascontiguousarray(S_ghost, dtype=np.float64).reshape(-1)
         rc = lib.orc_formal_solution_ext(*args, *[_ptr(a) for a in side["lo"]],
-                                         *[_ptr(a) for a in side["hi"]], _ptr(Izlo), _ptr(Izhi))
+                                         *[_ptr(a) for a in side["hi"]], _ptr(Izlo), _ptr(Izhi),
+                                         _ptr(Sg))
     else:
         rc = fn(*args)
     if rc != 0:
         raise RuntimeError(f"oracle formal solution failed ({rc})")
     out = dict(J=J.reshape(grid.shape), lstar=L.reshape(grid.shape), G_next=G_next)
-    if ext is not None:
+    if ext:
         out["I_zlo"] = Izlo.reshape(na, grid.n[1], grid.n[0])
         out["I_zhi"] = Izhi.reshape(na, grid.n[1], grid.n[0])
     if moments:
@@ -291,6 +306,62 @@ def gs_reverse(grid: Grid, chi, eps, B, lstar, J_F, S, G_prev, G_next, I_fixed=N
     if rc != 0:
         raise RuntimeError(f"oracle Gauss-Seidel sweep failed ({rc})")
     return dict(J=J.reshape(grid.shape), dS=dS.reshape(grid.shape), C=corr.reshape(grid.shape))
+
+
+def gs_cell_reverse_rays(grid: Grid) -> np.ndarray:
+    """Mask of the reverse rays of the cell-order Gauss-Seidel sweep: mu_V < 0
+    and every upwind vertex visited before the cell in decreasing cell index."""
+    lib = _load()
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    return np.array([bool(lib.orc_gs_cell_is_reverse(grid.n[2], _ptr(mu), k, *grid.d))
+                     for k in range(grid.na)])
+
+
+def gs_cell_weights(grid: Grid, chi) -> np.ndarray:
+    """The forward rays' correction weights [27][nz][ny][nx] (orc_gs_cell_weights)."""
+    lib = _load()
+    chi = np.ascontiguousarray(chi, dtype=np.float64).reshape(-1)
+    fwd = np.ascontiguousarray(~gs_cell_reverse_rays(grid), dtype=np.int32)
+    Wc = np.empty(27 * grid.cells)
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    rc = lib.orc_gs_cell_weights(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1], grid.d[2],
+                                 (ctypes.c_int * 3)(*grid.bc_lo), (ctypes.c_int * 3)(*grid.bc_hi),
+                                 grid.na, _ptr(mu), _ptr(grid.w),
+                                 fwd.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(chi), _ptr(Wc))
+    if rc != 0:
+        raise RuntimeError(f"oracle Gauss-Seidel weights failed ({rc})")
+    return Wc.reshape((27,) + grid.shape)
+
+
+def gs_cell_reverse(grid: Grid, chi, eps, B, lstar, J_F, Wc, S, G_prev, G_next, I_fixed=None,
+                    update=True):
+    """The cell-order reverse sweep of one Gauss-Seidel iteration for one
+    frequency (orc_gs_cell_reverse).  S is updated in place (unless
+    ``update`` is False); G_next holds the forward rays' outflow of the old S
+    and receives the reverse rays' rows.  Returns dict(J, dS, JR, C)."""
+    lib = _load()
+    C = grid.cells
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    chi, eps, B, lstar, J_F, Wc = f64(chi), f64(eps), f64(B), f64(lstar), f64(J_F), f64(Wc)
+    assert S.dtype == np.float64 and S.flags.c_contiguous and S.size == C
+    assert G_next.dtype == np.float64 and G_next.flags.c_contiguous
+    G_prev = np.ascontiguousarray(G_prev, dtype=np.float64)
+    if I_fixed is not None:
+        I_fixed = f64(I_fixed)
+    rev = np.ascontiguousarray(gs_cell_reverse_rays(grid), dtype=np.int32)
+    J, dS, JR, corr = (np.empty(C) for _ in range(4))
+    mu = np.ascontiguousarray(grid.mu).reshape(-1)
+    rc = lib.orc_gs_cell_reverse(grid.n[0], grid.n[1], grid.n[2], grid.d[0], grid.d[1], grid.d[2],
+                                 (ctypes.c_int * 3)(*grid.bc_lo), (ctypes.c_int * 3)(*grid.bc_hi),
+                                 grid.na, _ptr(mu), _ptr(grid.w),
+                                 rev.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 _ptr(chi), _ptr(B), _ptr(eps), _ptr(lstar), _ptr(J_F), _ptr(Wc),
+                                 _ptr(S), _ptr(I_fixed), _ptr(G_prev), _ptr(G_next), int(bool(update)),
+                                 _ptr(J), _ptr(dS), _ptr(JR), _ptr(corr))
+    if rc != 0:
+        raise RuntimeError(f"oracle Gauss-Seidel sweep failed ({rc})")
+    sh = grid.shape
+    return dict(J=J.reshape(sh), dS=dS.reshape(sh), JR=JR.reshape(sh), C=corr.reshape(sh))
 
 
 def max_relative_change(dS: np.ndarray, S: np.ndarray) -> float:
@@ -378,8 +449,15 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
     iteration solves the forward rays with the old S, then ``gs_reverse``
     updates S plane by plane; the J, H, K returned are those of a formal
     solution of the S (and ghosts) that the last iteration started from, and
-    ``J_gs`` holds the J each cell was last updated with."""
-    if method not in ("jacobi", "gauss_seidel"):
+    ``J_gs`` holds the J each cell was last updated with.
+
+    method="gauss_seidel_cell": the paper's cell order (Sec. 3.4): the forward
+    rays of ``gs_cell_reverse_rays`` are solved with the old S, then
+    ``gs_cell_reverse`` visits the cells by decreasing index, updating each
+    cell's S with the reverse rays' J of the current S plus the forward rays'
+    J corrected to first order with the weights of ``gs_cell_weights``;
+    outputs as for "gauss_seidel"."""
+    if method not in ("jacobi", "gauss_seidel", "gauss_seidel_cell"):
         raise ValueError(f"unknown ALI method {method!r}")
     chi = np.asarray(chi, dtype=np.float64).reshape((-1,) + grid.shape)
     eps = np.asarray(eps, dtype=np.float64).reshape(chi.shape)
@@ -397,11 +475,16 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
     r = math.inf
     it = 0
     S_fs, G_fs = S, G
-    gs = method == "gauss_seidel" and not lte
+    gs = method in ("gauss_seidel", "gauss_seidel_cell") and not lte
+    cell = method == "gauss_seidel_cell"
     if gs and interp != "linear":
         raise ValueError("the Gauss-Seidel iteration takes linear interpolation")
-    fwd = np.flatnonzero(~gs_reverse_rays(grid)) if gs else None
+    if gs:
+        fwd = np.flatnonzero(~(gs_cell_reverse_rays(grid) if cell else gs_reverse_rays(grid)))
+    else:
+        fwd = None
     J_gs = np.empty_like(chi) if gs else None
+    Wc = [gs_cell_weights(grid, chi[f]) for f in range(nf)] if (gs and cell) else None
     for it in range(1, max_iter + 1):
         if gs:
             S_new = S.copy()
@@ -416,8 +499,12 @@ def ali_solve(grid: Grid, chi, eps, B, freq_w=None, tol=1e-6, max_iter=1000, S_i
                 Gn = G[f].copy()
                 Gn[fwd] = res["G_next"]
                 Sf = np.ascontiguousarray(S_new[f]).reshape(-1)
-                out = gs_reverse(grid, chi[f], eps[f], B[f], lstar[f], res["J"], Sf, G[f], Gn,
-                                 fixed(f))
+                if cell:
+                    out = gs_cell_reverse(grid, chi[f], eps[f], B[f], lstar[f], res["J"], Wc[f], Sf,
+                                          G[f], Gn, fixed(f))
+                else:
+                    out = gs_reverse(grid, chi[f], eps[f], B[f], lstar[f], res["J"], Sf, G[f], Gn,
+                                     fixed(f))
                 S_new[f] = Sf.reshape(grid.shape)
                 dS[f] = out["dS"]
                 J_gs[f] = out["J"]

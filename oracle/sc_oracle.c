@@ -60,6 +60,10 @@ typedef struct {
      chi, S and B [ny][nx] and each ray's intensity there [na][ny][nx], supplied
      by the caller (lo = 0, hi = 1); NULL elsewhere */
   const double *xchi[2], *xS[2], *xI[2], *xB[2];
+  /* when set, S at a ghost vertex is read from this array (same layout as S)
+     instead of S itself: the ghost layers of the start of a Gauss-Seidel
+     iteration */
+  const double *Sg;
 } geom;
 
 static long cell_index(const geom *g, int i, int j, int k) {
@@ -158,6 +162,11 @@ static double field_value(const geom *g, const int c[3], const double *f, int wh
     }
     return x[side][face_index(g, 2, m[0], m[1], 0)];
   }
+  if (which && g->Sg) {
+    const int inside = c[0] >= 0 && c[0] < g->n[0] && c[1] >= 0 && c[1] < g->n[1] && c[2] >= 0 &&
+                       c[2] < g->n[2];
+    if (!inside) return g->Sg[map_field(g, c)];
+  }
   return f[map_field(g, c)];
 }
 
@@ -177,9 +186,10 @@ int orc_formal_solution_ext(int nx, int ny, int nz, double dx, double dy, double
                             const double *xB_lo,
                             const double *xchi_hi, const double *xS_hi, const double *xI_hi,
                             const double *xB_hi,
-                            double *I_zlo, double *I_zhi) {
+                            double *I_zlo, double *I_zhi, const double *S_ghost) {
   geom g;
   memset(&g, 0, sizeof g);
+  g.Sg = S_ghost;
   g.xchi[0] = xchi_lo; g.xS[0] = xS_lo; g.xI[0] = xI_lo; g.xB[0] = xB_lo;
   g.xchi[1] = xchi_hi; g.xS[1] = xS_hi; g.xI[1] = xI_hi; g.xB[1] = xB_hi;
   for (int side = 0; side < 2; ++side) {
@@ -342,7 +352,7 @@ int orc_formal_solution(int nx, int ny, int nz, double dx, double dy, double dz,
                         double *J, double *lstar, double *H, double *K, int nthreads) {
   return orc_formal_solution_ext(nx, ny, nz, dx, dy, dz, bc_lo, bc_hi, na, mu, wq, chi, S, B,
                                  I_fixed, G_prev, G_next, J, lstar, H, K, nthreads,
-                                 NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+                                 NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------
@@ -875,4 +885,287 @@ int orc_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------
+ * Gauss-Seidel ALI in the paper's cell order (Sec. 3.4, after Trujillo Bueno
+ * & Fabiani Bendicho 1995, generalised to 3D with linear interpolation).
+ *
+ * The reverse sweep visits the cells one at a time in the reverse of the
+ * paper's sweep order: V (z; y in 2D) from the top down, within a plane y
+ * descending, within a row x descending -- i.e. by decreasing cell index,
+ * starting at the top corner cell (x_N, y_N[, z_N]).  Each visited cell's S is
+ * updated at once with Eq. 24 and every later computation uses the new value.
+ *
+ * Rays split in two sets:
+ *   reverse rays: every upwind vertex (of nonzero weight) of a cell has a larger
+ *     cell index than the cell, i.e. is visited first.  These are the downward
+ *     rays (mu_V < 0) that cross the V face, or cross a face of another axis
+ *     while pointing to decreasing index along every axis they move in.  Their
+ *     intensities are computed during the reverse sweep, at the visit of each
+ *     cell, from the intensities and the current S of its upwind vertices;
+ *   forward rays: all others (the upward rays, and downward rays swept against
+ *     the reverse order).  Their formal solution is done beforehand with the
+ *     old S (J_F).  When a cell m gets its new S, the forward rays' J of the
+ *     cells that have m as an upwind vertex is corrected to first order with
+ *     weights saved beforehand: for each such vertex, w * wv * [Psi-(n) dS(m)
+ *     + E(n) Psi0(m) dS(m)], the change through the interpolated S and through
+ *     the interpolated intensity (the outgoing intensity at m, which takes
+ *     Psi0(m) dS(m)).  The correction is not transported further.
+ * The ghost layers (chi, S and the intensities, lagged or prescribed) are those
+ * of the start of the iteration: a ghost vertex's S does not change during the
+ * sweep, so only interior vertices carry corrections.  After the update of a
+ * cell every ray's intensity there takes Psi0 dS (the outgoing intensities are
+ * updated): the reverse rays' downwind cells then see it, and so do the outflow
+ * ghosts of the next iteration (periodic faces).
+ *
+ * At convergence dS = 0, every correction vanishes, and the fixed point is the
+ * Jacobi one.
+ * ---------------------------------------------------------------------- */
+
+static int setup_geom(geom *g, int nx, int ny, int nz, double dx, double dy, double dz,
+                      const int *bc_lo, const int *bc_hi) {
+  memset(g, 0, sizeof *g);
+  g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
+  g->d[0] = dx; g->d[1] = dy; g->d[2] = dz;
+  g->two_d = (nz == 1);
+  for (int a = 0; a < 3; ++a) { g->bc_lo[a] = bc_lo[a]; g->bc_hi[a] = bc_hi[a]; }
+  g->cells = (long)nx * ny * nz;
+  g->face[0] = (long)nz * ny; g->face[1] = (long)nz * nx; g->face[2] = (long)ny * nx;
+  g->goff[0] = 0; g->goff[1] = g->face[0]; g->goff[2] = g->face[0] + g->face[1];
+  g->gsize = g->face[0] + g->face[1] + g->face[2];
+  return (nx < 1 || ny < 1 || nz < 1) ? -1 : 0;
+}
+
+/* 1 if ray k is a reverse ray of the cell-order Gauss-Seidel sweep */
+int orc_gs_cell_is_reverse(int nz, const double *mu, int k, double dx, double dy, double dz) {
+  geom g;
+  memset(&g, 0, sizeof g);
+  g.two_d = (nz == 1);
+  g.d[0] = dx; g.d[1] = dy; g.d[2] = dz;
+  const int V = g.two_d ? 1 : 2;
+  if (mu[3 * k + V] >= 0.0) return 0;
+  int ax, sgn[3];
+  double s, frac[3];
+  ray_geometry(&g, &mu[3 * k], &ax, &s, frac, sgn);
+  const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+  for (int d1 = 0; d1 < 2; ++d1) {
+    for (int d2 = 0; d2 < 2; ++d2) {
+      const double wv = (d1 ? frac[b1] : 1.0 - frac[b1]) * (d2 ? frac[b2] : 1.0 - frac[b2]);
+      if (wv == 0.0) continue;
+      int o[3];
+      o[ax] = -sgn[ax];
+      o[b1] = -d1 * sgn[b1];
+      o[b2] = -d2 * sgn[b2];
+      /* visited first: the first nonzero offset in the order z, y, x is positive */
+      const int first = o[2] != 0 ? o[2] : (o[1] != 0 ? o[1] : o[0]);
+      if (first <= 0) return 0;
+    }
+  }
+  return 1;
+}
+
+/* offset slot of a vertex relative to its cell, (dx, dy, dz) in {-1, 0, 1}^3 */
+static int off_slot(const int o[3]) { return (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1); }
+
+/* Upwind-vertex data of ray (ax, sgn, frac) at cell c0: chi-, S- (from S), the
+   dependence weight of the cell's own S through ghost copies (selfw), and per
+   vertex its weight, slot, interior flag and field index. */
+typedef struct {
+  int nv;
+  double wv[4];
+  int slot[4], inside[4];
+  long fi[4], ci[4];
+  int c[4][3];
+} upwind;
+
+static void upwind_vertices(const geom *g, int ax, const int sgn[3], const double frac[3],
+                            const int c0[3], upwind *u) {
+  const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+  u->nv = 0;
+  for (int d1 = 0; d1 < 2; ++d1) {
+    for (int d2 = 0; d2 < 2; ++d2) {
+      const double wv = (d1 ? frac[b1] : 1.0 - frac[b1]) * (d2 ? frac[b2] : 1.0 - frac[b2]);
+      if (wv == 0.0) continue;
+      int c[3], o[3];
+      o[ax] = -sgn[ax];
+      o[b1] = -d1 * sgn[b1];
+      o[b2] = -d2 * sgn[b2];
+      for (int a = 0; a < 3; ++a) c[a] = c0[a] + o[a];
+      const int q = u->nv++;
+      u->wv[q] = wv;
+      u->slot[q] = off_slot(o);
+      u->inside[q] = c[0] >= 0 && c[0] < g->n[0] && c[1] >= 0 && c[1] < g->n[1] && c[2] >= 0 &&
+                     c[2] < g->n[2];
+      u->fi[q] = map_field(g, c);
+      u->ci[q] = u->inside[q] ? cell_index(g, c[0], c[1], c[2]) : -1;
+      for (int a = 0; a < 3; ++a) u->c[q][a] = c[a];
+    }
+  }
+}
+
+/* Correction weights of the forward rays (fwd[k] != 0), once per medium:
+   Wc [27][cells]: for cell n and upwind-vertex slot o, the sum over forward rays
+   with an interior vertex there of w wv [Psi-(n) + E(n) Psi0(vertex)]; slots
+   of ghost vertices stay 0. */
+int orc_gs_cell_weights(int nx, int ny, int nz, double dx, double dy, double dz,
+                        const int *bc_lo, const int *bc_hi, int na, const double *mu,
+                        const double *wq, const int *fwd, const double *chi, double *Wc) {
+  geom g;
+  if (setup_geom(&g, nx, ny, nz, dx, dy, dz, bc_lo, bc_hi) != 0 || na < 1) return -1;
+  const long C = g.cells;
+  double *Dk = (double *)malloc((size_t)C * sizeof(double));
+  if (!Dk) return -2;
+  for (long i = 0; i < 27 * C; ++i) Wc[i] = 0.0;
+  for (int k = 0; k < na; ++k) {
+    if (!fwd[k]) continue;
+    int ax, sgn[3];
+    double s, frac[3];
+    ray_geometry(&g, &mu[3 * k], &ax, &s, frac, sgn);
+    /* pass 1: D of this ray at every cell; pass 2: the weights */
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+          for (int ix = 0; ix < nx; ++ix) {
+            const int c0[3] = {ix, iy, iz};
+            const long ci = cell_index(&g, ix, iy, iz);
+            upwind u;
+            upwind_vertices(&g, ax, sgn, frac, c0, &u);
+            double chim = 0.0;
+            for (int q = 0; q < u.nv; ++q) chim += u.wv[q] * chi[u.fi[q]];
+            double E, psi0, psim;
+            sc_weights(0.5 * (chim + chi[ci]) * s, &E, &psi0, &psim);
+            if (pass == 0) {
+              Dk[ci] = psi0;
+              continue;
+            }
+            for (int q = 0; q < u.nv; ++q) {
+              if (!u.inside[q]) continue;
+              Wc[(long)u.slot[q] * C + ci] += wq[k] * u.wv[q] * (psim + E * Dk[u.ci[q]]);
+            }
+          }
+    }
+  }
+  free(Dk);
+  return 0;
+}
+
+/*
+ * One reverse sweep (one frequency).  rev[k] != 0 marks the reverse rays (the
+ * others are forward rays, already solved into J_F and their rows of G_next).
+ * S in: S^n, out: S^{n+1} (unchanged when update == 0, a dry run in which dS is
+ * taken as 0).  G_next: the reverse rays' rows are written; the forward rays'
+ * rows (their outflow from the old S) take D dS of the outflow cell.
+ * Outputs per cell: J_out (the J it was updated with), dS_out, JR_out (the
+ * reverse rays' part of J), C_out (the forward rays' correction); JR_out and
+ * C_out may be NULL.
+ */
+int orc_gs_cell_reverse(int nx, int ny, int nz, double dx, double dy, double dz,
+                        const int *bc_lo, const int *bc_hi,
+                        int na, const double *mu, const double *wq, const int *rev,
+                        const double *chi, const double *B, const double *eps, const double *lstar,
+                        const double *J_F, const double *Wc, double *S, const double *I_fixed,
+                        const double *G_prev, double *G_next, int update,
+                        double *J_out, double *dS_out, double *JR_out, double *C_out) {
+  geom g;
+  if (setup_geom(&g, nx, ny, nz, dx, dy, dz, bc_lo, bc_hi) != 0 || na < 1) return -1;
+  const long C = g.cells;
+  int nrev = 0;
+  for (int k = 0; k < na; ++k) nrev += rev[k] != 0;
+  double *Ir = (double *)malloc((size_t)(nrev ? nrev : 1) * C * sizeof(double));
+  int *rk = (int *)malloc((size_t)(nrev ? nrev : 1) * sizeof(int));
+  int *rof = (int *)malloc((size_t)na * sizeof(int));          /* reverse slot of ray k, or -1 */
+  double *Dr = (double *)malloc((size_t)(nrev ? nrev : 1) * sizeof(double));
+  double *S0 = (double *)malloc((size_t)C * sizeof(double));   /* S of the ghost layers */
+  if (!Ir || !rk || !rof || !Dr || !S0) {
+    free(Ir); free(rk); free(rof); free(Dr); free(S0);
+    return -2;
+  }
+  memcpy(S0, S, (size_t)C * sizeof(double));
+  {
+    int r = 0;
+    for (int k = 0; k < na; ++k) {
+      rof[k] = rev[k] ? r : -1;
+      if (rev[k]) rk[r++] = k;
+    }
+  }
+  for (long i = 0; i < C; ++i) dS_out[i] = 0.0;
+
+  for (long ci = C - 1; ci >= 0; --ci) {
+    const int c0[3] = {(int)(ci % nx), (int)((ci / nx) % ny), (int)(ci / ((long)nx * ny))};
+    /* the reverse rays at this cell, from their upwind vertices (visited first) */
+    double JR = 0.0;
+    for (int r = 0; r < nrev; ++r) {
+      const int k = rk[r];
+      int ax, sgn[3];
+      double s, frac[3];
+      ray_geometry(&g, &mu[3 * k], &ax, &s, frac, sgn);
+      upwind u;
+      upwind_vertices(&g, ax, sgn, frac, c0, &u);
+      double chim = 0.0, Sm = 0.0, Im = 0.0;
+      for (int q = 0; q < u.nv; ++q) {
+        chim += u.wv[q] * chi[u.fi[q]];
+        Sm += u.wv[q] * (u.inside[q] ? S[u.fi[q]] : S0[u.fi[q]]);
+        Im += u.wv[q] * (u.inside[q] ? Ir[(long)r * C + u.ci[q]]
+                                     : ghost_I(&g, u.c[q], k, na, B, I_fixed, G_prev));
+      }
+      double E, psi0, psim;
+      sc_weights(0.5 * (chim + chi[ci]) * s, &E, &psi0, &psim);
+      const double I0 = Im * E + psim * Sm + psi0 * S[ci];
+      Ir[(long)r * C + ci] = I0;
+      Dr[r] = psi0;
+      JR += wq[k] * I0;
+    }
+    /* the forward rays' first-order correction for the cells already updated */
+    double corr = 0.0;
+    for (int o = 0; o < 27; ++o) {
+      const double wc = Wc[(long)o * C + ci];
+      if (wc == 0.0) continue;
+      const int c[3] = {c0[0] + o % 3 - 1, c0[1] + (o / 3) % 3 - 1, c0[2] + o / 9 - 1};
+      corr += wc * dS_out[map_field(&g, c)];
+    }
+    const double J = J_F[ci] + corr + JR;
+    const double e = eps[ci];
+    const double dS = update ? ((1.0 - e) * J + e * B[ci] - S[ci]) / (1.0 - (1.0 - e) * lstar[ci]) : 0.0;
+    S[ci] += dS;
+    dS_out[ci] = dS;
+    J_out[ci] = J;
+    if (JR_out) JR_out[ci] = JR;
+    if (C_out) C_out[ci] = corr;
+    /* every ray's outgoing intensity at this cell takes D dS; outflow ghosts */
+    for (int r = 0; r < nrev; ++r) Ir[(long)r * C + ci] += Dr[r] * dS;
+    for (int k = 0; k < na; ++k) {
+      int ax, sgn[3];
+      double s, frac[3];
+      ray_geometry(&g, &mu[3 * k], &ax, &s, frac, sgn);
+      int on_face = 0;
+      for (int a = 0; a < 3; ++a)
+        if (g.bc_lo[a] == BC_PERIODIC && c0[a] == (sgn[a] > 0 ? g.n[a] - 1 : 0)) on_face = 1;
+      if (!on_face) continue;
+      const int r = rof[k];
+      double dI = 0.0;
+      if (r < 0 && dS != 0.0) {
+        upwind u;
+        upwind_vertices(&g, ax, sgn, frac, c0, &u);
+        double chim = 0.0;
+        for (int q = 0; q < u.nv; ++q) chim += u.wv[q] * chi[u.fi[q]];
+        double E, psi0, psim;
+        sc_weights(0.5 * (chim + chi[ci]) * s, &E, &psi0, &psim);
+        dI = psi0 * dS;
+      }
+      for (int a = 0; a < 3; ++a) {
+        if (g.bc_lo[a] != BC_PERIODIC) continue;
+        if (c0[a] != (sgn[a] > 0 ? g.n[a] - 1 : 0)) continue;
+        double *gp = &G_next[(long)k * g.gsize + g.goff[a] + face_index(&g, a, c0[0], c0[1], c0[2])];
+        if (r >= 0) *gp = Ir[(long)r * C + ci];
+        else *gp += dI;
+      }
+    }
+  }
+  free(Ir);
+  free(rk);
+  free(rof);
+  free(Dr);
+  free(S0);
+  return 0;
 }
