@@ -1,16 +1,20 @@
-"""Benchmark: converged short-characteristics + Jacobi-ALI solves of the 128^3 box.
+"""Benchmark: converged short-characteristics + Jacobi-ALI solves of the 256^3
+stratified turbulent atmosphere.
 
-Workload: a 128^3 fully periodic box with a log-normal turbulent density
-(k^-11/3 Gaussian random fields, seeds 1 and 2), grey LTE absorption plus
-electron scattering, B = T^4, 80 rays (LQ8), float32 sweeps with the FP64 ALI
-update, solved to max|dS|/S <= 1e-6.  Synthetic inputs, generated here.
+Workload (the largest single-GPU case): a 256^3 grid whose opacity is the
+stratified profile (vertical optical depth log-spaced from 1e-4 at the top to
+1e3 at the bottom) times a log-normal turbulent density (k^-11/3 Gaussian random
+field, seed 1), photon destruction probability eps = 1e-3, B = T^4 (log-normal
+T, seed 2), periodic x/y, I = B below and vacuum above, 48 rays (LQ6), float32
+sweeps with the FP64 ALI update, solved to max|dS|/S <= 1e-6; outputs J, the
+Eddington tensor K/J and the heating rate.  Synthetic inputs, generated here.
 
 One step = the whole hot path on resident device inputs: set the medium
 (validation, sweep-precision copies, Lambda*, ghosts), the ALI solve to
 convergence (formal solutions + updates), and the outputs (J, H, K, K/J, Q).
 Metric: cell*ray*frequency updates per second (updates = cells * rays *
 frequencies * formal solutions).  The L2 cache is flushed (256 MB written)
-before every timed step.
+before every timed step (the step's inputs, 400 MB, exceed it anyway).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,8 +40,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell*ray*nu updates/s"
 UNIT = "updates/s"
-N_BOX = 128
-N_MU = 8
+N_BOX = 256
+N_MU = 6
 TOL = 1e-6
 # algorithmic FP32 operations of one cell*ray update (Eq. 20 with linear
 # interpolation): three bilinear interpolants (chi-, S-, I-: 4 multiplies + 3 adds
@@ -45,15 +49,13 @@ TOL = 1e-6
 # Psi0 = e1 / dtau, Psi- = e0 - Psi0 (4), I0 = I- E + Psi- S- + Psi0 S0 (3 multiplies
 # + 2 adds), the J accumulation (multiply, add); the exponential is counted apart
 FLOPS_PER_UPDATE = 34
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-
+# special-function results per update: the exponential and the reciprocal of dtau
+MUFU_PER_UPDATE = 2
 
 # DRAM read + write bytes per launch of the sweep kernel from an ncu capture of
-# this workload and plan (profiles/sc_sweep_pipe_kernel_turbulent_box_128_lq8.md);
-# reported only for that plan, and to be re-taken whenever the kernel changes
-# (keyed by workload, plan and shared-memory size, which changes with the kernel's layout)
-PROFILED_TRAFFIC = {("turbulent_box_128^3_lq8", 3, 7, 10, 512, 175896): 119.319296e6 + 100.647168e6}
+# the same workload and plan (None when none was taken for the plan in use, or
+# the kernel has changed since); keyed by workload, plan and shared-memory size
+PROFILED_TRAFFIC = {}
 
 
 def profiled_traffic(plan, p):
@@ -65,13 +67,14 @@ def profiled_traffic(plan, p):
 SWEEP_KERNEL_NAMES = {1: "sc_sweep_kernel<float>", 2: "sc_sweep_tiled_kernel<float>",
                       3: "sc_sweep_pipe_kernel<float>"}
 
+
 def workload():
     from paper_1201_2222_gb300 import workloads as W
-    return W.turbulent_box(N_BOX, n_mu=N_MU, tol=TOL)
+    return W.large_stratified_turbulent(N_BOX, n_mu=N_MU, tol=TOL)
 
 
 def config_dict(p, flush):
-    return {"workload": f"turbulent_box_{p.nx}^3_LQ{p.n_mu}_{p.n_angles}rays_grey_eps_var_tol{TOL:g}",
+    return {"workload": f"stratified_turbulent_{p.nx}^3_LQ{p.n_mu}_{p.n_angles}rays_grey_eps1e-3_tol{TOL:g}",
             "cells": p.cells, "rays": p.n_angles, "frequencies": p.nf,
             "precision": "float32 sweeps, FP64 ALI", "l2": flush}
 
@@ -205,6 +208,47 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def sweep_roofline(stats_list, p, rates):
+    """Roofline of the formal-solution kernel from the sweep launches timed inside
+    the solves (CUDA events on the launching stream)."""
+    sweep_ms = sum(s["sweep_ms"] for s in stats_list)
+    sweep_n = sum(s["sweep_launches"] for s in stats_list)
+    per_launch_upd = p.cells * p.n_angles * p.nf
+    avg_s = (sweep_ms / sweep_n) / 1e3 if sweep_n else float("nan")
+    achieved = FLOPS_PER_UPDATE * per_launch_upd / avg_s / 1e12
+    peak = max(rates["fp32_fma_flops"], rates["fp32x2_fma_flops"]) / 1e12
+    mufu_peak = min(rates["mufu_ex2_per_s"], rates["mufu_rcp_per_s"])
+    return {"avg_launch_ms": avg_s * 1e3, "launches": sweep_n, "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "updates_per_s": per_launch_upd / avg_s,
+            "mufu_frac": MUFU_PER_UPDATE * per_launch_upd / avg_s / mufu_peak}
+
+
+def solve_rate(rt, p, prec, dev, n=2, tol=None, autotune=True):
+    """Time n converged solves (after one untimed) of problem p; CUDA-event sweep
+    statistics of the last one."""
+    import torch
+    tol = p.tol if tol is None else tol
+    chi, eps, B, fw = (torch.from_numpy(x).to(dev) for x in (p.chi, p.eps, p.B, p.freq_w))
+    g = rt.Grid.from_problem(p, prec=prec)
+    g.set_opacity_source(chi, eps, B, fw)
+    if autotune:
+        g.autotune()
+    g.ali_solve(tol=tol, max_iter=20000)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(n):
+        it, _, _ = g.ali_solve(tol=tol, max_iter=20000)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / n
+    g.enable_timing(True)
+    g.ali_solve(tol=tol, max_iter=20000)
+    st = g.stats()
+    plan = g.sweep_plan()
+    g.close()
+    return {"workload": p.name, "iters": it, "ms_per_solve": 1e3 * dt, "solves_per_s": 1.0 / dt,
+            "updates_per_s": p.cells * p.n_angles * p.nf * it / dt, "plan": plan, "stats": st}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -218,8 +262,10 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     from paper_1201_2222_gb300 import build, rt, workloads as W
     build.build()
-    p = workload()
     dev = torch.device("cuda", torch.cuda.current_device())
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    rates = rt.measure_rates()          # measured arithmetic peaks of this GPU
+    p = workload()
     chi = torch.from_numpy(p.chi).to(dev)
     eps = torch.from_numpy(p.eps).to(dev)
     B = torch.from_numpy(p.B).to(dev)
@@ -236,8 +282,8 @@ def run_gpu(args):
 
     def step(out):
         g.set_opacity_source(chi, eps, B, fw)
-        iters, resid, st = g.ali_solve(tol=TOL, max_iter=2000)
-        m = g.moments(on_device=True)
+        iters, resid, st = g.ali_solve(tol=TOL, max_iter=20000)
+        m = g.moments(on_device=True, want=("J", "f", "Q"))
         out.append((iters, resid, g.stats()))
         return m
 
@@ -274,79 +320,57 @@ def run_gpu(args):
     upd_local = float(sum(s["updates"] for _, _, s in rec))
     t_max, upd_all = reduce_max_sum(t_local, upd_local, dist)
     iters = [i for i, _, _ in rec]
-    sweep_ms = sum(s["sweep_ms"] for _, _, s in rec)
-    sweep_n = sum(s["sweep_launches"] for _, _, s in rec)
+    roof = sweep_roofline([s for _, _, s in rec], p, rates)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if True:
-        e2e_t = []
-        e2e_upd = 0
-        N = p.chi.size
-        h2d = 3 * N * 8 + p.nf * 8
-        d2h = (N + p.cells) * 8
-        # the step's inputs and its results (J, Q) in pinned host memory
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
-        chi_h, eps_h, B_h, fw_h = pin(p.chi), pin(p.eps), pin(p.B), pin(p.freq_w)
-        J_h = torch.empty(p.chi.shape, dtype=torch.float64).pin_memory()
-        Q_h = torch.empty(p.chi.shape[1:], dtype=torch.float64).pin_memory()
-        for i in range(1 + max(2, args.steps // 2)):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            g.set_opacity_source(chi_h, eps_h, B_h, fw_h)
-            it, _, _ = g.ali_solve(tol=TOL, max_iter=2000)
-            m = g.moments(on_device=False, want=("J", "Q"), out={"J": J_h, "Q": Q_h})
-            _ = float(m["Q"].sum())
-            dt = time.perf_counter() - t
-            if i > 0:
-                e2e_t.append(dt)
-                e2e_upd += p.cells * p.n_angles * p.nf * it
-        e2e_local = sum(e2e_t)
-        e2e_tmax, e2e_updall = reduce_max_sum(e2e_local, float(e2e_upd), dist)
-        e2e = {"value": e2e_updall / e2e_tmax, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
-
-    # plain FP64 GPU path for the mixed-vs-FP64 solves/s comparison (2 solves)
-    fp64 = None
-    if not args.skip_fp64:
-        g64 = rt.Grid.from_problem(p, prec=rt.FP64)
-        g64.set_opacity_source(chi, eps, B, fw)
-        g64.autotune()
-        g64.ali_solve(tol=TOL, max_iter=2000)
+    e2e_t = []
+    e2e_upd = 0
+    N = p.chi.size
+    h2d = 3 * N * 8 + p.nf * 8
+    d2h = (N + p.cells) * 8
+    # the step's inputs and its results (J, Q) in pinned host memory
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    chi_h, eps_h, B_h, fw_h = pin(p.chi), pin(p.eps), pin(p.B), pin(p.freq_w)
+    J_h = torch.empty(p.chi.shape, dtype=torch.float64).pin_memory()
+    Q_h = torch.empty(p.chi.shape[1:], dtype=torch.float64).pin_memory()
+    for i in range(1 + max(2, args.steps // 2)):
+        flush.fill_(1.0)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        it64, _, _ = g64.ali_solve(tol=TOL, max_iter=2000)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t
-        fp64 = {"solves_per_s": 1.0 / t64, "iters": it64,
-                "updates_per_s": p.cells * p.n_angles * p.nf * it64 / t64}
-        g64.close()
+        g.set_opacity_source(chi_h, eps_h, B_h, fw_h)
+        it, _, _ = g.ali_solve(tol=TOL, max_iter=20000)
+        m = g.moments(on_device=False, want=("J", "Q"), out={"J": J_h, "Q": Q_h})
+        _ = float(m["Q"].sum())
+        dt = time.perf_counter() - t
+        if i > 0:
+            e2e_t.append(dt)
+            e2e_upd += p.cells * p.n_angles * p.nf * it
+    e2e_tmax, e2e_updall = reduce_max_sum(sum(e2e_t), float(e2e_upd), dist)
+    e2e = {"value": e2e_updall / e2e_tmax, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    plan = g.sweep_plan()
+    g.close()
 
-    # the second-order option (quadratic face interpolation): formal-solution rate
-    # on the same medium, mixed precision, its own tuned plan
-    quad = None
-    if not args.skip_quad:
-        gq = rt.Grid.from_problem(p, prec=rt.MIXED)
-        gq.set_interpolation(rt.INTERP_QUADRATIC)
-        gq.set_opacity_source(chi, eps, B, fw)
-        gq.autotune()
-        gq.enable_timing(True)
-        gq.formal_solve(None)
-        qms = []
-        for _ in range(5):
-            gq.formal_solve(None)
-            qms.append(gq.stats()["sweep_ms"])
-        qms.sort()
-        quad = {"kernel": "sc_sweep_quad_kernel<float>", "sweep_ms_median": qms[len(qms) // 2],
-                "updates_per_s": p.cells * p.n_angles * p.nf / (qms[len(qms) // 2] / 1e3),
-                "plan": gq.sweep_plan()}
-        gq.close()
-
-    # the Gauss-Seidel scheme against Jacobi on the stratified scattering
-    # atmosphere (32^3, LQ4, eps 1e-2, FP64, tol 1e-6): iterations and solve time
-    gs = None
-    if not args.skip_gs:
+    extras = {}
+    if not args.skip_extras:
+        # the 128^3 periodic turbulent box (80 rays): mixed, and the plain FP64 path
+        pb = W.turbulent_box(128, n_mu=8, tol=TOL)
+        box = solve_rate(rt, pb, rt.MIXED, dev)
+        box["roofline"] = sweep_roofline([box.pop("stats")], pb, rates)
+        extras["turbulent_box_128"] = box
+        b64 = solve_rate(rt, pb, rt.FP64, dev, n=1)
+        b64.pop("stats")
+        extras["turbulent_box_128_fp64_path"] = b64
+        extras["mixed_over_fp64_solves_per_s"] = box["solves_per_s"] / b64["solves_per_s"]
+    if not args.skip_extras and not args.skip_multifreq:
+        # the 64^3 atmosphere with 64 frequency bins (all bins in one launch)
+        pm = W.multifrequency_atmosphere(64, nf=64)
+        mf = solve_rate(rt, pm, rt.MIXED, dev, n=1)
+        mf["roofline"] = sweep_roofline([mf.pop("stats")], pm, rates)
+        extras["multifrequency_64_64bins"] = mf
+    if not args.skip_extras and not args.skip_gs:
+        # the Gauss-Seidel scheme against Jacobi on the stratified scattering
+        # atmosphere (32^3, LQ4, eps 1e-2, FP64, tol 1e-6): iterations and solve time
         pa = W.stratified_atmosphere(32)
         gs = {"workload": f"{pa.name} (FP64, tol {pa.tol:g})"}
         for scheme in ("jacobi", "gauss_seidel"):
@@ -364,43 +388,59 @@ def run_gpu(args):
             ga.close()
         gs["iteration_ratio"] = gs["jacobi"]["iters"] / gs["gauss_seidel"]["iters"]
         gs["time_ratio"] = gs["jacobi"]["ms_per_solve"] / gs["gauss_seidel"]["ms_per_solve"]
+        extras["gauss_seidel"] = gs
+    if not args.skip_extras and not args.skip_quad:
+        # the second-order option (quadratic face interpolation): formal-solution
+        # rate on the 128^3 box, mixed precision, its own tuned plan
+        pb = W.turbulent_box(128, n_mu=8, tol=TOL)
+        gq = rt.Grid.from_problem(pb, prec=rt.MIXED)
+        gq.set_interpolation(rt.INTERP_QUADRATIC)
+        gq.set_opacity_source(pb.chi, pb.eps, pb.B, pb.freq_w)
+        gq.autotune()
+        gq.enable_timing(True)
+        gq.formal_solve(None)
+        qms = []
+        for _ in range(5):
+            gq.formal_solve(None)
+            qms.append(gq.stats()["sweep_ms"])
+        qms.sort()
+        extras["quadratic_path"] = {"workload": pb.name, "kernel": "sc_sweep_quad_kernel<float>",
+                                    "sweep_ms_median": qms[len(qms) // 2],
+                                    "updates_per_s": pb.cells * pb.n_angles * pb.nf / (qms[len(qms) // 2] / 1e3),
+                                    "plan": gq.sweep_plan()}
+        gq.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
     cpu = oracle_rate(p) if ws == 1 and not args.skip_cpu else None
-    per_launch_upd = p.cells * p.n_angles * p.nf
-    avg_launch_s = (sweep_ms / sweep_n) / 1e3 if sweep_n else float("nan")
-    achieved = FLOPS_PER_UPDATE * per_launch_upd / avg_launch_s / 1e12
-    clock_for_peak = 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_for_peak * 1e6 / 1e12
     lat = sorted(step_ms)
     line = {
         "metric": METRIC, "value": upd_all / t_max, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": config_dict(p, "flushed (256 MB written) before every timed step"),
+        "config": config_dict(p, "flushed (256 MB written) before every timed step; inputs 400 MB"),
         "solves_per_s": ws * args.steps / t_max,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
         "ali_iterations": iters[0] if len(set(iters)) == 1 else iters,
-        "fp64_path": fp64,
-        "gauss_seidel": gs,
-        "quadratic_path": quad,
-        "sweep_plan": g.sweep_plan(),
-        "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[g.sweep_plan()["variant"]],
-                     "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(g.sweep_plan(), p),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)",
-                     "flops_per_update": FLOPS_PER_UPDATE, "avg_launch_ms": avg_launch_s * 1e3,
-                     "launches": sweep_n},
+        "sweep_plan": plan,
+        "roofline": {"bound": "alu", "kernel": SWEEP_KERNEL_NAMES[plan["variant"]],
+                     "achieved": roof["achieved"], "peak": roof["peak"], "unit": "TFLOP/s",
+                     "frac": roof["frac"], "traffic": profiled_traffic(plan, p),
+                     "peak_source": "measured on this GPU by rt_measure_rates: the larger of its scalar "
+                                    "and packed-pair FP32 FMA rates (of measured)",
+                     "flops_per_update": FLOPS_PER_UPDATE, "avg_launch_ms": roof["avg_launch_ms"],
+                     "launches": roof["launches"], "sweep_updates_per_s": roof["updates_per_s"],
+                     "mufu_frac": roof["mufu_frac"]},
+        "measured_peaks": dict(rates, sm_count=sm_count),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "wall_s": wall1 - wall0,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -412,9 +452,9 @@ def run_profile(args):
     same workload (no warm-up loop, no baselines)."""
     import torch
     torch.cuda.set_device(0)
-    from paper_1201_2222_gb300 import build, rt
+    from paper_1201_2222_gb300 import build, rt, workloads as W
     build.build()
-    p = workload()
+    p = W.turbulent_box(128, n_mu=8, tol=TOL) if args.box128 else workload()
     g = rt.Grid.from_problem(p, prec=rt.FP64 if args.fp64 else rt.MIXED)
     if args.quadratic:
         g.set_interpolation(rt.INTERP_QUADRATIC)
@@ -441,9 +481,6 @@ def run_serve(args):
     from paper_1201_2222_gb300 import build, rt, workloads as W
     build.build()
     stream = W.serving_stream(args.serve, seed=7, rate=args.rate)
-    # bounded sample: eps clipped to >= 1e-3 (below about 6e-4 every frequency bin
-    # switches to FP64 sweeps and one 128^3 x 16-bin request takes many minutes)
-    stream = [dict(d, eps=max(d["eps"], 1e-3)) for d in stream]
     probs = [W.build_request(d) for d in stream]
     srv = rt.Server(workers=args.workers)
     t0 = time.perf_counter()
@@ -471,9 +508,9 @@ def run_serve(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "failed": int(bad), "iters_median": float(np.median(iters)), "wall_s": wall,
             "data": "synthetic", "dtype": "f32+f64",
-            "config": {"workload": "serving stream sample: sizes 32^3..128^3 and 512x512 2D, "
-                                   "1/4/16 frequencies, 24/48/80 rays, eps log-uniform in [1e-4, 1] "
-                                   "clipped to >= 1e-3"}}
+            "config": {"workload": f"serving stream sample: the first {len(ids)} requests (arrival seed 7) "
+                                   "of sizes 32^3..128^3 and 512x512 2D, 1/4/16 frequencies, 24/48/80 rays, "
+                                   "eps log-uniform in [1e-4, 1]"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -481,12 +518,14 @@ def run_serve(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU comparison solves")
     ap.add_argument("--skip-quad", action="store_true", help="omit the second-order formal-solution rate")
+    ap.add_argument("--skip-multifreq", action="store_true", help="omit the 64-bin atmosphere solve")
+    ap.add_argument("--skip-extras", action="store_true", help="omit every comparison beyond the headline")
     ap.add_argument("--skip-gs", action="store_true", help="omit the Gauss-Seidel against Jacobi comparison")
     ap.add_argument("--profile", action="store_true", help="one short solve for profilers")
     ap.add_argument("--profile-iters", type=int, default=3)
@@ -494,6 +533,7 @@ def main(argv=None):
     ap.add_argument("--quadratic", action="store_true", help="with --profile: the second-order sweep")
     ap.add_argument("--gauss-seidel", action="store_true", help="with --profile: the Gauss-Seidel iteration")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep plan")
+    ap.add_argument("--box128", action="store_true", help="with --profile: the 128^3 periodic box (80 rays)")
     ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster[,threads] instead of autotuning")
     ap.add_argument("--serve", type=int, default=0, help="run N requests of the serving stream instead")
     ap.add_argument("--rate", type=float, default=2.0, help="with --serve: arrivals per second")

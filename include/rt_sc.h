@@ -50,21 +50,35 @@ typedef enum {
  *   VACUUM:   no incoming intensity.
  *   THERMAL:  incoming intensity I = B of the adjacent boundary layer.
  *   FIXED:    incoming intensity given per angle with rt_set_boundary_intensity.
- * At every non-periodic face the ghost opacity and source function copy the
- * adjacent boundary layer. */
-typedef enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_THERMAL = 2, RT_BC_FIXED = 3 } rt_bc;
+ *   EXTERNAL: (z faces of FP64 3D grids of >= 2 planes, not combined with FIXED
+ *             x or y faces) a subdomain face of the domain decomposition of
+ *             Sec. 3.5: the ghost layer's opacity, source function and B, and the
+ *             incoming intensities (the neighbouring subdomain's, from its previous
+ *             formal solution), are set by rt_set_external_face.  Past such a face
+ *             an out-of-range non-periodic x or y face decides the ghost intensity
+ *             (thermal: the ghost layer's B), as it would in the undecomposed
+ *             domain.  Such grids sweep one cell per thread (variant 1).
+ * At every other non-periodic face the ghost opacity and source function copy
+ * the adjacent boundary layer. */
+typedef enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_THERMAL = 2, RT_BC_FIXED = 3,
+               RT_BC_EXTERNAL = 4 } rt_bc;
 
 /* Arithmetic of the formal solution.
  *   FP64:  everything in double precision.
  *   MIXED: the sweep (interpolation, segment weights, intensities, the per-sweep
- *          angle sums) in float32 with a Taylor form of the segment weights for
- *          small optical depth; J summed across sweeps, Lambda*, the ALI update,
- *          its denominator and the convergence test in double precision.  After
- *          the first formal solution of a solve the sweeps carry only the change
- *          of S (float32 rounding then scales with the update).  Frequency bins
- *          where scattering makes the problem ill-conditioned for float32 (unit
- *          roundoff / the smallest eps of optically thick cells > 1e-4) are swept
- *          in FP64 instead. */
+ *          angle sums) in float32 with a polynomial form of the segment weights
+ *          for small optical depth; J summed across sweeps, Lambda*, the ALI
+ *          update, its denominator and the convergence test in double precision.
+ *          A Jacobi ALI solve with linear interpolation does its first formal
+ *          solution in FP64 (on an internal FP64 copy of the grid, allocated by
+ *          rt_set_opacity_source unless every eps is 1) and then sweeps only the
+ *          change of S in float32, accumulating J in FP64, so that float32
+ *          rounding scales with the update, not with S.  The Jacobi update still
+ *          amplifies the increments' rounding by about 1/eps in optically thick
+ *          cells (measured: max relative error of S about 1.6e-8 / eps), so
+ *          frequency bins whose smallest eps among optically thick cells is
+ *          below 1.2e-4 (unit roundoff / eps > 5e-4) are solved in FP64 by an
+ *          internal FP64 grid of those bins (rt_get_sweep_plan reports how many). */
 typedef enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 } rt_precision;
 
 typedef struct {
@@ -207,6 +221,14 @@ rt_status rt_set_interpolation(rt_grid g, int order);
 typedef enum { RT_ITER_JACOBI = 0, RT_ITER_GAUSS_SEIDEL = 1 } rt_iteration;
 rt_status rt_set_iteration(rt_grid g, int scheme);
 
+/* Polls (about 64 ns apart) after which a wait at the Gauss-Seidel reverse
+ * phase's grid barrier gives up (default 2^22, a quarter of a second or more):
+ * every block then returns, the solve returns RT_ERR_CUDA with device error
+ * code 60 and the grid stays usable (the next solve clears the error).  No
+ * counterpart in the paper: a bound on a device-side wait, which tests set to 0
+ * to exercise the path.  Errors: RT_ERR_ARG for a negative limit. */
+rt_status rt_set_wait_limit(rt_grid g, long long polls);
+
 /* Form of the heating rate Q returned by rt_moments (Sec. 4).
  *   RT_HEAT_INTEGRAL:     Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu), chi_abs = eps chi.
  *   RT_HEAT_DIFFERENTIAL: Q = -4 pi sum_nu w_nu div H_nu, div H from centred
@@ -221,6 +243,34 @@ rt_status rt_set_iteration(rt_grid g, int scheme);
  * Errors: RT_ERR_ARG for another value. */
 typedef enum { RT_HEAT_INTEGRAL = 0, RT_HEAT_DIFFERENTIAL = 1, RT_HEAT_SWITCH = 2 } rt_heating_form;
 rt_status rt_set_heating_form(rt_grid g, int form);
+
+/* Ghost layer of a subdomain (RT_BC_EXTERNAL) z face, side 0 = low, 1 = high
+ * (Sec. 3.5): the neighbouring subdomain's opacity chi, source function S and
+ * B on its plane next to the face, [nf][ny][nx], and the intensity of every ray
+ * there from its previous formal solution, I [nf][n_angles][ny][nx] (only rays
+ * entering through the face are read).  Any pointer may be NULL (that part is
+ * kept).  A new chi recomputes Lambda*.  Errors: RT_ERR_STATE if the face is not
+ * a subdomain face. */
+rt_status rt_set_external_face(rt_grid g, int side, const double *chi, const double *S, const double *B,
+                               const double *I, int on_device, const rt_solve_opts *opts);
+
+/* The intensities the latest formal solution left on the grid's first (side 0)
+ * or last (side 1) z plane, I [nf][n_angles][ny][nx]: what the neighbouring
+ * subdomain beyond that face needs for its next formal solution.  Errors:
+ * RT_ERR_STATE if the face is not a subdomain face. */
+rt_status rt_get_face_intensity(rt_grid g, int side, double *I, int on_device, const rt_solve_opts *opts);
+
+/* A Jacobi ALI solve (Eq. 24) taken one step at a time, for callers that
+ * coordinate several grids (the subdomains of a domain decomposition) between
+ * iterations.  rt_ali_begin starts it (S = S_init, or B when NULL; periodic
+ * ghosts from S) with no stopping rule of its own; rt_ali_iterate performs n
+ * iterations (formal solution of the current S, update) and returns the
+ * iterations since rt_ali_begin and the max relative change of the last one
+ * (Eq. 25; of J when every eps = 1).  Jacobi iteration only.  Errors:
+ * RT_ERR_STATE before rt_set_opacity_source, for a Gauss-Seidel grid, or when
+ * another solve or formal solution has run since rt_ali_begin. */
+rt_status rt_ali_begin(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts);
+rt_status rt_ali_iterate(rt_grid g, int n, const rt_solve_opts *opts, int *iters_out, double *resid_out);
 
 /* Current source function S [nf][nz][ny][nx]. */
 rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts);
@@ -241,6 +291,8 @@ typedef struct {
   long long kernel_launches;
   long long updates;       /* cell * ray * frequency updates performed */
   long long graph_launches; /* ALI batches replayed as CUDA graphs (cumulative) */
+  int first_fp64;           /* 1 if the latest ALI solve (mixed grid) did its first formal
+                               solution in FP64 (see RT_PREC_MIXED) */
 } rt_stats;
 rt_status rt_enable_timing(rt_grid g, int enable);
 rt_status rt_get_stats(rt_grid g, rt_stats *out);
@@ -262,8 +314,7 @@ rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas,
 /* The sweep plan in use (7 ints): plan[0] variant, [1] groups per frequency,
  * [2] rays per group (max), [3] strips per plane (cluster size), [4] threads per
  * CTA, [5] dynamic shared memory bytes per CTA, [6] frequency bins a mixed grid
- * sweeps in FP64 because the float32 error bound (unit roundoff / the smallest
- * eps of optically thick cells) exceeds 1e-4 there. */
+ * solves in FP64 (see RT_PREC_MIXED). */
 rt_status rt_get_sweep_plan(rt_grid g, int *plan);
 
 /* Time candidate sweep configurations (variant x rays per group x strips) with
@@ -294,7 +345,8 @@ rt_status rt_autotune(rt_grid g, int *plan_out);
  *     any device work; so do fixed-intensity faces.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (device current): make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process, so
+ *     the entry point must not be called on a device after cudaDeviceReset.
  *   - Every call shares the array and it keeps the previous call's contents
  *     (only its control block is cleared): calls that overlap on the GPU, from
  *     several streams or threads, race and must be serialised by the caller. */
@@ -354,6 +406,18 @@ rt_status rt_wait(rt_server s, long long id, double timeout_s, rt_request_info *
  * J and S [nf][cells], Q [cells] (the integral form), and forgets the request.
  * Returns the solve's status (RT_ERR_STATE if it is not done). */
 rt_status rt_fetch(rt_server s, long long id, double *J, double *S, double *Q);
+
+/* Measured arithmetic rates of the current device (no counterpart in the paper:
+ * the ceilings the formal solution's roofline is reported against).  Writes
+ * min(n, 5) values: [0] FP32 flop/s of scalar fused multiply-adds, [1] FP32
+ * flop/s of packed-pair fused multiply-adds (fma.rn.f32x2), [2] special-function
+ * exponentials/s (ex2.approx), [3] special-function reciprocals/s (rcp.approx),
+ * [4] FP64 flop/s of fused multiply-adds.  Each is the best of three timed
+ * launches of a probe kernel (8 blocks of 256 threads per SM, 8 independent
+ * chains per thread) after a warm-up launch; the whole call takes well under a
+ * second.  Allocates (and frees) one small device buffer and synchronises the
+ * device.  Errors: RT_ERR_ARG (NULL or n < 1), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_measure_rates(double *rates, int n);
 
 /* Message describing the last error on this thread (never NULL). */
 const char *rt_last_error(void);

@@ -229,6 +229,7 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
             _ptr(G_next), _ptr(J), _ptr(L), _ptr(H), _ptr(K),
             int(nthreads))
     Izlo = Izhi = None
+    faces_out = ext is not None
     if S_ghost is not None and ext is None:
         ext = {}
     if ext is not None:
@@ -250,7 +251,7 @@ def formal_solution(grid: Grid, chi, S, B, G_prev=None, I_fixed=None, moments=Fa
     if rc != 0:
         raise RuntimeError(f"oracle formal solution failed ({rc})")
     out = dict(J=J.reshape(grid.shape), lstar=L.reshape(grid.shape), G_next=G_next)
-    if ext:
+    if faces_out:
         out["I_zlo"] = Izlo.reshape(na, grid.n[1], grid.n[0])
         out["I_zhi"] = Izhi.reshape(na, grid.n[1], grid.n[0])
     if moments:

@@ -302,16 +302,31 @@ struct rt_grid_s {
   rt_stats stats{};
   long long launches = 0;
 
-  // Mixed grids: frequency bins whose float32 error bound (unit roundoff over the
-  // smallest eps of optically thick cells) exceeds prec_limit are solved by an
-  // internal FP64 grid and masked out of this grid's ALI update.
+  // Mixed grids do the first formal solution of each Jacobi ALI solve in FP64,
+  // on this internal FP64 grid of every bin (the shadow: same medium, no Lambda*
+  // of its own); the later sweeps carry increments, whose float32 rounding
+  // scales with the update, and J is accumulated in FP64
+  rt_grid first64 = nullptr;
+  bool fp64_first = false;
+  bool shadow = false;                // this grid is another grid's FP64 first-solution shadow
+  bool stepped = false;               // an ALI solve begun by rt_ali_begin may be continued
+  // Mixed grids: frequency bins too ill-conditioned for float32 even as
+  // increments after an FP64 first formal solution (unit roundoff over the
+  // smallest eps of optically thick cells above bin_limit) are solved by an
+  // internal FP64 grid of those bins and masked out of this grid's ALI update
   rt_grid sub64 = nullptr;
   std::vector<int> bins64;
   unsigned char *fmask = nullptr;
   unsigned long long *epsmin = nullptr;
   double *tmp2 = nullptr;
   size_t tmp2_n = 0;
-  double prec_limit = 1e-4;
+  double bin_limit = 5e-4;
+  // Subdomain (RT_BC_EXTERNAL) z faces, FP64 grids, side 0 = low, 1 = high: the
+  // ghost layers set by rt_set_external_face (chi, S, B [nf][ny][nx], every ray's
+  // lagged intensity [nf][na][ny][nx]) and the intensities the sweeps leave on
+  // the first / last z plane for the neighbours [nf][na][ny][nx]
+  double *xchi[2] = {nullptr, nullptr}, *xS[2] = {nullptr, nullptr}, *xB[2] = {nullptr, nullptr};
+  double *xI[2] = {nullptr, nullptr}, *xout[2] = {nullptr, nullptr};
   int heat_form = RT_HEAT_INTEGRAL;   // form of Q returned by rt_moments (Sec. 4)
   int interp = RT_INTERP_LINEAR;      // order of the face interpolation (Sec. 3.3)
   void *Opart = nullptr;              // second-order sweeps: group partials of 1 - Lambda*
@@ -328,6 +343,7 @@ struct rt_grid_s {
   unsigned *gs_bar = nullptr;
   int *gs_list = nullptr;             // forward groups, then forward rays with mu_V < 0
   size_t gs_list_n = 0;
+  long long gs_polls = 1LL << 22;     // polls of a reverse-phase barrier wait before it gives up
   double *gs_acc = nullptr;           // incremental solves: J of the forward and of the reverse
                                       // rays [2][nf][cells]
 
@@ -689,7 +705,7 @@ template <typename T>
 rt_status fill_bc(rt_grid g, int face, cudaStream_t s) {
   const int ax = face / 2, side = face % 2;
   const int bc = side ? g->desc.bc_hi[ax] : g->desc.bc_lo[ax];
-  if (g->d.periodic[ax]) return RT_OK;
+  if (g->d.periodic[ax] || bc == RT_BC_EXTERNAL) return RT_OK;
   CU(rtk::launch_fill_bc<T>(g->d, g->na, face, bc, g->B, g->user_bc[face], (T *)g->Ibc[face], s));
   g->launches++;
   return RT_OK;
@@ -703,7 +719,7 @@ rt_status fill_bc_any(rt_grid g, int face, cudaStream_t s) {
 rt_status check_device_error(rt_grid g) {
   rtk::SolveState hs{};
   CU(cudaMemcpy(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost));
-  if (hs.err) return fail(RT_ERR_CUDA, "device bounds check failed (code %d, index %d)", hs.err, hs.err_info);
+  if (hs.err) return fail(RT_ERR_CUDA, "device check failed (code %d, index %d)", hs.err, hs.err_info);
   return RT_OK;
 }
 
@@ -738,6 +754,14 @@ rtk::SweepArgs<T> sweep_args(rt_grid g) {
   const size_t half = g->wt_bytes / 2;
   A.WE = wt ? (const T *)g->wt : nullptr;
   A.WP = wt ? (const T *)((const char *)g->wt + half) : nullptr;
+  for (int side = 0; side < 2; ++side) {   // subdomain z faces (FP64 grids only)
+    A.ext[side] = g->xI[side] != nullptr;
+    A.xchi[side] = (const T *)g->xchi[side];
+    A.xS[side] = (const T *)g->xS[side];
+    A.xB[side] = (const T *)g->xB[side];
+    A.xI[side] = (const T *)g->xI[side];
+    A.xout[side] = (T *)g->xout[side];
+  }
   return A;
 }
 
@@ -915,6 +939,7 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   G.SPV = (T *)g->SP[V];
   G.Ir = (T *)g->gsIr;
   G.fmask = g->fmask;
+  G.poll_limit = g->gs_polls;
   G.bar = g->gs_bar;
   return RT_OK;
 }
@@ -948,6 +973,14 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     A.gs_axis = GA.V;
     GA.A = A;
   }
+  // the float32 pipelined sweep writes the partials of the groups sweeping along
+  // x (the first groups) in their plane layout, which the Jacobi update reads
+  int nxg = 0;
+  if (sizeof(T) == 4 && !gs && g->variant == 3 && g->interp == RT_INTERP_LINEAR && g->d.n[0] % 4 == 0 &&
+      g->d.n[1] % 4 == 0) {
+    while (nxg < (int)g->groups.size() && g->groups[nxg].axis == 0) ++nxg;
+    A.jx = 1;
+  }
   rtk::AliArgs<T> L{};
   L.d = g->d;
   L.ngroups_per_f = (int)g->groups.size();
@@ -965,6 +998,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   L.lte = g->lte ? 1 : 0;
   L.incremental = incremental;
   L.fmask = g->fmask;
+  L.nxg = nxg;
   std::vector<EventPair> ev;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (g->timing) {
@@ -973,6 +1007,28 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     CU(cudaEventRecord(t0, s));
   }
   int enqueued = 0, batch = opts && opts->check_every > 0 ? opts->check_every : 4;
+  g->stats.first_fp64 = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (g->fp64_first && g->first64 && incremental && !gs && !g->lte && max_iter > 0) {
+      // The first formal solution in FP64 (the internal FP64 grid, from the same S
+      // and first-iteration ghosts) into J64, its outflow ghosts and their change
+      // into this grid's ghost buffers, then the first update with that J
+      rt_solve_opts o2{};
+      o2.stream = (void *)s;
+      rt_status r = rt_formal_solve(g->first64, g->S, g->J, nullptr, 1, &o2);
+      if (r != RT_OK) return r;
+      const long long ng = (long long)g->d.nf * g->na * g->d.gsize;
+      CU(rtk::launch_ghosts_from64(ng, (const double *)g->first64->G[1], (const double *)g->first64->G[0],
+                                   (float *)g->G[1], (float *)g->Gd[1], s));
+      rtk::AliArgs<T> L0 = L;
+      L0.Jpart = nullptr;
+      CU(rtk::launch_ali<T>(L0, s));
+      CU(rtk::launch_finish(g->st, s));
+      g->launches += 3;
+      enqueued = 1;
+      g->stats.first_fp64 = 1;
+    }
+  }
   rtk::SolveState hs{};
   // the launches of m iterations (every later kernel of a batch does nothing
   // once the solve has converged)
@@ -1029,19 +1085,19 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   };
   while (true) {
     const int m = std::min(batch, max_iter - enqueued);
-    const rt_grid_s::Graph *gr = (enqueued > 0 && !g->timing && g->graphs_ok) ? graph_for(m) : nullptr;
+    const rt_grid_s::Graph *gr = (m > 0 && enqueued > 0 && !g->timing && g->graphs_ok) ? graph_for(m) : nullptr;
     if (gr) {
       CU(cudaGraphLaunch(gr->exec, s));
       g->launches += gr->nlaunch;
       g->graph_launches++;
-    } else {
+    } else if (m > 0) {
       rt_status r = enqueue_batch(m);
       if (r != RT_OK) return r;
     }
     enqueued += m;
     CU(cudaMemcpyAsync(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (hs.err) return fail(RT_ERR_CUDA, "device bounds check failed (code %d, index %d)", hs.err, hs.err_info);
+    if (hs.err) return fail(RT_ERR_CUDA, "device check failed (code %d, index %d)", hs.err, hs.err_info);
     if (hs.done || enqueued >= max_iter) break;
     if (!(opts && opts->check_every > 0)) batch = std::min(batch * 2, 64);
   }
@@ -1053,7 +1109,8 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     g->stats.total_ms = tt;
-    rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches, (size_t)hs.iter);
+    rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches,
+                                 (size_t)std::max(0, hs.iter - g->stats.first_fp64));
     if (r != RT_OK) return r;
   }
   *iters = hs.iter;
@@ -1063,6 +1120,51 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   g->last_fs_from_Sfs = !g->lte;
   // (Gauss-Seidel: the J returned is that of a formal solution of Sfs)
   g->last_incremental = incremental != 0 && !gs;
+  g->sp_is_delta = incremental != 0;
+  return RT_OK;
+}
+
+// n Jacobi iterations continuing the solve begun by rt_ali_begin: the sweep
+// (incremental on mixed grids after the first), the update, the decision kernel
+// (whose stopping rule rt_ali_begin disabled); then the solve state is read.
+template <typename T>
+rt_status ali_iterate(rt_grid g, int n, cudaStream_t s, int *iters, double *resid) {
+  const int incremental = (g->desc.prec == RT_PREC_MIXED && g->interp == RT_INTERP_LINEAR) ? 1 : 0;
+  rt_status r = ensure_seg_table<T>(g, s);
+  if (r != RT_OK) return r;
+  rtk::SweepArgs<T> A = sweep_args<T>(g);
+  A.incremental = incremental;
+  rtk::AliArgs<T> L{};
+  L.d = g->d;
+  L.ngroups_per_f = (int)g->groups.size();
+  L.Jpart = (const T *)g->Jpart;
+  L.eps = g->eps;
+  L.B = g->B;
+  L.iden = g->iden;
+  L.Opart = g->interp == RT_INTERP_QUADRATIC ? (const T *)g->Opart : nullptr;
+  L.S64 = g->S;
+  L.Sfs = g->Sfs;
+  L.J64 = g->J;
+  L.Jprev = g->Jprev;
+  for (int a = 0; a < 3; ++a) L.SP[a] = g->used_axis[a] ? (T *)g->SP[a] : nullptr;
+  L.st = g->st;
+  L.lte = g->lte ? 1 : 0;
+  L.incremental = incremental;
+  for (int i = 0; i < n; ++i) {
+    if ((r = enqueue_sweep<T>(g, A, false, s, nullptr)) != RT_OK) return r;
+    CU(rtk::launch_ali<T>(L, s));
+    CU(rtk::launch_finish(g->st, s));
+    g->launches += 2;
+  }
+  rtk::SolveState hs{};
+  CU(cudaMemcpyAsync(&hs, g->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (hs.err) return fail(RT_ERR_CUDA, "device check failed (code %d, index %d)", hs.err, hs.err_info);
+  if (iters) *iters = hs.iter;
+  if (resid) *resid = hs.last_resid;
+  g->fs_total = hs.fs_count;
+  g->last_fs_from_Sfs = !g->lte;
+  g->last_incremental = incremental != 0;
   g->sp_is_delta = incremental != 0;
   return RT_OK;
 }
@@ -1148,7 +1250,7 @@ rt_status sync_sub_bc(rt_grid g, int face) {
 }
 
 // Decide which bins of a mixed grid need FP64 sweeps and (re)build the FP64 grid.
-rt_status plan_precision(rt_grid g) {
+rt_status plan_bins(rt_grid g) {
   const int nf = g->d.nf;
   cudaStream_t s = g->own;
   if (!g->epsmin) CU(cudaMalloc((void **)&g->epsmin, nf * sizeof(unsigned long long)));
@@ -1164,7 +1266,7 @@ rt_status plan_precision(rt_grid g) {
   for (int f = 0; f < nf; ++f) {
     double e;
     std::memcpy(&e, &bits[f], 8);
-    if (u32 / e > g->prec_limit) ill.push_back(f);
+    if (u32 / e > g->bin_limit) ill.push_back(f);
   }
   if (ill.empty()) {
     if (g->sub64) rt_destroy_grid(g->sub64);
@@ -1205,6 +1307,42 @@ rt_status plan_precision(rt_grid g) {
   return RT_OK;
 }
 
+// Mixed grids: the internal FP64 grid that does the first formal solution of
+// each Jacobi ALI solve with linear interpolation (not needed when every eps = 1,
+// whose solves only iterate the boundary ghosts).
+rt_status plan_first64(rt_grid g) {
+  g->fp64_first = !g->lte;
+  if (!g->fp64_first) {
+    if (g->first64) rt_destroy_grid(g->first64);
+  if (g->sub64) rt_destroy_grid(g->sub64);
+  if (g->fmask) cudaFree(g->fmask);
+  if (g->epsmin) cudaFree(g->epsmin);
+  if (g->tmp2) cudaFree(g->tmp2);
+    g->first64 = nullptr;
+    return RT_OK;
+  }
+  if (!g->first64) {
+    rt_grid_desc d = g->desc;
+    d.prec = RT_PREC_FP64;
+    rt_status r = rt_create_grid(&d, &g->first64);
+    if (r != RT_OK) return r;
+    g->first64->shadow = true;
+    g->first64->wt_off = true;   // one formal solution per solve: no segment-weight table
+  }
+  rt_status r = rt_set_opacity_source(g->first64, g->chi, g->eps, g->B, g->fw, 1);
+  if (r != RT_OK) return r;
+  for (int face = 0; face < 6; ++face) {
+    if (!g->user_bc[face]) continue;
+    rt_grid h = g->first64;
+    const size_t n = (size_t)g->d.nf * g->na * g->d.face[face / 2];
+    if (!h->user_bc[face]) CU(cudaMalloc((void **)&h->user_bc[face], n * 8));
+    CU(cudaMemcpy(h->user_bc[face], g->user_bc[face], n * 8, cudaMemcpyDeviceToDevice));
+    if ((r = fill_bc_any(h, face, h->own)) != RT_OK) return r;
+  }
+  CU(cudaStreamSynchronize(g->first64->own));
+  return RT_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
@@ -1223,11 +1361,20 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
     return fail(RT_ERR_ARG, "cell spacings must be > 0");
   if (D.prec != RT_PREC_FP64 && D.prec != RT_PREC_MIXED) return fail(RT_ERR_ARG, "bad precision");
   for (int a = 0; a < 3; ++a) {
-    if (D.bc_lo[a] < 0 || D.bc_lo[a] > 3 || D.bc_hi[a] < 0 || D.bc_hi[a] > 3)
+    const int lim = a == 2 ? RT_BC_EXTERNAL : RT_BC_FIXED;
+    if (D.bc_lo[a] < 0 || D.bc_lo[a] > lim || D.bc_hi[a] < 0 || D.bc_hi[a] > lim)
       return fail(RT_ERR_ARG, "bad boundary type on axis %d", a);
     if (a < 2 || D.nz > 1)
       if ((D.bc_lo[a] == RT_BC_PERIODIC) != (D.bc_hi[a] == RT_BC_PERIODIC))
         return fail(RT_ERR_ARG, "axis %d: a periodic axis must be periodic on both faces", a);
+  }
+  const bool ext = D.bc_lo[2] == RT_BC_EXTERNAL || D.bc_hi[2] == RT_BC_EXTERNAL;
+  if (ext) {
+    if (D.nz < 2 || D.prec != RT_PREC_FP64)
+      return fail(RT_ERR_ARG, "subdomain (external) z faces need an FP64 3D grid of >= 2 planes");
+    for (int a = 0; a < 2; ++a)
+      if (D.bc_lo[a] == RT_BC_FIXED || D.bc_hi[a] == RT_BC_FIXED)
+        return fail(RT_ERR_ARG, "subdomain z faces do not combine with fixed x or y faces");
   }
   rt_grid g = new rt_grid_s();
   g->desc = D;
@@ -1298,8 +1445,22 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
     ALLOC(g->Gd[1], gbytes);
   }
   for (int f = 0; f < 6; ++f) {
-    if (d.periodic[f / 2]) continue;
+    if (d.periodic[f / 2] || (f % 2 ? D.bc_hi[f / 2] : D.bc_lo[f / 2]) == RT_BC_EXTERNAL) continue;
     ALLOC(g->Ibc[f], (size_t)d.nf * g->na * d.face[f / 2] * ts);
+  }
+  for (int side = 0; side < 2; ++side) {
+    if ((side ? D.bc_hi[2] : D.bc_lo[2]) != RT_BC_EXTERNAL) continue;
+    const size_t lay = (size_t)d.nf * d.face[2] * 8, ray = lay * g->na;
+    ALLOC(g->xchi[side], lay);
+    ALLOC(g->xS[side], lay);
+    ALLOC(g->xB[side], lay);
+    ALLOC(g->xI[side], ray);
+    ALLOC(g->xout[side], ray);
+    if (cudaMemset(g->xchi[side], 0, lay) != cudaSuccess || cudaMemset(g->xS[side], 0, lay) != cudaSuccess ||
+        cudaMemset(g->xB[side], 0, lay) != cudaSuccess || cudaMemset(g->xI[side], 0, ray) != cudaSuccess ||
+        cudaMemset(g->xout[side], 0, ray) != cudaSuccess)
+      return cleanup(fail(RT_ERR_CUDA, "initialisation of the subdomain face buffers failed"));
+    g->wt_off = true;   // the segment-weight table does not see the ghost layer's chi
   }
   ALLOC(g->rays_d, (size_t)g->na * sizeof(RayGeom));
   ALLOC(g->st, sizeof(rtk::SolveState));
@@ -1322,10 +1483,7 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
 rt_status rt_destroy_grid(rt_grid g) {
   if (!g) return RT_OK;
   if (g->own) cudaStreamSynchronize(g->own);
-  if (g->sub64) rt_destroy_grid(g->sub64);
-  if (g->fmask) cudaFree(g->fmask);
-  if (g->epsmin) cudaFree(g->epsmin);
-  if (g->tmp2) cudaFree(g->tmp2);
+  if (g->first64) rt_destroy_grid(g->first64);
   void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml, g->iden,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
                   g->Gd[0], g->Gd[1],
@@ -1335,6 +1493,9 @@ rt_status rt_destroy_grid(rt_grid g) {
                   g->gsw, g->gsIr, g->gs_bar, g->gs_list, g->gs_acc, g->wt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (int side = 0; side < 2; ++side)
+    for (double *p : {g->xchi[side], g->xS[side], g->xB[side], g->xI[side], g->xout[side]})
+      if (p) cudaFree(p);
   for (auto &e : g->graphs) cudaGraphExecDestroy(e.exec);
   if (g->own) cudaStreamDestroy(g->own);
   delete g;
@@ -1387,6 +1548,8 @@ rt_status rt_set_sweep_config(rt_grid g, int angles_per_group, int cluster_ctas,
   if (angles_per_group < 0 || angles_per_group > 8 || cluster_ctas < 0 || cluster_ctas > 16 ||
       threads < 0 || threads > 512 || (threads % 32) || variant < 0 || variant > 3)
     return fail(RT_ERR_ARG, "bad sweep configuration");
+  if ((g->xI[0] || g->xI[1]) && variant > 1)
+    return fail(RT_ERR_ARG, "a grid with subdomain z faces sweeps one cell per thread (variant 1)");
   cudaStreamSynchronize(g->own);
   g->req_apg = angles_per_group;
   g->req_cluster = cluster_ctas;
@@ -1414,34 +1577,44 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
     CU(cudaMemcpyAsync(g->fw, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
   }
-  CU(cudaMemsetAsync(g->counts, 0, 2 * sizeof(int), s));
-  CU(rtk::launch_validate((long long)N, g->chi, g->eps, g->B, g->counts, s));
-  int counts[2] = {0, 0};
-  CU(cudaMemcpyAsync(counts, g->counts, sizeof counts, cudaMemcpyDeviceToHost, s));
-  CU(cudaStreamSynchronize(s));
-  g->launches++;
-  if (counts[0]) {
-    g->have_medium = false;
-    return fail(RT_ERR_ARG, "%d input values violate chi >= 0, 0 < eps <= 1, B >= 0 or are not finite", counts[0]);
-  }
-  g->lte = counts[1] == 0;
-  if ((r = permute_any(g, g->chi, g->chiP, s)) != RT_OK) return r;
-  if (g->desc.prec == RT_PREC_FP64) {
-    CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+  if (g->shadow) {
+    // another grid's FP64 first-solution shadow: that grid validated the medium
+    // and owns Lambda*; only the formal solution's inputs are needed here
+    g->lte = false;
   } else {
-    CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+    CU(cudaMemsetAsync(g->counts, 0, 2 * sizeof(int), s));
+    CU(rtk::launch_validate((long long)N, g->chi, g->eps, g->B, g->counts, s));
+    int counts[2] = {0, 0};
+    CU(cudaMemcpyAsync(counts, g->counts, sizeof counts, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    g->launches++;
+    if (counts[0]) {
+      g->have_medium = false;
+      return fail(RT_ERR_ARG, "%d input values violate chi >= 0, 0 < eps <= 1, B >= 0 or are not finite",
+                  counts[0]);
+    }
+    g->lte = counts[1] == 0;
   }
-  CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
-  g->launches += 2;
+  if ((r = permute_any(g, g->chi, g->chiP, s)) != RT_OK) return r;
+  if (!g->shadow) {
+    if (g->desc.prec == RT_PREC_FP64) {
+      CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
+    } else {
+      CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
+    }
+    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
+    g->launches += 2;
+  }
   CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
   if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
   if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
   for (int f = 0; f < 6; ++f)
     if ((r = fill_bc_any(g, f, s)) != RT_OK) return r;
-  if (g->desc.prec == RT_PREC_MIXED && (r = plan_precision(g)) != RT_OK) return r;
+  if (g->desc.prec == RT_PREC_MIXED && ((r = plan_first64(g)) != RT_OK || (r = plan_bins(g)) != RT_OK)) return r;
   g->gs_ready = false;
   g->gen++;
   g->have_medium = true;
+  g->stepped = false;
   return RT_OK;
 }
 
@@ -1459,12 +1632,14 @@ rt_status rt_set_boundary_intensity(rt_grid g, int face, const double *I) {
   rt_status r = fill_bc_any(g, face, g->own);
   if (r != RT_OK) return r;
   CU(cudaStreamSynchronize(g->own));
+  if (g->first64 && (r = rt_set_boundary_intensity(g->first64, face, I)) != RT_OK) return r;
   return sync_sub_bc(g, face);
 }
 
 rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lstar_out, int on_device,
                           const rt_solve_opts *opts) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  g->stepped = false;
   if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
   cudaStream_t s = pick_stream(g, opts);
   if (s != g->own) {   // order after the grid's own stream (set-up work)
@@ -1514,6 +1689,7 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
 rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
                        int *iters_out, double *resid_out) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  g->stepped = false;
   if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
   if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
   cudaStream_t s = pick_stream(g, opts);
@@ -1622,6 +1798,77 @@ rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, doub
   return check_device_error(g);
 }
 
+rt_status rt_set_external_face(rt_grid g, int side, const double *chi, const double *S, const double *B,
+                               const double *I, int on_device, const rt_solve_opts *opts) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (side < 0 || side > 1 || !g->xI[side]) return fail(RT_ERR_STATE, "z face %d is not a subdomain face", side);
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  const size_t lay = (size_t)g->d.nf * g->d.face[2];
+  rt_status r;
+  if (chi && (r = copy_in(g, g->xchi[side], chi, lay, on_device, s)) != RT_OK) return r;
+  if (S && (r = copy_in(g, g->xS[side], S, lay, on_device, s)) != RT_OK) return r;
+  if (B && (r = copy_in(g, g->xB[side], B, lay, on_device, s)) != RT_OK) return r;
+  if (I && (r = copy_in(g, g->xI[side], I, lay * g->na, on_device, s)) != RT_OK) return r;
+  if (chi && g->have_medium) {   // Lambda* sees the ghost layer's chi
+    CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
+    CU(rtk::launch_inv_denominator((long long)N_of(g), g->eps, g->oml, g->iden, s));
+    g->launches += 2;
+  }
+  if (!on_device || !opts || !opts->stream) CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_get_face_intensity(rt_grid g, int side, double *I, int on_device, const rt_solve_opts *opts) {
+  if (!g || !I) return fail(RT_ERR_ARG, "NULL argument");
+  if (side < 0 || side > 1 || !g->xout[side]) return fail(RT_ERR_STATE, "z face %d is not a subdomain face", side);
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  rt_status r = copy_out(I, g->xout[side], (size_t)g->d.nf * g->na * g->d.face[2], on_device, s);
+  if (r != RT_OK) return r;
+  CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_ali_begin(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  if (g->iteration != RT_ITER_JACOBI) return fail(RT_ERR_STATE, "stepped ALI solves take the Jacobi iteration");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  const size_t N = (size_t)N_of(g);
+  rt_status r;
+  if (S_init) {
+    if ((r = copy_in(g, g->S, S_init, N, on_device, s)) != RT_OK) return r;
+  } else {
+    CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
+  if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
+  // no stopping rule of its own: the caller decides after each rt_ali_iterate
+  CU(rtk::launch_state_op(g->st, 0, std::numeric_limits<int>::max(), -1.0, g->lte ? 1 : 0, s));
+  g->launches++;
+  g->stepped = true;
+  CU(cudaStreamSynchronize(s));
+  return RT_OK;
+}
+
+rt_status rt_ali_iterate(rt_grid g, int n, const rt_solve_opts *opts, int *iters_out, double *resid_out) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!g->stepped) return fail(RT_ERR_STATE, "rt_ali_begin has not been called since the medium was set");
+  if (n < 1) return fail(RT_ERR_ARG, "n must be >= 1");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  rt_status r = g->desc.prec == RT_PREC_FP64 ? ali_iterate<double>(g, n, s, iters_out, resid_out)
+                                             : ali_iterate<float>(g, n, s, iters_out, resid_out);
+  if (r != RT_OK) return r;
+  g->stats.iters = iters_out ? *iters_out : 0;
+  g->stats.resid = resid_out ? *resid_out : 0.0;
+  g->stats.updates = (long long)g->d.cells * g->na * g->d.nf * n;
+  g->stats.kernel_launches = g->launches;
+  return RT_OK;
+}
+
 rt_status rt_get_S(rt_grid g, double *S, int on_device, const rt_solve_opts *opts) {
   if (!g || !S) return fail(RT_ERR_ARG, "NULL argument");
   cudaStream_t s = pick_stream(g, opts);
@@ -1673,9 +1920,9 @@ rt_status rt_set_iteration(rt_grid g, int scheme) {
   if (g->have_medium) {
     if ((r = permute_any(g, g->chi, g->chiP, s)) != RT_OK) return r;
     if (g->desc.prec == RT_PREC_FP64) {
-      CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+      CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
     } else {
-      CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, s));
+      CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
     }
     CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
     g->launches += 2;
@@ -1686,6 +1933,14 @@ rt_status rt_set_iteration(rt_grid g, int scheme) {
   }
   CU(cudaStreamSynchronize(s));
   if (g->sub64) return rt_set_iteration(g->sub64, scheme);
+  return RT_OK;
+}
+
+rt_status rt_set_wait_limit(rt_grid g, long long polls) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (polls < 0) return fail(RT_ERR_ARG, "the poll limit must be >= 0");
+  g->gs_polls = polls;
+  g->gen++;   // captured batches hold the old limit
   return RT_OK;
 }
 
@@ -1751,6 +2006,7 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
       rtk::plane_axes(a, cax);
       minNv = std::min(minNv, g->d.n[cax[1]]);
     }
+    const bool ext = g->xI[0] || g->xI[1];
     const int variants[3] = {3, 2, 1};
     const int apgs[7] = {2, 3, 4, 5, 6, 7, 8};
     const int clusters[9] = {1, 2, 4, 6, 8, 9, 10, 12, 16};
@@ -1758,8 +2014,9 @@ rt_status rt_autotune(rt_grid g, int *plan_out) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best_ms = 1e300;
-    const int nvar = g->interp == RT_INTERP_QUADRATIC ? 1 : 3;   // second order: pipelined only
-    for (int vi = 0; vi < nvar; ++vi) {
+    // second order: pipelined only; subdomain faces: one cell per thread only
+    const int nvar = g->interp == RT_INTERP_QUADRATIC ? 1 : 3;
+    for (int vi = ext ? 2 : 0; vi < nvar; ++vi) {
       for (int ai = 0; ai < 7; ++ai) {
         for (int ci = 0; ci < 9; ++ci) {
           if (clusters[ci] > minNv) continue;

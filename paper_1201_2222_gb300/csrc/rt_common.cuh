@@ -17,7 +17,7 @@
 
 namespace rtk {
 
-enum { BC_PERIODIC = 0, BC_VACUUM = 1, BC_THERMAL = 2, BC_FIXED = 3 };
+enum { BC_PERIODIC = 0, BC_VACUUM = 1, BC_THERMAL = 2, BC_FIXED = 3, BC_EXTERNAL = 4 };
 
 constexpr int kMaxGroups = 512;
 

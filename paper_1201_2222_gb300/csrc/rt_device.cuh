@@ -58,9 +58,22 @@ __device__ __forceinline__ const T *ghost_ptr(const SweepArgs<T> &A, const int c
   const int m1 = !o1 ? c1 : (p1 ? (c1 < 0 ? c1 + n1 : c1 - n1) : (c1 < 0 ? 0 : n1 - 1));
   const int m2 = !o2 ? c2 : (p2 ? (c2 < 0 ? c2 + n2 : c2 - n2) : (c2 < 0 ? 0 : n2 - 1));
   int fax = -1, fside = 0;   // first non-periodic out-of-range axis in the order z, y, x
+  // a vertex past a subdomain (EXTERNAL) z face lies inside the undecomposed
+  // domain's z range: there an out-of-range bounded x or y face decides (thermal:
+  // B of the ghost layer), else the neighbour's lagged intensity
+  const int xs = (o2 && !p2 && A.ext[c2 < 0 ? 0 : 1]) ? (c2 < 0 ? 0 : 1) : -1;
   if (o0 && !p0) { fax = 0; fside = c0 >= n0; }
   if (o1 && !p1) { fax = 1; fside = c1 >= n1; }
-  if (o2 && !p2) { fax = 2; fside = c2 >= n2; }
+  if (o2 && !p2 && xs < 0) { fax = 2; fside = c2 >= n2; }
+  if (xs >= 0) {
+    const long long f2 = (long long)n0 * n1, fc = (long long)m1 * n0 + m0;
+    if (fax >= 0) {
+      if (inc || (fside ? A.d.bc_hi[fax] : A.d.bc_lo[fax]) != BC_THERMAL) return nullptr;
+      return A.xB[xs] + RT_IDX((long long)f * f2 + fc, (long long)A.d.nf * f2, 61);
+    }
+    if (inc) return nullptr;
+    return A.xI[xs] + RT_IDX(((long long)f * A.na + angle) * f2 + fc, (long long)A.d.nf * A.na * f2, 62);
+  }
   if (fax >= 0) {
     if (inc) return nullptr;
     // face cell index: x face [z][y], y face [z][x], z face [y][x]
@@ -165,6 +178,68 @@ __device__ __forceinline__ void seg_weights(double dtau, double &E, double &psi0
 }
 
 constexpr int kPipeX0 = 4;   // first interior column of a staged row (16-byte aligned)
+
+// ------------------------------------------------- shared memory by 32-bit address
+// Loads and stores with the shared state space spelled out, so that address
+// arithmetic stays 32-bit and no access goes through generic addressing.
+__device__ __forceinline__ float4 lds128(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+// v = shared word at a where `take` is non-zero (only those lanes access memory)
+__device__ __forceinline__ void lds32_if(float &v, unsigned a, unsigned take) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.shared.f32 %0, [%1];\n}"
+               : "+f"(v)
+               : "r"(a), "r"(take)
+               : "memory");
+}
+__device__ __forceinline__ void sts128(unsigned a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+// address of the same shared-memory offset in cluster CTA `rank`
+__device__ __forceinline__ unsigned mapa_rank(unsigned a, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void stc128(unsigned a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
+// Division by a divisor fixed for a kernel's lifetime, by one high multiply, an
+// add and a shift (Granlund & Montgomery 1994): for 0 <= n < 2^31 and d >= 1,
+// n / d = (umulhi(n, m) + n) >> l with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1.
+struct FastDiv {
+  unsigned m, l, d;
+  __host__ __device__ FastDiv() : m(1), l(0), d(1) {}
+  __host__ __device__ explicit FastDiv(unsigned dv) : d(dv) {
+    l = 0;
+    while ((1u << l) < dv) ++l;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - dv)) / dv + 1);
+  }
+  __device__ __forceinline__ int div(int n) const { return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l); }
+};
+
+// ------------------------------------------------ special-function approximations
+// 2^x and 1/x by the special-function unit (flush-to-zero; about 2 ulp).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // A compile-time sign of mu_u or mu_v (selects the interpolation stencil).
 template <int V>

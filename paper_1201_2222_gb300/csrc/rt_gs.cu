@@ -50,9 +50,10 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
 // has made it.  Arrivals are counted in two levels (blocks in groups of
 // kGsBarGroup on their own counters, bar[1 + group]; the last block of a group
 // adds the group to bar[0]) so that no counter takes more than a few dozen
-// atomics per barrier.  Returns false (and records the timeout) if a wait gave
-// up or another block already did; the caller then returns.
-__device__ bool grid_sync(unsigned *bar, unsigned epoch, SolveState *st) {
+// atomics per barrier.  A wait gives up after `limit` polls (about 64 ns
+// apart).  Returns false (and records the timeout) if a wait gave up or another
+// block already did; the caller then returns.
+__device__ bool grid_sync(unsigned *bar, unsigned epoch, SolveState *st, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -67,7 +68,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned epoch, SolveState *st) {
     const unsigned target = epoch * ngrp;
     long long polls = 0;
     while (ld_relaxed(bar) < target) {   // the fence below orders what follows
-      if (*(volatile int *)&st->err == kGsBarrierTimeout || ++polls > (1LL << 22)) {
+      if (*(volatile int *)&st->err == kGsBarrierTimeout || ++polls > limit) {
         atomicCAS(&st->err, 0, kGsBarrierTimeout);
         good = 0;
         break;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells * nf;
        i += (long long)gridDim.x * blockDim.x)
     G.Sfs[i] = G.S64[i];
-  if (!grid_sync(G.bar, ++nbar, st)) return;
+  if (!grid_sync(G.bar, ++nbar, st, G.poll_limit)) return;
 
   const int fs = st->fs_count;
   const int prev = fs & 1;
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
       }
       __syncthreads();
     }
-    if (!grid_sync(G.bar, ++nbar, st)) return;
+    if (!grid_sync(G.bar, ++nbar, st, G.poll_limit)) return;
     if (fix) {
       // top plane of a bounded V axis: the upwind S of the ghost layer was this
       // plane's; add Psi- times its change, then store the outflow ghosts.  One
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(kGsThreads, 3) gs_reverse_kernel(const GsArgs<
         }
         if (G.JR64) G.JR64[fc + c] += extra;
       }
-      if (!grid_sync(G.bar, ++nbar, st)) return;
+      if (!grid_sync(G.bar, ++nbar, st, G.poll_limit)) return;
     }
   }
   // residual: block maximum, then one atomic per block

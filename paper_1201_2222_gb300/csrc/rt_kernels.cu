@@ -96,6 +96,16 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
   const int sa = gp.sa;
   const int wlast = sa > 0 ? Nw - 1 : 0;
   cg::cluster_group cluster = cg::this_cluster();
+  // subdomain z faces: z is the sweep axis w (z sweeps) or the plane axis v (x,
+  // y sweeps); the ghost layer's cells are [y][x], (x, y) = (u, v) for z sweeps,
+  // (w, u) for x sweeps, (u, w) for y sweeps
+  const bool zw = cax[2] == 2, zv = cax[1] == 2;
+  const int xw = (zw && A.ext[sa > 0 ? 0 : 1]) ? (sa > 0 ? 0 : 1) : -1;   // beyond the first plane
+  const int n0 = A.d.n[0];
+  const long long f2 = (long long)n0 * A.d.n[1];
+  auto xfc = [&](int uu, int ww) -> long long {   // ghost-layer cell of plane cell (uu, v past the face, ww)
+    return gp.axis == 0 ? (long long)uu * n0 + ww : (long long)ww * n0 + uu;
+  };
 
   for (int t = 0; t < Nw; ++t) {
     const int w = sa > 0 ? t : Nw - 1 - t;
@@ -129,8 +139,29 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
           const long long iB = pbase + (long long)v * Nu + um;
           const long long iC = pbase + (long long)vm * Nu + u;
           const long long iD = pbase + (long long)vm * Nu + um;
-          const T sA = SP[RT_IDX(iA, cells, 4)], sB = SP[RT_IDX(iB, cells, 4)];
-          const T sC = SP[RT_IDX(iC, cells, 4)], sD = SP[RT_IDX(iD, cells, 4)];
+          // the upwind face beyond a subdomain z face: the whole face (z sweeps at the
+          // first plane) or its rows v - sv (x, y sweeps) read the ghost layer
+          const bool xall = !wp_in && xw >= 0;
+          const int xr = (!xall && zv && !vb_in && A.ext[vb < 0 ? 0 : 1]) ? (vb < 0 ? 0 : 1) : -1;
+          T sA, sB, sC, sD;
+          if (xall) {
+            const T *X = A.xS[xw] + (long long)f * f2;
+            sA = X[RT_IDX((long long)v * Nu + u, f2, 63)];
+            sB = X[RT_IDX((long long)v * Nu + um, f2, 63)];
+            sC = X[RT_IDX((long long)vm * Nu + u, f2, 63)];
+            sD = X[RT_IDX((long long)vm * Nu + um, f2, 63)];
+          } else {
+            sA = SP[RT_IDX(iA, cells, 4)];
+            sB = SP[RT_IDX(iB, cells, 4)];
+            if (xr >= 0) {
+              const T *X = A.xS[xr] + (long long)f * f2;
+              sC = X[RT_IDX(xfc(u, wpm), f2, 64)];
+              sD = X[RT_IDX(xfc(um, wpm), f2, 64)];
+            } else {
+              sC = SP[RT_IDX(iC, cells, 4)];
+              sD = SP[RT_IDX(iD, cells, 4)];
+            }
+          }
           T IA, IB, IC, ID;
           if (wp_in) {
             const int rowA = (a * Rmax + lv) * Nu;
@@ -168,8 +199,25 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
             E = A.WE[wi];
             psi0 = A.WP[wi];
           } else {
-            const T cA = chiP[RT_IDX(iA, cells, 3)], cB = chiP[RT_IDX(iB, cells, 3)];
-            const T cC = chiP[RT_IDX(iC, cells, 3)], cD = chiP[RT_IDX(iD, cells, 3)];
+            T cA, cB, cC, cD;
+            if (xall) {
+              const T *X = A.xchi[xw] + (long long)f * f2;
+              cA = X[(long long)v * Nu + u];
+              cB = X[(long long)v * Nu + um];
+              cC = X[(long long)vm * Nu + u];
+              cD = X[(long long)vm * Nu + um];
+            } else {
+              cA = chiP[RT_IDX(iA, cells, 3)];
+              cB = chiP[RT_IDX(iB, cells, 3)];
+              if (xr >= 0) {
+                const T *X = A.xchi[xr] + (long long)f * f2;
+                cC = X[xfc(u, wpm)];
+                cD = X[xfc(um, wpm)];
+              } else {
+                cC = chiP[RT_IDX(iC, cells, 3)];
+                cD = chiP[RT_IDX(iD, cells, 3)];
+              }
+            }
             const T chim = p.wa * cA + p.wb * cB + p.wc * cC + p.wd * cD;
             const T dtau = (chim + chi0) * p.hs;
             T om;
@@ -177,6 +225,14 @@ __global__ void __launch_bounds__(512) sc_sweep_kernel(const SweepArgs<T> A) {
           }
           const T I0 = Sm + E * (Im - Sm) + psi0 * (S0 - Sm);
           cur[RT_IDX((a * Rmax + lv) * Nu + u, smem_n, 7)] = I0;
+          {   // intensities on the first / last z plane, for the neighbouring subdomains
+            const int z = zw ? w : v;
+            const int side = z == 0 ? 0 : (z == A.d.n[2] - 1 ? 1 : -1);
+            if (side >= 0 && A.xout[side]) {
+              const long long fc = zw ? (long long)v * Nu + u : xfc(u, w);
+              A.xout[side][RT_IDX(((long long)f * A.na + p.angle) * f2 + fc, (long long)A.d.nf * A.na * f2, 65)] = I0;
+            }
+          }
           const T wI = p.wq * I0;
           Jacc += wI;
           if (MOM) {
@@ -614,6 +670,78 @@ __device__ __forceinline__ void vec_update(const AngleParam<float> &p, const flo
   }
 }
 
+// ------------------------------------------------ packed-pair update (float32)
+// The vectorised pipelined sweep's formal-solution step without moments: a
+// thread's four cells form two pairs, and every per-cell operation of Eq. 20
+// (interpolants, dtau, segment weights, the intensity update, the J sum) runs
+// on a pair with one packed-FP32 instruction (f32x2).  The pairs of the cell's
+// own column on a row are aligned register pairs of the row's 128-bit load; the
+// upwind-column values (offset by the sign of mu_u) enter by scalar FMAs.
+
+// One staged row around a 4-cell segment: columns u0..u0+3 as two pairs, and
+// the column before (l) or after (r) it, whichever the stencil needs.
+struct Row4 {
+  float2 a0, a1;
+  float l, r;
+};
+
+template <int SU>
+__device__ __forceinline__ void row4(unsigned addr, unsigned needL, unsigned needR, Row4 &o) {
+  const float4 q = lds128(addr);
+  o.a0 = make_float2(q.x, q.y);
+  o.a1 = make_float2(q.z, q.w);
+  if (SU > 0) {
+    o.l = __shfl_up_sync(0xffffffffu, q.w, 1);
+    lds32_if(o.l, addr - 4u, needL);   // first lane of a warp or first segment of a row
+  } else {
+    o.r = __shfl_down_sync(0xffffffffu, q.x, 1);
+    lds32_if(o.r, addr + 16u, needR);
+  }
+}
+
+// value of the upwind column (u - SU) for cell j of a segment (the row's cell
+// j + 1 - SU in the order l, a0.x, a0.y, a1.x, a1.y, r)
+template <int SU>
+__device__ __forceinline__ float upcol(const Row4 &o, int j) {
+  if (SU > 0) return j == 0 ? o.l : (j == 1 ? o.a0.x : (j == 2 ? o.a0.y : o.a1.x));
+  return j == 0 ? o.a0.y : (j == 1 ? o.a1.x : (j == 2 ? o.a1.y : o.r));
+}
+
+// bilinear interpolant of one cell pair (cells 2h, 2h+1): w = {wa, wa, wb, wb},
+// v = {wc, wc, wd, wd}; rows X (own row) and Y (row v - SV)
+template <int SU>
+__device__ __forceinline__ float2 bilin2(const float4 &w, const float4 &v, const Row4 &X, const Row4 &Y, int h) {
+  const float2 xa = h ? X.a1 : X.a0, ya = h ? Y.a1 : Y.a0;
+  float2 m = __fmul2_rn(make_float2(w.x, w.y), xa);
+  m = __ffma2_rn(make_float2(v.x, v.y), ya, m);
+  m.x = fmaf(w.z, upcol<SU>(X, 2 * h), m.x);
+  m.y = fmaf(w.z, upcol<SU>(X, 2 * h + 1), m.y);
+  m.x = fmaf(v.z, upcol<SU>(Y, 2 * h), m.x);
+  m.y = fmaf(v.z, upcol<SU>(Y, 2 * h + 1), m.y);
+  return m;
+}
+
+// E = e^-x and Psi0 = 1 - (1 - E)/x of a pair.  Below x = 1/2 Psi0 is
+// x (c0 + c1 x + ... + c4 x^4), a polynomial fitted to Psi0/x on [0, 1/2] by
+// minimising the largest error (about 6e-9 absolute in Psi0, under float32
+// resolution; the Taylor series needs eight terms for the same); above it the
+// direct form, whose error (that of the exponential over x) is then below 3e-7.
+// Constants enter through scalar instructions (they take immediate operands,
+// the packed ones do not).
+__device__ __forceinline__ void seg_weights2(float2 x, float2 &E, float2 &psi0) {
+  E.x = ex2_approx(x.x * -1.4426950408889634f);
+  E.y = ex2_approx(x.y * -1.4426950408889634f);
+  float px = fmaf(x.x, 0.0011282316f, -0.0081961248f), py = fmaf(x.y, 0.0011282316f, -0.0081961248f);
+  px = fmaf(x.x, px, 0.041633245f); py = fmaf(x.y, py, 0.041633245f);
+  px = fmaf(x.x, px, -0.16666308f); py = fmaf(x.y, py, -0.16666308f);
+  px = fmaf(x.x, px, 0.49999988f); py = fmaf(x.y, py, 0.49999988f);
+  const float2 small = __fmul2_rn(x, make_float2(px, py));
+  const float2 e0 = make_float2(1.f - E.x, 1.f - E.y);
+  const float2 q = __fmul2_rn(e0, make_float2(rcp_approx(x.x), rcp_approx(x.y)));
+  psi0.x = x.x < 0.5f ? small.x : 1.f - q.x;
+  psi0.y = x.y < 0.5f ? small.y : 1.f - q.y;
+}
+
 template <typename T, int AMAX, bool MOM, int SEG, bool VEC>
 __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
   if (A.skip_if_done && A.st->done) return;
@@ -655,7 +783,17 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   const long long smem_n = 2LL * ib + 6LL * pb;
 #endif
   __shared__ AngleParam<T> P[AMAX];
-  if (threadIdx.x < gp.na) P[threadIdx.x] = A.ang[gp.a0 + threadIdx.x];
+  // the packed-pair path's ray constants: {wa, wa, wb, wb}, {wc, wc, wd, wd}, {hs, hs, wq, wq}
+  __shared__ float4 P2[(VEC && !MOM) ? AMAX : 1][3];
+  if (threadIdx.x < gp.na) {
+    const AngleParam<T> q = A.ang[gp.a0 + threadIdx.x];
+    P[threadIdx.x] = q;
+    if constexpr (VEC && !MOM) {
+      P2[threadIdx.x][0] = make_float4(q.wa, q.wa, q.wb, q.wb);
+      P2[threadIdx.x][1] = make_float4(q.wc, q.wc, q.wd, q.wd);
+      P2[threadIdx.x][2] = make_float4(q.hs, q.hs, q.wq, q.wq);
+    }
+  }
 
   const int fs = A.st->fs_count + A.parity_offset;
   const int prev = fs & 1;
@@ -689,6 +827,12 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   }
   __syncthreads();
 
+  // divisions of the per-plane work loops, by divisors fixed for the launch
+  const FastDiv dq(vec ? Nu / 4 : Nu), dNu(Nu), drows(R + 2), d2rows(2 * (R + 2)), dR(R > 0 ? R : 1),
+      dnrowNu((v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0) > 0 ? ((v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0)) * Nu : 1),
+      dnseg(nseg);
+  const bool vedge = v0 == 0 || v1 == Nv;   // this strip holds a v-face row of the domain
+
   // chi and S of plane wsrc (rows v0-1 .. v1, columns -1 .. Nu, wrapped or clamped) -> ring slot
   auto stage = [&](int wsrc, int slot) {
     T *Cd = Cr + slot * pb, *Sd = Sr + slot * pb;
@@ -696,7 +840,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     if (vec) {
       const int q = Nu / 4;
       for (int idx = threadIdx.x; idx < rows * q; idx += blockDim.x) {
-        const int row = idx / q, k = idx - row * q;
+        const int row = dq.div(idx), k = idx - row * q;
         int vv = v0 - 1 + row;
         vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
         const long long o = (long long)wsrc * plane + (long long)vv * Nu + 4 * k;
@@ -705,7 +849,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       }
     } else {
       for (int idx = threadIdx.x; idx < rows * Nu; idx += blockDim.x) {
-        const int row = idx / Nu, u = idx - row * Nu;
+        const int row = dq.div(idx), u = idx - row * Nu;
         int vv = v0 - 1 + row;
         vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
         const long long o = (long long)wsrc * plane + (long long)vv * Nu + u;
@@ -714,7 +858,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       }
     }
     for (int idx = threadIdx.x; idx < 2 * rows; idx += blockDim.x) {
-      const int side = idx / rows, row = idx - side * rows;
+      const int side = drows.div(idx), row = idx - side * rows;
       int vv = v0 - 1 + row;
       vv = vv < 0 ? (perV ? vv + Nv : 0) : (vv >= Nv ? (perV ? vv - Nv : Nv - 1) : vv);
       const int uu = side ? (perU ? 0 : Nu - 1) : (perU ? Nu - 1 : 0);
@@ -738,8 +882,8 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       return;
     }
     for (int idx = threadIdx.x; idx < na * 2 * (R + 2); idx += blockDim.x) {
-      const int a = idx / (2 * (R + 2)), r2 = idx - a * 2 * (R + 2);
-      const int side = r2 / (R + 2), row = r2 - side * (R + 2);
+      const int a = d2rows.div(idx), r2 = idx - a * 2 * (R + 2);
+      const int side = drows.div(r2), row = r2 - side * (R + 2);
       const int vv = v0 - 1 + row;
       // a periodic u face with v inside the grid: the lagged ghost is the u-face
       // entry (w, v) of the ray's block (the general lookup gives the same address)
@@ -750,8 +894,8 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     }
     const int nrow = (v0 == 0 ? 1 : 0) + (v1 == Nv ? 1 : 0);   // rows outside the domain in v
     for (int idx = threadIdx.x; idx < na * nrow * Nu; idx += blockDim.x) {
-      const int a = idx / (nrow * Nu), r2 = idx - a * nrow * Nu;
-      const int which = r2 / Nu, u = r2 - which * Nu;
+      const int a = dnrowNu.div(idx), r2 = idx - a * nrow * Nu;
+      const int which = dNu.div(r2), u = r2 - which * Nu;
       const bool lo = (v0 == 0) && (which == 0);
       const int row = lo ? 0 : R + 1;
       // a periodic v face (u inside the grid): the v-face entry (w, u) of the ray's block
@@ -774,14 +918,14 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     T *dst = Gpre + (long long)buf * A.ray_slots * gpl;
     if (perU) {
       for (int idx = threadIdx.x; idx < na * R; idx += blockDim.x) {
-        const int a = idx / R, lv = idx - a * R;
+        const int a = dR.div(idx), lv = idx - a * R;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
         cp_async_elem(dst + a * gpl + lv, Gp + gb + plane + (long long)wp * Nv + v0 + lv);
       }
     }
-    if (perV) {
+    if (perV && vedge) {
       for (int idx = threadIdx.x; idx < na * Nu; idx += blockDim.x) {
-        const int a = idx / Nu, u = idx - a * Nu;
+        const int a = dNu.div(idx), u = idx - a * Nu;
         const int vr = P[a].sv > 0 ? Nv - 1 : 0;
         if (vr < v0 || vr >= v1) continue;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
@@ -805,7 +949,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     const T *pre = Gpre + (long long)buf * A.ray_slots * gpl;
     if (perU) {
       for (int idx = threadIdx.x; idx < na * R; idx += blockDim.x) {
-        const int a = idx / R, lv = idx - a * R;
+        const int a = dR.div(idx), lv = idx - a * R;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
         const int col = P[a].su > 0 ? Nu - 1 : 0;
         const long long off = RT_IDX(gb + plane + (long long)wp * Nv + v0 + lv, gn, 54);
@@ -814,9 +958,9 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
         else ghost_store<T>(Gp, Gn, Gdn, off, I0, inc, emit);
       }
     }
-    if (perV) {
+    if (perV && vedge) {
       for (int idx = threadIdx.x; idx < na * Nu; idx += blockDim.x) {
-        const int a = idx / Nu, u = idx - a * Nu;
+        const int a = dNu.div(idx), u = idx - a * Nu;
         const int vr = P[a].sv > 0 ? Nv - 1 : 0;
         if (vr < v0 || vr >= v1) continue;
         const long long gb = ((long long)f * A.na + P[a].angle) * A.d.gsize;
@@ -857,6 +1001,27 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   };
   issue(0);
 
+  // packed-pair path with one task per thread: the J partials of a plane are
+  // stored after the plane's cluster barrier, so that the barrier's release does
+  // not wait for their global writes (they drain during the next plane)
+  const bool defer = VEC && !MOM && R * nseg <= (int)blockDim.x;
+  const bool jxl = VEC && !MOM && A.jx && gp.axis == 0;   // partials in this group's plane layout
+  float4 Jpend = make_float4(0.f, 0.f, 0.f, 0.f);
+  long long cpend = -1;
+  auto flush_J = [&]() {
+    if (cpend < 0) return;
+    float *Jf = reinterpret_cast<float *>(Jout);
+    if (csu == 1 || jxl) {
+      *reinterpret_cast<float4 *>(Jf + RT_IDX(cpend, cells, 56)) = Jpend;
+    } else {
+      Jf[RT_IDX(cpend, cells, 57)] = Jpend.x;
+      Jf[RT_IDX(cpend + csu, cells, 57)] = Jpend.y;
+      Jf[RT_IDX(cpend + 2 * csu, cells, 57)] = Jpend.z;
+      Jf[RT_IDX(cpend + 3 * csu, cells, 57)] = Jpend.w;
+    }
+    cpend = -1;
+  };
+
   for (int t = 0; t < Nw; ++t) {
     const int w = sa > 0 ? t : Nw - 1 - t;
     T *Icur = Ib + (t & 1) * ib;
@@ -868,7 +1033,127 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
     // plane of the next step, after the cluster barrier)
     T *Ntop = Ntop0 ? Ntop0 + (t & 1) * ib + top_row * W + kPipeX0 : nullptr;
     T *Nbot = Nbot0 ? Nbot0 + (t & 1) * ib + kPipeX0 : nullptr;
-    if constexpr (VEC) {
+    if constexpr (VEC && !MOM) {
+      // packed pairs, every shared-memory access by 32-bit address
+      if (defer) {
+        flush_J();                                   // the previous plane's J partials
+        if (t > 0) ghost_pass(Iprv, w - sa, (t + 1) & 1);   // and its outflow ghosts
+      }
+      const int ntask = R * nseg;
+      const int lane = threadIdx.x & 31;
+      const unsigned sb = smem_addr(smem_raw);
+      const unsigned pb4 = (unsigned)pb * 4u, W4 = (unsigned)W * 4u;
+      const unsigned sIprv = sb + (unsigned)(((t + 1) & 1) * ib) * 4u;
+      const unsigned sIcur = sb + (unsigned)((t & 1) * ib) * 4u;
+      const unsigned sCp = sb + (unsigned)(2 * ib + ((t + 2) % 3) * pb) * 4u;
+      const unsigned sCc = sb + (unsigned)(2 * ib + (t % 3) * pb) * 4u;
+      const unsigned sSp = sb + (unsigned)(2 * ib + 3 * pb + ((t + 2) % 3) * pb) * 4u;
+      const unsigned sSc = sb + (unsigned)(2 * ib + 3 * pb + (t % 3) * pb) * 4u;
+      // this plane's halo rows of the neighbouring strips, in their shared memory
+      const unsigned rTop = Ntop0 ? mapa_rank(sIcur + (unsigned)(top_row * W + kPipeX0) * 4u, rank - 1) : 0u;
+      const unsigned rBot = Nbot0 ? mapa_rank(sIcur + (unsigned)kPipeX0 * 4u, rank + 1) : 0u;
+      for (int base = threadIdx.x - lane; base < ntask; base += blockDim.x) {
+        const int sidx = base + lane;
+        const bool active = sidx < ntask;
+        const int sc = active ? sidx : ntask - 1;
+        const int lv = dnseg.div(sc), seg = sc - lv * nseg;
+        const int u0 = seg * 4, v = v0 + lv, row = lv + 1;
+        const unsigned needL = !(active && seg > 0 && lane > 0);
+        const unsigned needR = !(active && seg < nseg - 1 && lane < 31 && sidx + 1 < ntask);
+        const unsigned ro = (unsigned)(row * W + kPipeX0 + u0) * 4u;
+        const bool pushTop = active && lv == 0 && Ntop0 != nullptr;
+        const bool pushBot = active && lv == R - 1 && Nbot0 != nullptr;
+        // chi and S of the upwind plane, rows v-1, v, v+1 (both stencil sides: the
+        // rays' signs of mu_u differ within the group)
+        Row4 cm, c0, cp, sm, s0, sp;
+        {
+          const float4 q = lds128(sCp + ro - W4);
+          cm.a0 = make_float2(q.x, q.y); cm.a1 = make_float2(q.z, q.w);
+          cm.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(cm.l, sCp + ro - W4 - 4u, needL);
+          cm.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(cm.r, sCp + ro - W4 + 16u, needR);
+        }
+        {
+          const float4 q = lds128(sCp + ro);
+          c0.a0 = make_float2(q.x, q.y); c0.a1 = make_float2(q.z, q.w);
+          c0.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(c0.l, sCp + ro - 4u, needL);
+          c0.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(c0.r, sCp + ro + 16u, needR);
+        }
+        {
+          const float4 q = lds128(sCp + ro + W4);
+          cp.a0 = make_float2(q.x, q.y); cp.a1 = make_float2(q.z, q.w);
+          cp.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(cp.l, sCp + ro + W4 - 4u, needL);
+          cp.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(cp.r, sCp + ro + W4 + 16u, needR);
+        }
+        {
+          const float4 q = lds128(sSp + ro - W4);
+          sm.a0 = make_float2(q.x, q.y); sm.a1 = make_float2(q.z, q.w);
+          sm.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(sm.l, sSp + ro - W4 - 4u, needL);
+          sm.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(sm.r, sSp + ro - W4 + 16u, needR);
+        }
+        {
+          const float4 q = lds128(sSp + ro);
+          s0.a0 = make_float2(q.x, q.y); s0.a1 = make_float2(q.z, q.w);
+          s0.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(s0.l, sSp + ro - 4u, needL);
+          s0.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(s0.r, sSp + ro + 16u, needR);
+        }
+        {
+          const float4 q = lds128(sSp + ro + W4);
+          sp.a0 = make_float2(q.x, q.y); sp.a1 = make_float2(q.z, q.w);
+          sp.l = __shfl_up_sync(0xffffffffu, q.w, 1); lds32_if(sp.l, sSp + ro + W4 - 4u, needL);
+          sp.r = __shfl_down_sync(0xffffffffu, q.x, 1); lds32_if(sp.r, sSp + ro + W4 + 16u, needR);
+        }
+        const float4 q0 = lds128(sCc + ro), r0 = lds128(sSc + ro);
+        const float2 chi0[2] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w)};
+        const float2 S0[2] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w)};
+        float2 Jp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        auto ray = [&](auto su_c, auto sv_c, int a) {
+          constexpr int SU = decltype(su_c)::value, SV = decltype(sv_c)::value;
+          const float4 wab = P2[a][0], wcd = P2[a][1], hq = P2[a][2];
+          const unsigned ia = sIprv + (unsigned)a * pb4 + ro;
+          Row4 Ir, Iw;
+          row4<SU>(ia, needL, needR, Ir);
+          row4<SU>(SV > 0 ? ia - W4 : ia + W4, needL, needR, Iw);   // halo rows hold the neighbours' rows
+          const Row4 &cY = SV > 0 ? cm : cp;
+          const Row4 &sY = SV > 0 ? sm : sp;
+          float2 o[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float2 chim = bilin2<SU>(wab, wcd, c0, cY, h);
+            const float2 Sm = bilin2<SU>(wab, wcd, s0, sY, h);
+            const float2 Im = bilin2<SU>(wab, wcd, Ir, Iw, h);
+            const float2 dtau = __fmul2_rn(__fadd2_rn(chim, chi0[h]), make_float2(hq.x, hq.y));
+            float2 E, psi0;
+            seg_weights2(dtau, E, psi0);
+            // I0 = S- + E (I- - S-) + Psi0 (S0 - S-)
+            const float2 d1 = make_float2(Im.x - Sm.x, Im.y - Sm.y);
+            const float2 d2 = make_float2(S0[h].x - Sm.x, S0[h].y - Sm.y);
+            float2 I0 = __ffma2_rn(E, d1, Sm);
+            I0 = __ffma2_rn(psi0, d2, I0);
+            o[h] = I0;
+            Jp[h] = __ffma2_rn(make_float2(hq.z, hq.w), I0, Jp[h]);
+          }
+          const float4 o4 = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+          const unsigned ao = (unsigned)a * pb4;
+          if (active) sts128(sIcur + ao + ro, o4);
+          if (pushTop) stc128(rTop + ao + (unsigned)u0 * 4u, o4);
+          if (pushBot) stc128(rBot + ao + (unsigned)u0 * 4u, o4);
+        };
+        auto block = [&](auto su_c, auto sv_c, int k0, int kn) {
+#pragma unroll 2
+          for (int q = 0; q < kn; ++q) ray(su_c, sv_c, k0 + q);
+        };
+        block(SignC<-1>{}, SignC<-1>{}, gp.kb[0], gp.kb[1] - gp.kb[0]);
+        block(SignC<1>{}, SignC<-1>{}, gp.kb[1], gp.kb[2] - gp.kb[1]);
+        block(SignC<-1>{}, SignC<1>{}, gp.kb[2], gp.kb[3] - gp.kb[2]);
+        block(SignC<1>{}, SignC<1>{}, gp.kb[3], gp.kb[4] - gp.kb[3]);
+        if (active) {
+          Jpend = make_float4(Jp[0].x, Jp[0].y, Jp[1].x, Jp[1].y);
+          cpend = jxl ? (long long)u0 + (long long)v * Nu + (long long)w * plane
+                      : (long long)(u0) * csu + (long long)v * csv + (long long)w * csw;
+          if (!defer) flush_J();
+        }
+      }
+    } else if constexpr (VEC) {
       // float32 rows whose length is a multiple of 4: one segment per lane, a
       // warp-uniform trip count so every shuffle has the whole warp
       const int ntask = R * nseg;
@@ -878,7 +1163,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
         const int sidx = base + lane;
         const bool active = sidx < ntask;
         const int sc = active ? sidx : ntask - 1;
-        const int lv = sc / nseg, seg = sc - lv * nseg;
+        const int lv = dnseg.div(sc), seg = sc - lv * nseg;
         const int u0 = seg * 4, v = v0 + lv, row = lv + 1;
         const bool haveL = active && seg > 0 && lane > 0;
         const bool haveR = active && seg < nseg - 1 && lane < 31 && sidx + 1 < ntask;
@@ -983,7 +1268,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       }
     } else {
       for (int sidx = threadIdx.x; sidx < R * nseg; sidx += blockDim.x) {
-        const int lv = sidx / nseg, seg = sidx - lv * nseg;
+        const int lv = dnseg.div(sidx), seg = sidx - lv * nseg;
         const int u0 = seg * SEG, v = v0 + lv, row = lv + 1;
         const int ncell = min(SEG, Nu - u0);
         T cm[SEG + 2], c0[SEG + 2], cp[SEG + 2], sm[SEG + 2], s0[SEG + 2], sp[SEG + 2];
@@ -1073,7 +1358,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       }
     }
     // outflow ghosts of the previous plane, read from its (still intact) buffer
-    if (t > 0) ghost_pass(Iprv, w - sa, (t + 1) & 1);
+    if (t > 0 && !defer) ghost_pass(Iprv, w - sa, (t + 1) & 1);
     cp_async_wait_all();
     // the CTA is done with the chi/S slot and the halo columns the next issue
     // refills; the cluster barrier (strip edges pushed to the neighbours) is
@@ -1087,6 +1372,7 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
       issue(t + 1);
     }
   }
+  flush_J();
   ghost_pass(Ib + ((Nw - 1) & 1) * ib, sa > 0 ? Nw - 1 : 0, (Nw - 1) & 1);
   (void)top_edge;
   (void)bot_edge;
@@ -1146,24 +1432,56 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
   const bool inc = A.incremental && !first;
   const int x = x0 + tx;
   double rmax = 0.0;
+  // float32 partials are summed exactly into a float pair (TwoSum) in group
+  // order; those of the first nxg groups (sweeps along x) are in the [x][z][y]
+  // layout and come through a shared-memory transpose of the tile
   if (A.fmask && A.fmask[f]) {   // this frequency is solved by another grid
     block_max_to(0.0, &A.st->resid_bits);
     return;
   }
+  constexpr int KR = kAliTile / kAliRows;
+  float xhi[KR], xlo[KR];
 #pragma unroll
-  for (int k = 0; k < kAliTile / kAliRows; ++k) {
+  for (int k = 0; k < KR; ++k) xhi[k] = xlo[k] = 0.f;
+  if (sizeof(T) == 4 && A.Jpart && A.nxg > 0) {
+    __shared__ float tJ[kAliTile][kAliTile + 1];
+    for (int p = 0; p < A.nxg; ++p) {
+      const float *src = reinterpret_cast<const float *>(A.Jpart) + ((long long)p * A.d.nf + f) * cells;
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const int xx = x0 + ty + k * kAliRows, yy = y0 + tx;
+        tJ[ty + k * kAliRows][tx] = (xx < nx && yy < ny) ? src[((long long)xx * nz + z) * ny + yy] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < KR; ++k) {
+        const float v = tJ[tx][ty + k * kAliRows];
+        const float s2 = xhi[k] + v;
+        const float bp = s2 - xhi[k];
+        xlo[k] += (xhi[k] - (s2 - bp)) + (v - bp);
+        xhi[k] = s2;
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
     const int y = y0 + ty + k * kAliRows;
     T snew = T(0);
     if (x < nx && y < ny) {
       const long long c = ((long long)z * ny + y) * nx + x;
       const long long i = fbase + c;
       double dJ;
-      if (sizeof(T) == 4) {
+      if (!A.Jpart) {
+        // the formal solution was done elsewhere (a mixed grid's FP64 first one):
+        // its J is already in J64
+        dJ = A.J64[i];
+      } else if (sizeof(T) == 4) {
         // float32 partials summed exactly into a float pair (TwoSum), then one FP64
         // add: the result is the FP64 sum to ~1e-14 at FP32 cost
-        float hi = 0.f, lo = 0.f;
+        float hi = xhi[k], lo = xlo[k];
 #pragma unroll 4
-        for (int p = 0; p < A.ngroups_per_f; ++p) {
+        for (int p = A.nxg; p < A.ngroups_per_f; ++p) {
           const float x = (float)A.Jpart[(long long)p * A.d.nf * cells + i];
           const float s2 = hi + x;
           const float bp = s2 - hi;
@@ -1223,6 +1541,17 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
   block_max_to(rmax, &A.st->resid_bits);
 }
 
+// Lagged ghosts after an FP64 formal solution done for a float32 grid: the
+// outflow Gout and, for the incremental sweeps that follow, its change against
+// the ghosts Gin the solution started from.
+__global__ void ghosts_from64_kernel(long long n, const double *Gout, const double *Gin, float *G, float *Gd) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    G[i] = (float)Gout[i];
+    Gd[i] = (float)(Gout[i] - Gin[i]);
+  }
+}
+
 // Jacobi denominator of Eq. 24, inverted once per medium: the update then
 // multiplies instead of dividing in FP64 every iteration.
 __global__ void inv_denominator_kernel(long long n, const double *eps, const double *oml, double *iden) {
@@ -1249,7 +1578,9 @@ __global__ void finish_kernel(SolveState *st) {
 
 // Small state edits, in stream order.
 __global__ void state_op_kernel(SolveState *st, int op, int a, double b, int c) {
-  if (op == 0) {           // reset for a new ALI solve
+  if (op == 0) {           // reset for a new ALI solve (and its error word)
+    st->err = 0;
+    st->err_info = 0;
     st->fs_count = 0;
     st->iter = 0;
     st->done = 0;
@@ -1283,7 +1614,8 @@ constexpr int kLstarChunk = 64;   // rays staged in shared memory at a time
 
 template <typename T>
 __global__ void __launch_bounds__(256) lstar_kernel(Dims d, const double *chi, const RayGeom *rays,
-                                                    int na, double *lstar, double *oml) {
+                                                    int na, double *lstar, double *oml,
+                                                    const double *xchi_lo, const double *xchi_hi) {
   __shared__ LstarRay<T> R[kLstarChunk];
   const long long cells = d.cells;
   const long long N = cells * d.nf;
@@ -1333,8 +1665,10 @@ __global__ void __launch_bounds__(256) lstar_kernel(Dims d, const double *chi, c
           int xx = x + q.off[v][0], yy = y + q.off[v][1], zz = z + q.off[v][2];
           xx = xx < 0 ? (px ? nx - 1 : 0) : (xx >= nx ? (px ? 0 : nx - 1) : xx);
           yy = yy < 0 ? (py ? ny - 1 : 0) : (yy >= ny ? (py ? 0 : ny - 1) : yy);
+          // beyond a subdomain z face: the ghost layer's chi
+          const double *xc = zz < 0 ? xchi_lo : (zz >= nz ? xchi_hi : nullptr);
           zz = zz < 0 ? (pz ? nz - 1 : 0) : (zz >= nz ? (pz ? 0 : nz - 1) : zz);
-          chim += q.w4[v] * (T)chf[((long long)zz * ny + yy) * nx + xx];
+          chim += q.w4[v] * (T)(xc ? xc[(f * ny + yy) * nx + xx] : chf[((long long)zz * ny + yy) * nx + xx]);
         }
         const T dtau = (chim + chi0) * q.hs;
         T E, psi0, om;
@@ -1721,6 +2055,12 @@ cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_ghosts_from64(long long n, const double *Gout, const double *Gin, float *G, float *Gd,
+                                 cudaStream_t s) {
+  ghosts_from64_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, Gout, Gin, G, Gd);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish(SolveState *st, cudaStream_t s) {
   finish_kernel<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();
@@ -1733,8 +2073,10 @@ cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cuda
 
 template <typename T>
 cudaError_t launch_lstar(const Dims &d, const double *chi, const RayGeom *rays, int na, double *lstar,
-                         double *oml, cudaStream_t s) {
-  lstar_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, chi, rays, na, lstar, oml);
+                         double *oml, const double *const xchi[2], cudaStream_t s) {
+  lstar_kernel<T><<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, chi, rays, na, lstar, oml,
+                                                                 xchi ? xchi[0] : nullptr,
+                                                                 xchi ? xchi[1] : nullptr);
   return cudaGetLastError();
 }
 
@@ -1779,15 +2121,16 @@ cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double *oml,
-                                 unsigned long long *out, cudaStream_t s) {
-  eps_thick_min_kernel<<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, eps, oml, out);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
                                    cudaStream_t s) {
   inv_denominator_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, eps, oml, iden);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps_thick_min(const Dims &d, const double *eps, const double *oml,
+                                 unsigned long long *out, cudaStream_t s) {
+  eps_thick_min_kernel<<<grid_for(d.cells * d.nf, 256), 256, 0, s>>>(d, eps, oml, out);
   return cudaGetLastError();
 }
 
@@ -1811,7 +2154,7 @@ cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, c
   template int sweep_max_active_clusters<T>(int, int, int, int, size_t);                          \
   template cudaError_t launch_ali<T>(const AliArgs<T> &, cudaStream_t);                             \
   template cudaError_t launch_lstar<T>(const Dims &, const double *, const RayGeom *, int, double *, \
-                                       double *, cudaStream_t);                                     \
+                                       double *, const double *const[2], cudaStream_t);                                     \
   template cudaError_t launch_permute<T>(const Dims &, const double *, T *, T *, T *, cudaStream_t);  \
   template cudaError_t launch_init_ghosts<T>(const Dims &, int, const RayGeom *, const double *, T *, \
                                              cudaStream_t);                                         \

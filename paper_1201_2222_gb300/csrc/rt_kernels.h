@@ -33,13 +33,24 @@ struct SweepArgs {
                              // [slot][nf][w][v][u] of the slot's group (NULL: computed)
   int gs_forward;            // 1: Gauss-Seidel forward phase -- groups crossing the
   int gs_axis;               //    gs_axis face with mu < 0 (the reverse rays) do nothing
+  // subdomain (EXTERNAL) z faces, side 0 = low, 1 = high (one-cell-per-thread
+  // sweep only): the ghost layer's chi, S and B [nf][ny][nx] and every ray's
+  // lagged intensity there [nf][na][ny][nx]; the sweep writes its own
+  // intensities on the first / last z plane into xout [nf][na][ny][nx]
+  int ext[2];
+  const T *xchi[2], *xS[2], *xB[2], *xI[2];
+  T *xout[2];
+  int jx;                    // 1: the float32 pipelined sweep writes the J partials of
+                             //    groups sweeping along x in their plane layout [x][z][y]
+                             //    (contiguous rows); consumers must read them so
 };
 
 template <typename T>
 struct AliArgs {
   Dims d;
   int ngroups_per_f;
-  const T *Jpart;
+  const T *Jpart;            // NULL: J64 already holds this formal solution's J (first iteration)
+  int nxg;                   // the first nxg groups' partials are in the [x][z][y] layout (jx)
   const double *eps, *B;
   const double *iden;        // 1 / [eps + (1 - eps)(1 - Lambda*)], fixed for a medium
   const T *Opart;            // second-order sweeps: group partials of 1 - Lambda* of this
@@ -84,6 +95,7 @@ struct GsArgs {
                              // (2 planes), Psi0, Psi-
   const unsigned char *fmask;
   unsigned *bar;             // grid-barrier counter, zero at launch
+  long long poll_limit;      // polls of a barrier wait before it gives up
 };
 
 // Correction weights of the forward rays: for each cell and each of the 3 x 3
@@ -139,13 +151,17 @@ cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, in
 template <typename T>
 cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s);
 cudaError_t launch_finish(SolveState *st, cudaStream_t s);
+// G = (float) Gout, Gd = (float) (Gout - Gin) over n ghost entries
+cudaError_t launch_ghosts_from64(long long n, const double *Gout, const double *Gin, float *G, float *Gd,
+                                 cudaStream_t s);
 // iden = 1 / [eps + (1 - eps)(1 - Lambda*)] (the Jacobi denominator of Eq. 24)
 cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
                                    cudaStream_t s);
 cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cudaStream_t s);
+// xchi[2]: the ghost layers' chi [nf][ny][nx] beyond EXTERNAL z faces (NULL elsewhere)
 template <typename T>
 cudaError_t launch_lstar(const Dims &d, const double *chi, const RayGeom *rays, int na, double *lstar,
-                         double *oml, cudaStream_t s);
+                         double *oml, const double *const xchi[2], cudaStream_t s);
 cudaError_t launch_validate(long long n, const double *chi, const double *eps, const double *B,
                             int *counts, cudaStream_t s);
 template <typename T>

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-PERIODIC, VACUUM, THERMAL, FIXED = 0, 1, 2, 3
+PERIODIC, VACUUM, THERMAL, FIXED, EXTERNAL = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 HEAT_INTEGRAL, HEAT_DIFFERENTIAL, HEAT_SWITCH = 0, 1, 2
 INTERP_LINEAR, INTERP_QUADRATIC = 1, 2
@@ -46,7 +46,7 @@ class rt_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("resid", ctypes.c_double), ("sweep_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_int), ("total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong),
-                ("graph_launches", ctypes.c_longlong)]
+                ("graph_launches", ctypes.c_longlong), ("first_fp64", ctypes.c_int)]
 
 
 class rt_server_opts(ctypes.Structure):
@@ -106,6 +106,15 @@ _SIGS = {
     "rt_poll": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.POINTER(rt_request_info)]),
     "rt_wait": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(rt_request_info)]),
     "rt_fetch": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP, _VP, _VP]),
+    "rt_measure_rates": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "rt_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "rt_set_external_face": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int,
+                                            ctypes.POINTER(rt_solve_opts)]),
+    "rt_get_face_intensity": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int,
+                                             ctypes.POINTER(rt_solve_opts)]),
+    "rt_ali_begin": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts)]),
+    "rt_ali_iterate": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "rt_last_error": (ctypes.c_char_p, []),
 }
 
@@ -157,6 +166,17 @@ def angle_table(n_mu, two_d=False):
     w = np.empty(n)
     lib.rt_angle_table(n_mu, 1 if two_d else 0, mu.ctypes.data, w.ctypes.data)
     return mu, w
+
+
+RATE_NAMES = ("fp32_fma_flops", "fp32x2_fma_flops", "mufu_ex2_per_s", "mufu_rcp_per_s", "fp64_fma_flops")
+
+
+def measure_rates():
+    """Measured arithmetic rates of the current CUDA device (rt_measure_rates)."""
+    lib = load()
+    out = np.zeros(len(RATE_NAMES))
+    _check(lib.rt_measure_rates(out.ctypes.data, len(RATE_NAMES)))
+    return dict(zip(RATE_NAMES, (float(x) for x in out)))
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -334,6 +354,45 @@ class Grid:
                                  1 if on_device else 0, ctypes.byref(o)))
         return res
 
+    def set_external_face(self, side, chi=None, S=None, B=None, I=None):
+        """Ghost layer of a subdomain z face (rt_set_external_face): chi, S, B
+        [nf][ny][nx] and the rays' incoming intensities I [nf][na][ny][nx] (host)."""
+        lay = self.nfreq * self.shape[2] * self.shape[3]
+        keep = []
+        def ptr(x, n):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+            if a.size != n:
+                raise ValueError(f"expected {n} values, got {a.size}")
+            keep.append(a)
+            return a.ctypes.data
+        o = self._opts()
+        _check(load().rt_set_external_face(self._h, int(side), ptr(chi, lay), ptr(S, lay), ptr(B, lay),
+                                           ptr(I, lay * self.n_angles), 0, ctypes.byref(o)))
+
+    def face_intensity(self, side):
+        """Intensities of the last formal solution on the first (0) or last (1) z
+        plane, [nf][na][ny][nx] (rt_get_face_intensity)."""
+        I = np.empty((self.nfreq, self.n_angles) + self.shape[2:])
+        o = self._opts()
+        _check(load().rt_get_face_intensity(self._h, int(side), I.ctypes.data, 0, ctypes.byref(o)))
+        return I
+
+    def ali_begin(self, S_init=None):
+        """Start a Jacobi ALI solve taken one step at a time (rt_ali_begin)."""
+        ps, ds, ks = (None, 0, None) if S_init is None else self._in(S_init)
+        o = self._opts(on_device=bool(ds))
+        _check(load().rt_ali_begin(self._h, ps, ds, ctypes.byref(o)))
+
+    def ali_iterate(self, n=1):
+        """n more iterations (rt_ali_iterate): (iterations since begin, last max |dS|/S)."""
+        it = ctypes.c_int(0)
+        r = ctypes.c_double(0.0)
+        o = self._opts()
+        _check(load().rt_ali_iterate(self._h, int(n), ctypes.byref(o), ctypes.byref(it), ctypes.byref(r)))
+        return it.value, r.value
+
     def get_S(self, on_device=False):
         S = self._out(self.shape, on_device)
         o = self._opts(on_device=on_device)
@@ -345,6 +404,10 @@ class Grid:
         if isinstance(scheme, str):
             scheme = {"jacobi": ITER_JACOBI, "gauss_seidel": ITER_GAUSS_SEIDEL}[scheme.lower()]
         _check(load().rt_set_iteration(self._h, int(scheme)))
+
+    def set_wait_limit(self, polls):
+        """Polls before a Gauss-Seidel grid-barrier wait gives up (rt_set_wait_limit)."""
+        _check(load().rt_set_wait_limit(self._h, int(polls)))
 
     def set_interpolation(self, order):
         """Face interpolation: INTERP_LINEAR / "linear" or INTERP_QUADRATIC / "quadratic"."""

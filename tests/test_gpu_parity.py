@@ -2,14 +2,16 @@
 
 Tolerances: the FP64 path must match the oracle to 1e-5 relative (it agrees to
 round-off in practice, so the tests use 1e-8..1e-10).  The mixed path (float32
-sweeps, FP64 ALI) must match to 1e-3 relative in J and S, with a floor of 1e-5
-of the frequency bin's largest value (float32 rounding in a sweep is relative to
-the largest intensity in the stencil, so cells 1e6 dimmer than their neighbours
-carry absolute, not relative, float32 errors), and in the heating rate to
-|dQ| <= 1e-3 |Q| + 1e-4 * 4 pi chi_abs B (Q = 4 pi chi_abs (J - B) cancels where
-J ~ B; a fixed float32 error in J is amplified by about 1/eps in the diffusion
-regime).  The ALI iteration count must agree within one iteration.
+sweeps, FP64 ALI) must match to 1e-3 relative, cell by cell, in J, S and the
+diagonal of K and of the Eddington tensor f = K/J; the components that vanish
+by symmetry or cancel between rays (H, the off-diagonal K and f) to 1e-3 of J
+(of 1 for f); and the heating rate to |dQ| <= 1e-3 |Q| + 1e-6 * 4 pi chi_abs B
+(Q = 4 pi chi_abs (J - B) cancels where J ~ B).  The ALI iteration count must
+agree within one iteration.  Every converged-solve comparison reports the
+plain relative error of each output (``solve_errors``).
 """
+import json
+import os
 import math
 
 import numpy as np
@@ -48,12 +50,47 @@ def rel(a, b):
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
 
 
-def mixed_ok(x, ref, rtol=1e-3, floor=1e-5):
-    """|x - ref| <= rtol |ref| + floor * (largest |ref| of the frequency bin)."""
-    x = np.asarray(x)
-    ref = np.asarray(ref)
-    binmax = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1).reshape((-1,) + (1,) * (ref.ndim - 1))
-    return bool(np.all(np.abs(x - ref) <= rtol * np.abs(ref) + floor * binmax))
+def solve_errors(p, got, ref, iters, ref_iters):
+    """Errors of one converged solve against the oracle: plain max relative error
+    of S, J, K_xx..K_zz, f_xx..f_zz and Q; max error of H, K_xy.., f_xy.. over J
+    (over 1 for f); the iteration difference."""
+    e = {"iters": int(iters), "iters_oracle": int(ref_iters), "S": rel(got["S"], ref["S"]),
+         "J": rel(got["J"], ref["J"])}
+    J = np.abs(ref["J"])
+    names = ("xx", "yy", "zz", "xy", "xz", "yz")
+    for q in range(3):
+        e["H" + "xyz"[q] + "/J"] = float(np.max(np.abs(got["H"][:, q] - ref["H"][:, q]) / J))
+    for q in range(6):
+        if q < 3:
+            e["K" + names[q]] = rel(got["K"][:, q], ref["K"][:, q])
+            e["f" + names[q]] = rel(got["f"][:, q], ref["f"][:, q])
+        else:
+            e["K" + names[q] + "/J"] = float(np.max(np.abs(got["K"][:, q] - ref["K"][:, q]) / J))
+            e["f" + names[q]] = float(np.max(np.abs(got["f"][:, q] - ref["f"][:, q])))
+    emission = 4 * math.pi * np.sum(p.freq_w[:, None, None, None] * p.eps * p.chi * p.B, axis=0)
+    e["Q"] = rel(got["Q"], ref["Q"])
+    e["Q_gated"] = float(np.max(np.abs(got["Q"] - ref["Q"]) / (np.abs(ref["Q"]) + 1e-3 * emission + 1e-300)))
+    return e
+
+
+def gate(e, prec):
+    """The tolerances of the module docstring on the errors of ``solve_errors``."""
+    t = 1e-8 if prec == "fp64" else 1e-3
+    assert abs(e["iters"] - e["iters_oracle"]) <= 1, e
+    if prec == "fp64":
+        assert e["iters"] == e["iters_oracle"], e
+    for k, v in e.items():
+        if k in ("iters", "iters_oracle", "Q"):
+            continue
+        assert v < t, (k, v, e)
+
+
+def record(name, prec, e):
+    """Appends the errors to the file named by RT_SC_ERROR_TABLE (if set)."""
+    path = os.environ.get("RT_SC_ERROR_TABLE")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"case": name, "prec": prec, **e}) + "\n")
 
 
 # ------------------------------------------------------------- formal solution
@@ -118,38 +155,18 @@ def test_fixed_boundary_searchlight(rt):
 
 # ------------------------------------------------------------------ ALI solves
 
-def _compare_solve(rt, p, prec, tol=None, cfg=None, max_iter=3000):
+def _compare_solve(rt, p, prec, tol=None, cfg=None, max_iter=3000, nthreads=1):
     tol = p.tol if tol is None else tol
-    og, ref = O.solve_problem(p, tol=tol, max_iter=max_iter)
+    og, ref = O.solve_problem(p, tol=tol, max_iter=max_iter, nthreads=nthreads)
     g = make(rt, p, prec, **(cfg or {}))
     iters, resid, st = g.ali_solve(tol=tol, max_iter=max_iter)
     assert st == rt.RT_OK
-    assert abs(iters - ref["iters"]) <= 1, (iters, ref["iters"])
-    S = g.get_S()
-    m = g.moments()
-    t = TOL[prec]
-    if prec == "fp64":
-        assert iters == ref["iters"]
-        assert rel(S, ref["S"]) < 1e-8
-        assert rel(m["J"], ref["J"]) < 1e-8
-    else:
-        # both stop within delta_c of the same fixed point
-        assert mixed_ok(S, ref["S"]), rel(S, ref["S"])
-        assert mixed_ok(m["J"], ref["J"]), rel(m["J"], ref["J"])
-    H = m["H"]
-    for q in range(3):
-        scale = np.abs(ref["J"]).max()
-        assert np.abs(H[:, q] - ref["H"][:, q]).max() < t * scale
-    trK = m["K"][:, 0] + m["K"][:, 1] + m["K"][:, 2]
-    trKr = ref["K"][:, 0] + ref["K"][:, 1] + ref["K"][:, 2]
-    assert (rel(trK, trKr) < 1e-8) if prec == "fp64" else mixed_ok(trK, trKr)
-    np.testing.assert_allclose(m["f"][:, 0] + m["f"][:, 1] + m["f"][:, 2], 1.0, rtol=1e-5 if prec == "mixed" else 1e-12)
-    emission = 4 * math.pi * np.sum(p.freq_w[:, None, None, None] * p.eps * p.chi * p.B, axis=0)
-    dQ = np.abs(m["Q"] - ref["Q"])
-    if prec == "fp64":
-        assert np.all(dQ <= 1e-8 * np.abs(ref["Q"]) + 1e-10 * emission + 1e-300)
-    else:
-        assert np.all(dQ <= 1e-3 * np.abs(ref["Q"]) + 1e-4 * emission + 1e-300)
+    got = dict(g.moments(), S=g.get_S())
+    e = solve_errors(p, got, ref, iters, ref["iters"])
+    record(p.name, prec, e)
+    gate(e, prec)
+    np.testing.assert_allclose(got["f"][:, 0] + got["f"][:, 1] + got["f"][:, 2], 1.0,
+                               rtol=1e-5 if prec == "mixed" else 1e-12)
     return iters, ref["iters"]
 
 
@@ -171,13 +188,16 @@ def test_turbulent_box_small(rt, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_multifrequency_small(rt, prec):
     """Frequency-dependent absorption over 8 bins at 16^3 (all bins in one launch).
-    The high-frequency bins scatter almost purely (eps ~ 1e-6 in thick layers), so a
-    mixed grid must sweep those in FP64 (float32 error ~ unit roundoff / eps)."""
+    The high-frequency bins scatter almost purely (eps ~ 1e-6 in thick layers):
+    a mixed grid does the first formal solution of each solve in FP64 and sweeps
+    float32 increments after it, and solves the bins too ill-conditioned even
+    for those (unit roundoff / eps beyond the limit) in FP64."""
     p = W.multifrequency_atmosphere(16, nf=8)
     if prec == "mixed":
         g = make(rt, p, prec)
-        plan = g.sweep_plan()
-        assert 0 < plan["fp64_bins"] < p.nf, plan
+        assert 0 < g.sweep_plan()["fp64_bins"] < p.nf
+        g.ali_solve(tol=p.tol, max_iter=3000)
+        assert g.stats()["first_fp64"] == 1
     _compare_solve(rt, p, prec)
 
 
@@ -196,7 +216,7 @@ def test_mixed_converges_past_float32_floor(rt):
     iters, resid, st = g.ali_solve(tol=1e-9, max_iter=20000)
     assert st == rt.RT_OK and resid <= 1e-9
     assert abs(iters - ref["iters"]) <= 1, (iters, ref["iters"])
-    assert mixed_ok(g.get_S(), ref["S"])
+    assert rel(g.get_S(), ref["S"]) < 1e-3
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
