@@ -51,6 +51,8 @@ TOL = 1e-6
 FLOPS_PER_UPDATE = 34
 # special-function results per update: the exponential and the reciprocal of dtau
 MUFU_PER_UPDATE = 2
+# CTAs per cluster of every grid in the request server's shared-launch mode
+SHARED_CLUSTER = 4
 
 # DRAM read + write bytes per launch of the sweep kernel from an ncu capture of
 # the same workload and plan (None when none was taken for the plan in use, or
@@ -410,6 +412,13 @@ def run_gpu(args):
                                     "plan": gq.sweep_plan()}
         gq.close()
 
+    if not args.skip_extras and not args.skip_serve:
+        # the request stream (first 16 requests, 4 arrivals/s, the full eps range)
+        # through the server: each solve on its worker, then the shared-launch mode
+        extras["serving_16_requests"] = {
+            "per_worker_solves": serve_sample(rt, W, 16, 4.0, 4, 0),
+            "shared_launches": serve_sample(rt, W, 16, 4.0, 4, SHARED_CLUSTER)}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -472,17 +481,16 @@ def run_profile(args):
     return 0
 
 
-def run_serve(args):
-    """A sample of the mixed-size request stream through the request server:
-    Poisson arrivals at ``--rate`` requests/s, ``--workers`` solves in flight;
-    prints one JSON line with p50/p99 latency (arrival to result) and throughput."""
+def serve_sample(rt, W, n, rate, workers, shared_cluster=0, log=None):
+    """The first ``n`` requests of the mixed-size request stream (arrival seed 7,
+    Poisson arrivals at ``rate``/s, eps log-uniform in [1e-4, 1]) through the
+    request server; returns p50/p99 latency (arrival to result), aggregate
+    updates/s and solves/s."""
     import torch
-    torch.cuda.set_device(0)
-    from paper_1201_2222_gb300 import build, rt, workloads as W
-    build.build()
-    stream = W.serving_stream(args.serve, seed=7, rate=args.rate)
+    stream = W.serving_stream(n, seed=7, rate=rate)
     probs = [W.build_request(d) for d in stream]
-    srv = rt.Server(workers=args.workers)
+    srv = rt.Server(workers=workers, shared_cluster=shared_cluster)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     ids = []
     for d, p in zip(stream, probs):
@@ -494,23 +502,38 @@ def run_serve(args):
     for rid, t_sub, p in ids:
         info = srv.wait(rid, timeout=3600)
         srv.fetch(rid, raise_on_fail=False)
-        print(f"request {rid}: {p.name} iters {info['iters']} status {info['status']} "
-              f"queue {info['queue_ms']:.0f} ms solve {info['solve_ms']:.0f} ms", file=sys.stderr, flush=True)
+        if log:
+            print(f"request {rid}: {p.name} iters {info['iters']} status {info['status']} "
+                  f"queue {info['queue_ms']:.0f} ms solve {info['solve_ms']:.0f} ms", file=log, flush=True)
         bad += info["status"] != rt.RT_OK
         lat.append(info["queue_ms"] + info["solve_ms"])
         upd += p.cells * p.n_angles * p.nf * info["iters"]
         iters.append(info["iters"])
     wall = time.perf_counter() - t0
+    shared = srv.shared_launches()
     srv.close()
     lat = np.array(lat)
-    line = {"mode": "serve", "requests": len(ids), "workers": args.workers, "rate_per_s": args.rate,
-            "metric": METRIC, "value": upd / wall, "unit": UNIT, "solves_per_s": len(ids) / wall,
+    return {"requests": len(ids), "workers": workers, "shared_cluster": shared_cluster,
+            "rate_per_s": rate, "value": upd / wall, "unit": UNIT, "solves_per_s": len(ids) / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "failed": int(bad), "iters_median": float(np.median(iters)), "wall_s": wall,
-            "data": "synthetic", "dtype": "f32+f64",
-            "config": {"workload": f"serving stream sample: the first {len(ids)} requests (arrival seed 7) "
-                                   "of sizes 32^3..128^3 and 512x512 2D, 1/4/16 frequencies, 24/48/80 rays, "
-                                   "eps log-uniform in [1e-4, 1]"}}
+            "shared_launches": shared}
+
+
+def run_serve(args):
+    """A sample of the mixed-size request stream through the request server:
+    Poisson arrivals at ``--rate`` requests/s, ``--workers`` worker threads
+    (``--shared C``: the shared-launch mode with C CTAs per cluster); prints one
+    JSON line with p50/p99 latency (arrival to result) and throughput."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1201_2222_gb300 import build, rt, workloads as W
+    build.build()
+    res = serve_sample(rt, W, args.serve, args.rate, args.workers, args.shared, log=sys.stderr)
+    line = {"mode": "serve", "metric": METRIC, **res, "data": "synthetic", "dtype": "f32+f64",
+            "config": {"workload": f"serving stream sample: the first {res['requests']} requests (arrival "
+                                   "seed 7) of sizes 32^3..128^3 and 512x512 2D, 1/4/16 frequencies, "
+                                   "24/48/80 rays, eps log-uniform in [1e-4, 1]"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -537,7 +560,10 @@ def main(argv=None):
     ap.add_argument("--plan", default="", help="sweep plan variant,rays_per_group,cluster[,threads] instead of autotuning")
     ap.add_argument("--serve", type=int, default=0, help="run N requests of the serving stream instead")
     ap.add_argument("--rate", type=float, default=2.0, help="with --serve: arrivals per second")
-    ap.add_argument("--workers", type=int, default=4, help="with --serve: solves in flight")
+    ap.add_argument("--workers", type=int, default=4, help="with --serve: worker threads")
+    ap.add_argument("--shared", type=int, default=0,
+                    help="with --serve: shared-launch mode with this many CTAs per cluster (0: off)")
+    ap.add_argument("--skip-serve", action="store_true", help="omit the request-stream sample")
     args = ap.parse_args(argv)
     if args.serve:
         return run_serve(args)

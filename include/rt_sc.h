@@ -75,10 +75,16 @@ typedef enum { RT_BC_PERIODIC = 0, RT_BC_VACUUM = 1, RT_BC_THERMAL = 2, RT_BC_FI
  *          change of S in float32, accumulating J in FP64, so that float32
  *          rounding scales with the update, not with S.  The Jacobi update still
  *          amplifies the increments' rounding by about 1/eps in optically thick
- *          cells (measured: max relative error of S about 1.6e-8 / eps), so
- *          frequency bins whose smallest eps among optically thick cells is
- *          below 1.2e-4 (unit roundoff / eps > 5e-4) are solved in FP64 by an
- *          internal FP64 grid of those bins (rt_get_sweep_plan reports how many). */
+ *          cells (measured without the later FP64 iterations: max relative error
+ *          of S about 1.6e-8 / eps), so each time the largest relative change of S
+ *          has fallen 100-fold another iteration is done in FP64, whose J replaces
+ *          the accumulated one (rt_set_fp64_anchors; the errors then fall to
+ *          1e-9..1e-6 on the benchmark media), and frequency bins whose smallest
+ *          eps among optically thick cells is below 1.2e-4 (unit roundoff / eps >
+ *          5e-4, rt_set_fp64_bin_limit) are solved in FP64 by an internal FP64
+ *          grid of those bins (rt_get_sweep_plan reports how many): there the
+ *          FP64 iterations would have to come so often, to keep the iteration
+ *          count within one of the FP64 solve's, that they would cost as much. */
 typedef enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 } rt_precision;
 
 typedef struct {
@@ -162,6 +168,25 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
 rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
                        int *iters_out, double *resid_out);
 
+/* The Jacobi ALI solves (Eqs. 24-25) of n grids together, each from S = B with
+ * the same iterates, results and iteration count as rt_ali_solve would give it
+ * (bit for bit), with the sweeps of grids that can share a launch merged: every
+ * iteration, one launch sweeps all grids with the pipelined sweep (variant 3:
+ * the mixed default) of the same precision and cluster size (rt_set_sweep_config
+ * sets it; rows of a multiple of 4 cells or not) -- up to 24 grids per launch --
+ * and the other grids' sweeps are launched one by one; then each grid's update.
+ * Grids leave as they finish; each keeps its own host-check schedule (as in
+ * rt_ali_solve).  All work runs on opts->stream (NULL: the first grid's own
+ * stream).  opts (may be NULL) applies to every grid.  iters, resid, status:
+ * per grid (each may be NULL).  No counterpart in the paper: many small
+ * problems then fill the GPU as one large one does.  Errors: RT_ERR_ARG for a
+ * NULL grid; RT_ERR_STATE for a grid without medium, with the Gauss-Seidel
+ * iteration or with quadratic interpolation (before any solve); otherwise the
+ * first failing grid's status (RT_ERR_NOT_CONVERGED where max_iter ran out;
+ * the other grids still finish). */
+rt_status rt_ali_solve_many(rt_grid *grids, int n, const rt_solve_opts *opts, int *iters, double *resid,
+                            int *status);
+
 /* Outputs of the last formal solution of the latest solve (Sec. 4): J [nf][cells],
  * H [nf][3][cells], K [nf][6][cells] (xx, yy, zz, xy, xz, yz), the variable
  * Eddington tensor f = K/J [nf][6][cells], and the heating rate Q [cells] in the
@@ -229,6 +254,26 @@ rt_status rt_set_iteration(rt_grid g, int scheme);
  * to exercise the path.  Errors: RT_ERR_ARG for a negative limit. */
 rt_status rt_set_wait_limit(rt_grid g, long long polls);
 
+/* Mixed grids, Jacobi ALI solves with linear interpolation: after the first
+ * (FP64) iteration, another iteration is done in FP64 from the current S each
+ * time the largest relative change of S (Eq. 25) has fallen by the factor
+ * `drop` since the last one (checked between batches of iterations; default
+ * 1e-2; 0 disables).  Its J replaces the J accumulated in FP64 from the float32
+ * increments, dropping the rounding they carried so far; without it that
+ * rounding biases the converged S by about unit roundoff / eps in optically
+ * thick cells, which the heating rate's cancellation J - B shows where J is
+ * close to B.  The iteration count is unchanged (an FP64 iteration replaces a
+ * float32 one).  Errors: RT_ERR_ARG for drop outside [0, 1). */
+rt_status rt_set_fp64_anchors(rt_grid g, double drop);
+
+/* Mixed grids: the limit on unit roundoff / (smallest eps among optically thick
+ * cells) above which a frequency bin is solved by the internal FP64 grid of
+ * such bins (see RT_PREC_MIXED; default 5e-4).  Takes effect at the next
+ * rt_set_opacity_source.  INFINITY keeps every bin in float32; 0 moves every
+ * bin with an optically thick cell to FP64.  Errors: RT_ERR_ARG for a negative
+ * or NaN limit. */
+rt_status rt_set_fp64_bin_limit(rt_grid g, double limit);
+
 /* Form of the heating rate Q returned by rt_moments (Sec. 4).
  *   RT_HEAT_INTEGRAL:     Q = 4 pi sum_nu w_nu chi_abs,nu (J_nu - B_nu), chi_abs = eps chi.
  *   RT_HEAT_DIFFERENTIAL: Q = -4 pi sum_nu w_nu div H_nu, div H from centred
@@ -293,6 +338,10 @@ typedef struct {
   long long graph_launches; /* ALI batches replayed as CUDA graphs (cumulative) */
   int first_fp64;           /* 1 if the latest ALI solve (mixed grid) did its first formal
                                solution in FP64 (see RT_PREC_MIXED) */
+  int fp64_anchors;         /* later iterations of that solve done in FP64
+                               (rt_set_fp64_anchors) */
+  long long shared_launches; /* sweeps launched together with other grids' sweeps
+                               (rt_ali_solve_many, the server's shared mode; cumulative) */
 } rt_stats;
 rt_status rt_enable_timing(rt_grid g, int enable);
 rt_status rt_get_stats(rt_grid g, rt_stats *out);
@@ -363,11 +412,21 @@ rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const double *chi, c
  * worker's own CUDA stream, solves, takes J, S and Q back to host memory and
  * frees the grid.  Solves on different workers overlap on the GPU; each result
  * is the same as that of the same solve run alone (deterministic kernels and a
- * plan that depends on the problem only).  All calls are thread-safe. */
+ * plan that depends on the problem only; in the shared mode, alone with the
+ * server's cluster size set by rt_set_sweep_config).  All calls are
+ * thread-safe. */
 typedef struct rt_server_s *rt_server;
 typedef struct {
   long long device_bytes;   /* admission budget; <= 0: 80 % of the free device memory */
-  int workers;              /* solves in flight at most (>= 1) */
+  int workers;              /* worker threads (>= 1): solves in flight at most, or, in the
+                               shared mode, grids being set up or read back at once */
+  int shared_cluster;       /* 0: each solve on its worker.  1..16: shared mode -- every
+                               admitted Jacobi solve with linear interpolation runs in
+                               lock-step with the others on one scheduler thread, as in
+                               rt_ali_solve_many, each grid planned with this many CTAs per
+                               cluster where that plan fits; the workers set grids up and
+                               read results back (Gauss-Seidel and quadratic requests still
+                               run on a worker) */
 } rt_server_opts;
 typedef struct {
   rt_grid_desc desc;
@@ -393,6 +452,8 @@ typedef struct {
  * arrays it allocates, with the moments pass).  Errors: RT_ERR_ARG. */
 rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes);
 rt_status rt_server_create(const rt_server_opts *opts, rt_server *out);
+/* Shared sweep launches issued by the server's scheduler so far (shared mode). */
+rt_status rt_server_shared_launches(rt_server s, long long *n);
 /* Waits for the running solves; queued ones are dropped. */
 rt_status rt_server_destroy(rt_server s);
 /* Copies the request's inputs and queues it.  Errors: RT_ERR_ARG (NULL or bad

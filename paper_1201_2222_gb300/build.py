@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["rt_api.cu", "rt_kernels.cu", "rt_quad.cu", "rt_server.cu", "rt_gs.cu", "rt_probe.cu"]
-HEADERS = ["rt_common.cuh", "rt_kernels.h", "rt_device.cuh"]
+HEADERS = ["rt_common.cuh", "rt_kernels.h", "rt_device.cuh", "rt_lockstep.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

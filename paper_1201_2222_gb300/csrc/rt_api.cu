@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <limits>
 #include <mutex>
@@ -18,6 +19,7 @@
 
 #include "rt_common.cuh"
 #include "rt_kernels.h"
+#include "rt_lockstep.h"
 #include "rt_sc.h"
 
 using rtk::AngleParam;
@@ -308,6 +310,10 @@ struct rt_grid_s {
   // scales with the update, and J is accumulated in FP64
   rt_grid first64 = nullptr;
   bool fp64_first = false;
+  // ... and, whenever the largest relative change of S has fallen by this factor
+  // since the last FP64 formal solution, one more iteration in FP64 from the
+  // current S, whose J replaces the accumulated one (0: none after the first)
+  double anchor_drop = 1e-2;
   bool shadow = false;                // this grid is another grid's FP64 first-solution shadow
   bool stepped = false;               // an ALI solve begun by rt_ali_begin may be continued
   // Mixed grids: frequency bins too ill-conditioned for float32 even as
@@ -423,6 +429,7 @@ int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)
 // Largest CTA of a sweep variant in the grid's precision.
 int sweep_thread_cap(rt_grid g, int variant) {
   if (variant == 1) return 512;
+  if (g->interp == RT_INTERP_QUADRATIC) return rtk::kQuadThreads;
   return g->desc.prec == RT_PREC_FP64 ? rtk::sweep_max_threads<double>() : rtk::sweep_max_threads<float>();
 }
 
@@ -944,6 +951,80 @@ rt_status gs_setup(rt_grid g, cudaStream_t s, bool incremental, rtk::GsArgs<T> &
   return RT_OK;
 }
 
+// Sweep and Jacobi-update arguments of an ALI solve of g with the pipelined or
+// one-cell-per-thread sweep (the Gauss-Seidel forward-phase flags are set by the
+// caller).  The float32 pipelined sweep writes the partials of the groups
+// sweeping along x (the first groups) in their plane layout, which the Jacobi
+// update reads.
+template <typename T>
+void solve_args(rt_grid g, int incremental, bool gs, rtk::SweepArgs<T> &A, rtk::AliArgs<T> &L) {
+  A = sweep_args<T>(g);
+  A.incremental = incremental;
+  int nxg = 0;
+  if (sizeof(T) == 4 && !gs && g->variant == 3 && g->interp == RT_INTERP_LINEAR && g->d.n[0] % 4 == 0 &&
+      g->d.n[1] % 4 == 0) {
+    while (nxg < (int)g->groups.size() && g->groups[nxg].axis == 0) ++nxg;
+    A.jx = 1;
+  }
+  L = rtk::AliArgs<T>{};
+  L.d = g->d;
+  L.ngroups_per_f = (int)g->groups.size();
+  L.Jpart = (const T *)g->Jpart;
+  L.eps = g->eps;
+  L.B = g->B;
+  L.iden = g->iden;
+  L.Opart = g->interp == RT_INTERP_QUADRATIC ? (const T *)g->Opart : nullptr;
+  L.S64 = g->S;
+  L.Sfs = g->Sfs;
+  L.J64 = g->J;
+  L.Jprev = g->Jprev;
+  for (int a = 0; a < 3; ++a) L.SP[a] = g->used_axis[a] ? (T *)g->SP[a] : nullptr;
+  L.st = g->st;
+  L.lte = g->lte ? 1 : 0;
+  L.incremental = incremental;
+  L.fmask = g->fmask;
+  L.nxg = nxg;
+}
+
+template <typename T>
+rt_status formal_once(rt_grid g, cudaStream_t s);
+
+// One Jacobi iteration of a mixed grid whose formal solution is done in FP64 by
+// the internal FP64 grid, from the current S: the first iteration of a solve
+// (ghosts from S, as for every first formal solution) or a later one (the lagged
+// ghosts taken from this grid's current float32 ghosts, prev = their parity).
+// J64 receives the FP64 J, this grid's next ghosts and their change the FP64
+// outflow; then the update and the decision.  The float32 increments that
+// follow start from this J: the rounding accumulated in J64 so far is dropped.
+rt_status fp64_iteration(rt_grid g, const rtk::AliArgs<float> &L, int prev, bool first, cudaStream_t s) {
+  rt_grid h = g->first64;
+  const long long ng = (long long)g->d.nf * g->na * g->d.gsize;
+  rt_status r;
+  if (first) {
+    rt_solve_opts o2{};
+    o2.stream = (void *)s;
+    if ((r = rt_formal_solve(h, g->S, g->J, nullptr, 1, &o2)) != RT_OK) return r;
+  } else {
+    const size_t N = (size_t)N_of(g);
+    CU(cudaMemcpyAsync(h->S, g->S, N * 8, cudaMemcpyDeviceToDevice, s));
+    if ((r = permute_any(h, h->S, h->SP, s)) != RT_OK) return r;
+    CU(rtk::launch_f32_to_f64(ng, (const float *)g->G[prev], (double *)h->G[0], s));
+    CU(rtk::launch_state_op(h->st, 2, 0, 0.0, 0, s));
+    h->fs_total = 0;
+    h->launches += 2;
+    if ((r = formal_once<double>(h, s)) != RT_OK) return r;
+    CU(cudaMemcpyAsync(g->J, h->J, N * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  CU(rtk::launch_ghosts_from64(ng, (const double *)h->G[1], (const double *)h->G[0], (float *)g->G[prev ^ 1],
+                               (float *)g->Gd[prev ^ 1], s));
+  rtk::AliArgs<float> L0 = L;
+  L0.Jpart = nullptr;
+  CU(rtk::launch_ali<float>(L0, s));
+  CU(rtk::launch_finish(g->st, s));
+  g->launches += 3;
+  return RT_OK;
+}
+
 template <typename T>
 rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *iters, double *resid,
                    bool *converged) {
@@ -966,39 +1047,14 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     rt_status r = ensure_seg_table<T>(g, s);
     if (r != RT_OK) return r;
   }
-  rtk::SweepArgs<T> A = sweep_args<T>(g);
-  A.incremental = incremental;
+  rtk::SweepArgs<T> A;
+  rtk::AliArgs<T> L;
+  solve_args<T>(g, incremental, gs, A, L);
   if (gs) {
     A.gs_forward = 1;
     A.gs_axis = GA.V;
     GA.A = A;
   }
-  // the float32 pipelined sweep writes the partials of the groups sweeping along
-  // x (the first groups) in their plane layout, which the Jacobi update reads
-  int nxg = 0;
-  if (sizeof(T) == 4 && !gs && g->variant == 3 && g->interp == RT_INTERP_LINEAR && g->d.n[0] % 4 == 0 &&
-      g->d.n[1] % 4 == 0) {
-    while (nxg < (int)g->groups.size() && g->groups[nxg].axis == 0) ++nxg;
-    A.jx = 1;
-  }
-  rtk::AliArgs<T> L{};
-  L.d = g->d;
-  L.ngroups_per_f = (int)g->groups.size();
-  L.Jpart = (const T *)g->Jpart;
-  L.eps = g->eps;
-  L.B = g->B;
-  L.iden = g->iden;
-  L.Opart = g->interp == RT_INTERP_QUADRATIC ? (const T *)g->Opart : nullptr;
-  L.S64 = g->S;
-  L.Sfs = g->Sfs;
-  L.J64 = g->J;
-  L.Jprev = g->Jprev;
-  for (int a = 0; a < 3; ++a) L.SP[a] = g->used_axis[a] ? (T *)g->SP[a] : nullptr;
-  L.st = g->st;
-  L.lte = g->lte ? 1 : 0;
-  L.incremental = incremental;
-  L.fmask = g->fmask;
-  L.nxg = nxg;
   std::vector<EventPair> ev;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (g->timing) {
@@ -1008,23 +1064,16 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
   }
   int enqueued = 0, batch = opts && opts->check_every > 0 ? opts->check_every : 4;
   g->stats.first_fp64 = 0;
+  g->stats.fp64_anchors = 0;
+  // mixed Jacobi solves: FP64 iterations (the first, then one each time the
+  // residual has fallen by anchor_drop since the last), float32 increments between
+  const bool fp64_its = sizeof(T) == 4 && g->fp64_first && g->first64 && incremental && !gs && !g->lte;
+  double anchor_ref = -1.0;
+  bool anchor_next = false;
   if constexpr (sizeof(T) == 4) {
-    if (g->fp64_first && g->first64 && incremental && !gs && !g->lte && max_iter > 0) {
-      // The first formal solution in FP64 (the internal FP64 grid, from the same S
-      // and first-iteration ghosts) into J64, its outflow ghosts and their change
-      // into this grid's ghost buffers, then the first update with that J
-      rt_solve_opts o2{};
-      o2.stream = (void *)s;
-      rt_status r = rt_formal_solve(g->first64, g->S, g->J, nullptr, 1, &o2);
+    if (fp64_its && max_iter > 0) {
+      rt_status r = fp64_iteration(g, L, 0, true, s);
       if (r != RT_OK) return r;
-      const long long ng = (long long)g->d.nf * g->na * g->d.gsize;
-      CU(rtk::launch_ghosts_from64(ng, (const double *)g->first64->G[1], (const double *)g->first64->G[0],
-                                   (float *)g->G[1], (float *)g->Gd[1], s));
-      rtk::AliArgs<T> L0 = L;
-      L0.Jpart = nullptr;
-      CU(rtk::launch_ali<T>(L0, s));
-      CU(rtk::launch_finish(g->st, s));
-      g->launches += 3;
       enqueued = 1;
       g->stats.first_fp64 = 1;
     }
@@ -1084,7 +1133,17 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     return &g->graphs.back();
   };
   while (true) {
-    const int m = std::min(batch, max_iter - enqueued);
+    int m = std::min(batch, max_iter - enqueued);
+    if constexpr (sizeof(T) == 4) {
+      if (anchor_next && m > 0) {   // this batch begins with an FP64 iteration
+        rt_status r = fp64_iteration(g, L, (hs.fs_count + A.parity_offset) & 1, false, s);
+        if (r != RT_OK) return r;
+        ++enqueued;
+        --m;
+        g->stats.fp64_anchors++;
+        anchor_next = false;
+      }
+    }
     const rt_grid_s::Graph *gr = (m > 0 && enqueued > 0 && !g->timing && g->graphs_ok) ? graph_for(m) : nullptr;
     if (gr) {
       CU(cudaGraphLaunch(gr->exec, s));
@@ -1099,6 +1158,14 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     CU(cudaStreamSynchronize(s));
     if (hs.err) return fail(RT_ERR_CUDA, "device check failed (code %d, index %d)", hs.err, hs.err_info);
     if (hs.done || enqueued >= max_iter) break;
+    if (fp64_its && g->anchor_drop > 0.0) {
+      if (anchor_ref < 0.0) {
+        anchor_ref = hs.last_resid;
+      } else if (hs.last_resid <= anchor_ref * g->anchor_drop) {
+        anchor_next = true;
+        anchor_ref = hs.last_resid;
+      }
+    }
     if (!(opts && opts->check_every > 0)) batch = std::min(batch * 2, 64);
   }
   if (g->timing) {
@@ -1110,7 +1177,7 @@ rt_status ali_loop(rt_grid g, const rt_solve_opts *opts, cudaStream_t s, int *it
     cudaEventDestroy(t1);
     g->stats.total_ms = tt;
     rt_status r = collect_events(ev, &g->stats.sweep_ms, &g->stats.sweep_launches,
-                                 (size_t)std::max(0, hs.iter - g->stats.first_fp64));
+                                 (size_t)std::max(0, hs.iter - g->stats.first_fp64 - g->stats.fp64_anchors));
     if (r != RT_OK) return r;
   }
   *iters = hs.iter;
@@ -1686,14 +1753,8 @@ rt_status rt_formal_solve(rt_grid g, const double *S, double *J_out, double *lst
   return RT_OK;
 }
 
-rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
-                       int *iters_out, double *resid_out) {
-  if (!g) return fail(RT_ERR_ARG, "NULL grid");
-  g->stepped = false;
-  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
-  if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
-  cudaStream_t s = pick_stream(g, opts);
-  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+// An ALI solve's start: S = S_init (or B), its sweep copies and the first ghosts.
+static rt_status solve_prologue(rt_grid g, const double *S_init, int on_device, cudaStream_t s) {
   const size_t N = (size_t)N_of(g);
   rt_status r;
   if (S_init) {
@@ -1702,14 +1763,15 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
     CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
   }
   if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
-  if ((r = init_ghosts_any(g, g->S, s)) != RT_OK) return r;
-  int iters = 0;
-  double resid = 0.0;
-  bool conv = false;
-  r = g->desc.prec == RT_PREC_FP64 ? ali_loop<double>(g, opts, s, &iters, &resid, &conv)
-                                   : ali_loop<float>(g, opts, s, &iters, &resid, &conv);
-  if (r != RT_OK) return r;
-  if (g->sub64) {   // FP64 bins, then their S, J and last-formal-solution S merged back
+  return init_ghosts_any(g, g->S, s);
+}
+
+// An ALI solve's end: the FP64 bins of a mixed grid solved by their FP64 grid and
+// their S, J and last-formal-solution S merged back; the statistics.
+static rt_status solve_epilogue(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
+                         cudaStream_t s, int *iters, double *resid, bool *conv) {
+  rt_status r;
+  if (g->sub64) {
     const size_t C = (size_t)g->d.cells, m = g->bins64.size();
     if ((r = ensure_tmp2(g, m * C)) != RT_OK) return r;
     const double *Ssub = nullptr;
@@ -1726,23 +1788,43 @@ rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_
     double res2 = 0.0;
     r = rt_ali_solve(g->sub64, Ssub, 1, &o2, &it2, &res2);
     if (r != RT_OK && r != RT_ERR_NOT_CONVERGED) return r;
-    if (r == RT_ERR_NOT_CONVERGED) conv = false;
-    iters = std::max(iters, it2);
-    resid = std::max(resid, res2);
+    if (r == RT_ERR_NOT_CONVERGED) *conv = false;
+    *iters = std::max(*iters, it2);
+    *resid = std::max(*resid, res2);
     if ((r = move_bins(g->bins64, g->sub64->S, g->S, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
     if ((r = move_bins(g->bins64, g->sub64->J, g->J, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
     if ((r = move_bins(g->bins64, g->sub64->Sfs, g->Sfs, C, false, cudaMemcpyDeviceToDevice, s)) != RT_OK) return r;
     CU(cudaStreamSynchronize(s));
     g->stats.sweep_ms += g->sub64->stats.sweep_ms;
   }
+  g->stats.iters = *iters;
+  g->stats.resid = *resid;
+  g->stats.updates = (long long)g->d.cells * g->na * g->d.nf * *iters;
+  g->stats.kernel_launches = g->launches;
+  if (!*conv) return fail(RT_ERR_NOT_CONVERGED, "not converged after %d formal solutions (residual %g)", *iters, *resid);
+  return RT_OK;
+}
+
+rt_status rt_ali_solve(rt_grid g, const double *S_init, int on_device, const rt_solve_opts *opts,
+                       int *iters_out, double *resid_out) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  g->stepped = false;
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
+  cudaStream_t s = pick_stream(g, opts);
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  rt_status r = solve_prologue(g, S_init, on_device, s);
+  if (r != RT_OK) return r;
+  int iters = 0;
+  double resid = 0.0;
+  bool conv = false;
+  r = g->desc.prec == RT_PREC_FP64 ? ali_loop<double>(g, opts, s, &iters, &resid, &conv)
+                                   : ali_loop<float>(g, opts, s, &iters, &resid, &conv);
+  if (r != RT_OK) return r;
+  r = solve_epilogue(g, S_init, on_device, opts, s, &iters, &resid, &conv);
   if (iters_out) *iters_out = iters;
   if (resid_out) *resid_out = resid;
-  g->stats.iters = iters;
-  g->stats.resid = resid;
-  g->stats.updates = (long long)g->d.cells * g->na * g->d.nf * iters;
-  g->stats.kernel_launches = g->launches;
-  if (!conv) return fail(RT_ERR_NOT_CONVERGED, "not converged after %d formal solutions (residual %g)", iters, resid);
-  return RT_OK;
+  return r;
 }
 
 rt_status rt_moments(rt_grid g, double *J, double *H, double *K, double *f, double *Q, int on_device,
@@ -1944,6 +2026,20 @@ rt_status rt_set_wait_limit(rt_grid g, long long polls) {
   return RT_OK;
 }
 
+rt_status rt_set_fp64_anchors(rt_grid g, double drop) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!(drop >= 0.0 && drop < 1.0)) return fail(RT_ERR_ARG, "drop must be in [0, 1)");
+  g->anchor_drop = drop;
+  return RT_OK;
+}
+
+rt_status rt_set_fp64_bin_limit(rt_grid g, double limit) {
+  if (!g) return fail(RT_ERR_ARG, "NULL grid");
+  if (!(limit >= 0.0)) return fail(RT_ERR_ARG, "the limit must be >= 0");
+  g->bin_limit = limit;
+  return RT_OK;
+}
+
 rt_status rt_set_heating_form(rt_grid g, int form) {
   if (!g) return fail(RT_ERR_ARG, "NULL grid");
   if (form != RT_HEAT_INTEGRAL && form != RT_HEAT_DIFFERENTIAL && form != RT_HEAT_SWITCH)
@@ -2102,6 +2198,304 @@ rt_status rt_get_stats(rt_grid g, rt_stats *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------- lock-step solves
+// Jacobi ALI solves of several grids advanced together on one stream.  Every
+// iteration: one shared sweep launch per set of grids whose pipelined sweeps can
+// share a launch (same precision, cluster size and row vectorisation; up to
+// kMultiMax grids each), a launch of its own for any other grid's sweep, then
+// each grid's Jacobi update and decision.  Each grid goes through the same
+// iterations as rt_ali_solve: the same kernels on the same data (a cell's
+// arithmetic does not depend on the CTA size or on the other grids of the
+// launch), its host checks after the same iterations (batches of 4, doubling to
+// 64, or check_every) and so its FP64 iterations on the same iterations -- the
+// results are the same bit for bit.  The step runs up to the nearest check of
+// any member, so members that began at different times are checked on their
+// own schedules.
+struct LsMember {
+  rt_grid g = nullptr;
+  void *tag = nullptr;
+  rt_solve_opts opts{};
+  int max_iter = 1000;
+  bool f32 = false;
+  int incremental = 0;
+  rtk::SweepArgs<float> Af{};
+  rtk::AliArgs<float> Lf{};
+  rtk::SweepArgs<double> Ad{};
+  rtk::AliArgs<double> Ld{};
+  int enqueued = 0, batch = 4, next_check = 0;
+  bool fp64_its = false, anchor_next = false;
+  double anchor_ref = -1.0;
+  rtk::SolveState hs{};
+};
+
+struct rt_lockstep_s {
+  cudaStream_t s = nullptr;
+  std::vector<LsMember *> m;
+  rtk::SolveState *hs = nullptr;   // pinned, one per member
+  size_t hs_cap = 0;
+  long long shared = 0;
+};
+
+rt_status ls_create(cudaStream_t s, rt_lockstep *out) {
+  if (!out) return fail(RT_ERR_ARG, "NULL out");
+  rt_lockstep L = new rt_lockstep_s();
+  L->s = s;
+  *out = L;
+  return RT_OK;
+}
+
+void ls_destroy(rt_lockstep L) {
+  if (!L) return;
+  for (LsMember *x : L->m) delete x;
+  if (L->hs) cudaFreeHost(L->hs);
+  delete L;
+}
+
+size_t ls_size(rt_lockstep L) { return L ? L->m.size() : 0; }
+long long ls_shared_launches(rt_lockstep L) { return L ? L->shared : 0; }
+
+rt_status ls_add(rt_lockstep L, rt_grid g, const rt_solve_opts *opts, void *tag) {
+  if (!L || !g) return fail(RT_ERR_ARG, "NULL argument");
+  if (!g->have_medium) return fail(RT_ERR_STATE, "rt_set_opacity_source has not succeeded");
+  if (g->iteration == RT_ITER_GAUSS_SEIDEL || g->interp != RT_INTERP_LINEAR)
+    return fail(RT_ERR_STATE, "lock-step solves take the Jacobi iteration with linear interpolation");
+  if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
+  g->stepped = false;
+  cudaStream_t s = L->s;
+  if (s != g->own) CU(cudaStreamSynchronize(g->own));
+  rt_status r = solve_prologue(g, nullptr, 0, s);
+  if (r != RT_OK) return r;
+  LsMember *x = new LsMember();
+  x->g = g;
+  x->tag = tag;
+  x->opts = opts ? *opts : rt_solve_opts{1e-6, 1000, 0, nullptr};
+  x->opts.stream = (void *)s;
+  x->max_iter = x->opts.max_iter > 0 ? x->opts.max_iter : 1000;
+  x->f32 = g->desc.prec == RT_PREC_MIXED;
+  x->incremental = x->f32 ? 1 : 0;
+  x->batch = x->opts.check_every > 0 ? x->opts.check_every : 4;
+  auto bail = [&](rt_status e) { delete x; return e; };
+  if (cudaSuccess != rtk::launch_state_op(g->st, 0, x->max_iter, x->opts.tol, g->lte ? 1 : 0, s))
+    return bail(fail(RT_ERR_CUDA, "state reset launch failed"));
+  g->launches++;
+  g->stats.first_fp64 = 0;
+  g->stats.fp64_anchors = 0;
+  if (x->f32) {
+    if ((r = ensure_seg_table<float>(g, s)) != RT_OK) return bail(r);
+    solve_args<float>(g, x->incremental, false, x->Af, x->Lf);
+    x->fp64_its = g->fp64_first && g->first64 && !g->lte;
+    if (x->fp64_its) {
+      if ((r = fp64_iteration(g, x->Lf, 0, true, s)) != RT_OK) return bail(r);
+      x->enqueued = 1;
+      g->stats.first_fp64 = 1;
+    }
+  } else {
+    if ((r = ensure_seg_table<double>(g, s)) != RT_OK) return bail(r);
+    solve_args<double>(g, 0, false, x->Ad, x->Ld);
+  }
+  x->next_check = x->enqueued + std::min(x->batch, x->max_iter - x->enqueued);
+  L->m.push_back(x);
+  return RT_OK;
+}
+
+namespace {
+
+bool ls_mergeable(const LsMember *x) { return x->g->variant == 3; }
+
+// shared launches of the pipelined sweeps of members `idx` (one precision)
+template <typename T>
+rt_status ls_sweep_shared(rt_lockstep L, const std::vector<LsMember *> &idx) {
+  // sets of the same cluster size and vectorisation
+  std::vector<bool> used(idx.size(), false);
+  for (size_t i = 0; i < idx.size(); ++i) {
+    if (used[i]) continue;
+    const rt_grid g0 = idx[i]->g;
+    // (rows of every sweep axis a multiple of 4 cells: the float32 kernel's 128-bit rows)
+    const bool v0 = sizeof(T) == 4 && g0->d.n[0] % 4 == 0 && g0->d.n[1] % 4 == 0;
+    std::vector<LsMember *> set;
+    for (size_t j = i; j < idx.size(); ++j) {
+      const rt_grid gj = idx[j]->g;
+      const bool vj = sizeof(T) == 4 && gj->d.n[0] % 4 == 0 && gj->d.n[1] % 4 == 0;
+      if (!used[j] && gj->cluster == g0->cluster && vj == v0) {
+        used[j] = true;
+        set.push_back(idx[j]);
+      }
+    }
+    for (size_t k0 = 0; k0 < set.size(); k0 += rtk::kMultiMax) {
+      const size_t k1 = std::min(set.size(), k0 + rtk::kMultiMax);
+      rtk::MultiSweep<T> M{};
+      M.n = (int)(k1 - k0);
+      M.base[0] = 0;
+      int amax = 1, threads = 32;
+      size_t smem = 0;
+      for (size_t k = k0; k < k1; ++k) {
+        LsMember *x = set[k];
+        const int q = (int)(k - k0);
+        if constexpr (sizeof(T) == 4) M.a[q] = x->Af;
+        else M.a[q] = x->Ad;
+        M.base[q + 1] = M.base[q] + (int)x->g->groups.size() * x->g->d.nf;
+        amax = std::max(amax, x->g->amax);
+        threads = std::max(threads, x->g->threads);
+        smem = std::max(smem, x->g->smem);
+        x->g->launches++;
+        if (M.n > 1) x->g->stats.shared_launches++;
+      }
+      CU(rtk::launch_sweep_multi<T>(M, amax, threads, smem, L->s));
+      L->shared++;
+    }
+  }
+  return RT_OK;
+}
+
+template <typename T>
+rt_status ls_update(LsMember *x, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) CU(rtk::launch_ali<float>(x->Lf, s));
+  else CU(rtk::launch_ali<double>(x->Ld, s));
+  CU(rtk::launch_finish(x->g->st, s));
+  x->g->launches += 2;
+  return RT_OK;
+}
+
+}  // namespace
+
+rt_status ls_step(rt_lockstep L, std::vector<LsResult> *done) {
+  if (!L) return fail(RT_ERR_ARG, "NULL lock-step set");
+  cudaStream_t s = L->s;
+  int m = INT_MAX;
+  for (LsMember *x : L->m) m = std::min(m, x->next_check - x->enqueued);
+  if (L->m.empty()) m = 0;
+  for (int it = 0; it < m; ++it) {
+    std::vector<LsMember *> sh32, sh64, own;
+    for (LsMember *x : L->m) {
+      if (it == 0 && x->anchor_next) {   // this batch of x begins with an FP64 iteration
+        rt_status r = fp64_iteration(x->g, x->Lf, (x->hs.fs_count + x->Af.parity_offset) & 1, false, s);
+        if (r != RT_OK) return r;
+        x->g->stats.fp64_anchors++;
+        x->anchor_next = false;
+        x->enqueued++;
+        continue;
+      }
+      (ls_mergeable(x) ? (x->f32 ? sh32 : sh64) : own).push_back(x);
+    }
+    rt_status r;
+    if (!sh32.empty() && (r = ls_sweep_shared<float>(L, sh32)) != RT_OK) return r;
+    if (!sh64.empty() && (r = ls_sweep_shared<double>(L, sh64)) != RT_OK) return r;
+    for (LsMember *x : own) {
+      r = x->f32 ? enqueue_sweep<float>(x->g, x->Af, false, s, nullptr)
+                 : enqueue_sweep<double>(x->g, x->Ad, false, s, nullptr);
+      if (r != RT_OK) return r;
+    }
+    for (auto *v : {&sh32, &sh64, &own})
+      for (LsMember *x : *v) {
+        r = x->f32 ? ls_update<float>(x, s) : ls_update<double>(x, s);
+        if (r != RT_OK) return r;
+        x->enqueued++;
+      }
+  }
+  // every member's state, then the members at their checks
+  if (L->m.size() > L->hs_cap) {
+    if (L->hs) cudaFreeHost(L->hs);
+    L->hs = nullptr;
+    L->hs_cap = 0;
+    CU(cudaMallocHost((void **)&L->hs, L->m.size() * sizeof(rtk::SolveState)));
+    L->hs_cap = L->m.size();
+  }
+  for (size_t i = 0; i < L->m.size(); ++i)
+    CU(cudaMemcpyAsync(&L->hs[i], L->m[i]->g->st, sizeof(rtk::SolveState), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  std::vector<LsMember *> keep;
+  for (size_t i = 0; i < L->m.size(); ++i) {
+    LsMember *x = L->m[i];
+    x->hs = L->hs[i];
+    if (x->enqueued < x->next_check) {
+      keep.push_back(x);
+      continue;
+    }
+    rt_grid g = x->g;
+    const rtk::SolveState &hs = x->hs;
+    bool finished = true;
+    rt_status st = RT_OK;
+    if (hs.err) {
+      st = fail(RT_ERR_CUDA, "device check failed (code %d, index %d)", hs.err, hs.err_info);
+    } else if (!(hs.done || x->enqueued >= x->max_iter)) {
+      finished = false;
+      if (x->fp64_its && g->anchor_drop > 0.0) {
+        if (x->anchor_ref < 0.0) {
+          x->anchor_ref = hs.last_resid;
+        } else if (hs.last_resid <= x->anchor_ref * g->anchor_drop) {
+          x->anchor_next = true;
+          x->anchor_ref = hs.last_resid;
+        }
+      }
+      if (!(x->opts.check_every > 0)) x->batch = std::min(x->batch * 2, 64);
+      x->next_check = x->enqueued + std::min(x->batch, x->max_iter - x->enqueued);
+    }
+    if (!finished) {
+      keep.push_back(x);
+      continue;
+    }
+    int iters = hs.iter;
+    double resid = hs.last_resid;
+    bool conv = hs.converged != 0;
+    if (st == RT_OK) {
+      g->fs_total = hs.fs_count;
+      g->last_fs_from_Sfs = !g->lte;
+      g->last_incremental = x->incremental != 0;
+      g->sp_is_delta = x->incremental != 0;
+      st = solve_epilogue(g, nullptr, 0, &x->opts, s, &iters, &resid, &conv);
+    }
+    done->push_back(LsResult{g, x->tag, st, iters, resid, st == RT_OK ? std::string() : g_err});
+    delete x;
+  }
+  L->m.swap(keep);
+  return RT_OK;
+}
+
+extern "C" rt_status rt_ali_solve_many(rt_grid *grids, int n, const rt_solve_opts *opts, int *iters,
+                                       double *resid, int *status) {
+  if (n < 0 || (n > 0 && !grids)) return fail(RT_ERR_ARG, "NULL grids or n < 0");
+  for (int i = 0; i < n; ++i) {
+    if (!grids[i]) return fail(RT_ERR_ARG, "grid %d is NULL", i);
+    if (!grids[i]->have_medium) return fail(RT_ERR_STATE, "grid %d: rt_set_opacity_source has not succeeded", i);
+    if (grids[i]->iteration == RT_ITER_GAUSS_SEIDEL || grids[i]->interp != RT_INTERP_LINEAR)
+      return fail(RT_ERR_STATE, "grid %d: lock-step solves take the Jacobi iteration with linear interpolation", i);
+  }
+  if (opts && !(opts->tol >= 0.0)) return fail(RT_ERR_ARG, "tol must be >= 0");
+  cudaStream_t s = opts && opts->stream ? (cudaStream_t)opts->stream : (n > 0 ? grids[0]->own : nullptr);
+  rt_lockstep L = nullptr;
+  rt_status r = ls_create(s, &L);
+  if (r != RT_OK) return r;
+  std::vector<int> idx(n);
+  rt_status first = RT_OK;
+  std::string first_msg;
+  for (int i = 0; i < n; ++i) {
+    idx[i] = i;
+    if ((r = ls_add(L, grids[i], opts, &idx[i])) != RT_OK) {
+      ls_destroy(L);
+      return r;
+    }
+  }
+  std::vector<LsResult> done;
+  while (ls_size(L) > 0) {
+    if ((r = ls_step(L, &done)) != RT_OK) {
+      ls_destroy(L);
+      return r;
+    }
+  }
+  ls_destroy(L);
+  for (const LsResult &d : done) {
+    const int i = *(const int *)d.tag;
+    if (iters) iters[i] = d.iters;
+    if (resid) resid[i] = d.resid;
+    if (status) status[i] = d.status;
+    if (d.status != RT_OK && first == RT_OK) {
+      first = d.status;
+      first_msg = d.message;
+    }
+  }
+  return first == RT_OK ? RT_OK : fail(first, "%s", first_msg.c_str());
+}
 
 // ----------------------------------------------------- allocation-free formal solution
 // Working memory for rt_formal_solve_noalloc: one array in this library's device

@@ -742,12 +742,13 @@ __device__ __forceinline__ void seg_weights2(float2 x, float2 &E, float2 &psi0) 
   psi0.y = x.y < 0.5f ? small.y : 1.f - q.y;
 }
 
+// One cluster's (group, frequency) instance `inst` of the grid described by A
+// (blockIdx.x % A.cluster is the CTA's strip).
 template <typename T, int AMAX, bool MOM, int SEG, bool VEC>
-__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(const SweepArgs<T> A) {
+__device__ __forceinline__ void pipe_body(const SweepArgs<T> &A, const int inst) {
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;
   const int rank = blockIdx.x % C;
-  const int inst = blockIdx.x / C;
   const int gi = inst % A.ngroups;
   const int f = inst / A.ngroups;
   const GroupParam gp = A.grp[gi];
@@ -1378,6 +1379,23 @@ __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(c
   (void)bot_edge;
 }
 
+template <typename T, int AMAX, bool MOM, int SEG, bool VEC>
+__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_pipe_kernel(const __grid_constant__ SweepArgs<T> A) {
+  pipe_body<T, AMAX, MOM, SEG, VEC>(A, blockIdx.x / A.cluster);
+}
+
+// The sweeps of several grids in one launch (the request server's shared
+// launches): clusters [base[k], base[k+1]) run grid k's instances.  Every grid
+// has the same cluster size; the launch's CTA size and shared memory are the
+// largest of the grids' (the per-plane loops stride by blockDim).
+template <typename T, int AMAX, int SEG, bool VEC>
+__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_multi_kernel(const __grid_constant__ MultiSweep<T> M) {
+  const int c = blockIdx.x / M.a[0].cluster;
+  int k = 0;
+  while (k + 1 < M.n && c >= M.base[k + 1]) ++k;
+  pipe_body<T, AMAX, false, SEG, VEC>(M.a[k], c - M.base[k]);
+}
+
 // --------------------------------------------------------------------- ALI update
 
 __device__ __forceinline__ double rel_change(double d, double x) {
@@ -1494,8 +1512,9 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
 #pragma unroll 4
         for (int p = 0; p < A.ngroups_per_f; ++p) dJ += (double)A.Jpart[(long long)p * A.d.nf * cells + i];
       }
-      // incremental solves accumulate J in FP64 from the swept increments
-      const double J = inc ? A.J64[i] + dJ : dJ;
+      // incremental solves accumulate J in FP64 from the swept increments (an
+      // FP64 iteration's J replaces the accumulated one)
+      const double J = (inc && A.Jpart) ? A.J64[i] + dJ : dJ;
       double r;
       if (A.lte) {
         const double Jp = A.incremental ? A.J64[i] : A.Jprev[i];
@@ -1550,6 +1569,12 @@ __global__ void ghosts_from64_kernel(long long n, const double *Gout, const doub
     G[i] = (float)Gout[i];
     Gd[i] = (float)(Gout[i] - Gin[i]);
   }
+}
+
+__global__ void f32_to_f64_kernel(long long n, const float *src, double *dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
 }
 
 // Jacobi denominator of Eq. 24, inverted once per medium: the update then
@@ -1987,6 +2012,43 @@ cudaError_t launch_sweep_pipe(const SweepArgs<T> &A, int amax, bool moments, int
   }
 }
 
+template <typename T, int AMAX, bool VEC>
+static cudaError_t launch_multi_t(const MultiSweep<T> &M, int threads, size_t smem, cudaStream_t s) {
+  auto kern = sc_sweep_multi_kernel<T, AMAX, kSweepSeg, VEC>;
+  cudaError_t e = prepare_kernel((const void *)kern);
+  if (e != cudaSuccess) return e;
+  const int C = M.a[0].cluster;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * M.base[M.n]), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = C > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, M);
+}
+
+template <typename T>
+cudaError_t launch_sweep_multi(const MultiSweep<T> &M, int amax, int threads, size_t smem, cudaStream_t s) {
+  if (M.n < 1 || M.n > kMultiMax) return cudaErrorInvalidValue;
+  for (int k = 0; k < M.n; ++k)
+    if (M.a[k].cluster != M.a[0].cluster || pipe_vec_ok<T>(M.a[k].d) != pipe_vec_ok<T>(M.a[0].d))
+      return cudaErrorInvalidValue;
+  const bool vec = pipe_vec_ok<T>(M.a[0].d) && sizeof(T) == 4;
+  switch (amax) {
+    case 1: return vec ? launch_multi_t<T, 1, true>(M, threads, smem, s) : launch_multi_t<T, 1, false>(M, threads, smem, s);
+    case 2: return vec ? launch_multi_t<T, 2, true>(M, threads, smem, s) : launch_multi_t<T, 2, false>(M, threads, smem, s);
+    case 4: return vec ? launch_multi_t<T, 4, true>(M, threads, smem, s) : launch_multi_t<T, 4, false>(M, threads, smem, s);
+    case 8: return vec ? launch_multi_t<T, 8, true>(M, threads, smem, s) : launch_multi_t<T, 8, false>(M, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_sweep_tiled(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                                cudaStream_t s) {
@@ -2058,6 +2120,11 @@ cudaError_t launch_ali(const AliArgs<T> &A, cudaStream_t s) {
 cudaError_t launch_ghosts_from64(long long n, const double *Gout, const double *Gin, float *G, float *Gd,
                                  cudaStream_t s) {
   ghosts_from64_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, Gout, Gin, G, Gd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(long long n, const float *src, double *dst, cudaStream_t s) {
+  f32_to_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst);
   return cudaGetLastError();
 }
 
@@ -2151,6 +2218,7 @@ cudaError_t launch_heating(const Dims &d, const double *fw, const double *chi, c
   template cudaError_t launch_seg_table<T>(const SweepArgs<T> &, int, int, T *, T *, cudaStream_t);   \
   template cudaError_t launch_sweep_tiled<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
   template cudaError_t launch_sweep_pipe<T>(const SweepArgs<T> &, int, bool, int, size_t, cudaStream_t); \
+  template cudaError_t launch_sweep_multi<T>(const MultiSweep<T> &, int, int, size_t, cudaStream_t);   \
   template int sweep_max_active_clusters<T>(int, int, int, int, size_t);                          \
   template cudaError_t launch_ali<T>(const AliArgs<T> &, cudaStream_t);                             \
   template cudaError_t launch_lstar<T>(const Dims &, const double *, const RayGeom *, int, double *, \

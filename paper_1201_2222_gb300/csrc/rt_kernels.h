@@ -132,6 +132,24 @@ __host__ __device__ inline int pipe_row_len(int Nu, int seg) { return ((4 + Nu +
 template <typename T>
 cudaError_t launch_sweep_pipe(const SweepArgs<T> &A, int amax, bool moments, int threads, size_t smem,
                               cudaStream_t s);
+// The pipelined sweeps of up to kMultiMax grids in one launch: grid k's
+// (group, frequency) instances are clusters base[k] .. base[k+1] - 1.  All grids
+// have the same cluster size and the same vectorisation (rows of a multiple of
+// 4 cells, or not); passed by value as the kernel's parameter.
+constexpr int kMultiMax = 24;
+static_assert(sizeof(SweepArgs<double>) * kMultiMax + 4 * (kMultiMax + 2) <= 32764, "kernel parameter limit");
+template <typename T>
+struct MultiSweep {
+  SweepArgs<T> a[kMultiMax];
+  int base[kMultiMax + 1];
+  int n;
+};
+template <typename T>
+cudaError_t launch_sweep_multi(const MultiSweep<T> &M, int amax, int threads, size_t smem, cudaStream_t s);
+// threads per CTA of the second-order sweep at most: its 3 x 3 stencils of chi,
+// S and I for the upwind and downwind points need more than the 128 registers a
+// thread of a 512-thread CTA may hold (they spilled to local memory)
+constexpr int kQuadThreads = 256;
 // second-order sweep (rt_quad.cu): monotonic quadratic face interpolation and
 // Bezier-controlled segment integration, chi/S staged in a four-plane ring
 template <typename T>
@@ -154,6 +172,7 @@ cudaError_t launch_finish(SolveState *st, cudaStream_t s);
 // G = (float) Gout, Gd = (float) (Gout - Gin) over n ghost entries
 cudaError_t launch_ghosts_from64(long long n, const double *Gout, const double *Gin, float *G, float *Gd,
                                  cudaStream_t s);
+cudaError_t launch_f32_to_f64(long long n, const float *src, double *dst, cudaStream_t s);
 // iden = 1 / [eps + (1 - eps)(1 - Lambda*)] (the Jacobi denominator of Eq. 24)
 cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
                                    cudaStream_t s);

@@ -136,7 +136,7 @@ __device__ __forceinline__ T quad_update(const T (&Iu)[3][3], const T (&Su)[3][3
 }
 
 template <typename T, int AMAX, bool MOM>
-__global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_quad_kernel(const SweepArgs<T> A) {
+__global__ void __launch_bounds__(kQuadThreads) sc_sweep_quad_kernel(const SweepArgs<T> A) {
   constexpr int SEG = kSweepSeg;
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;

@@ -1,6 +1,8 @@
 // Request server: queued ALI solves on worker threads, admitted by estimated
-// device footprint, each on its own grid and CUDA stream (see rt_sc.h).  Host
-// code only; it drives the grids through the library's public C API.
+// device footprint, each on its own grid and CUDA stream (see rt_sc.h); in the
+// shared mode the Jacobi solves of every admitted request run in lock-step on
+// one scheduler thread, their sweeps merged into shared launches (rt_lockstep.h),
+// while the workers set grids up and take results back.  Host code only.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -13,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include "rt_lockstep.h"
 #include "rt_sc.h"
 
 rt_status rt_internal_error(rt_status st, const char *msg);   // rt_api.cu
@@ -41,6 +44,7 @@ struct Request {
   Clock::time_point t_submit, t_start, t_done;
   std::vector<double> J, S, Q;
   std::string message;       // the solve's error message (worker thread's rt_last_error)
+  rt_grid g = nullptr;       // shared mode: the grid while it is set up, solved and read
 };
 
 }  // namespace
@@ -56,6 +60,13 @@ struct rt_server_s {
   bool stop = false;
   long long next_id = 1;
   std::vector<std::thread> workers;
+  // shared mode (cluster > 0): grids set up by the workers wait in `ready` for
+  // the scheduler, which moves solved ones to `solved` for a worker to read back
+  int cluster = 0;
+  std::deque<Request *> ready, solved;
+  std::vector<Request *> in_lockstep;
+  long long shared_launches = 0;
+  std::thread scheduler;
 };
 
 namespace {
@@ -93,33 +104,184 @@ void run_solve(Request *r, int device) {
   r->resid = resid;
 }
 
+// Shared mode: the request's grid, planned with the server's cluster size where
+// that plan fits (else the grid's own plan: it then shares launches only with
+// grids that ended up with the same one), with its medium set.
+rt_status prepare_grid(Request *r, int device, int cluster) {
+  cudaSetDevice(device);
+  rt_status st = rt_create_grid(&r->desc, &r->g);
+  if (st != RT_OK) return st;
+  if (rt_set_sweep_config(r->g, 0, cluster, 0, 3) != RT_OK) st = rt_set_sweep_config(r->g, 0, 0, 0, 0);
+  if (st == RT_OK)
+    st = rt_set_opacity_source(r->g, r->chi.data(), r->eps.data(), r->B.data(), r->fw.data(), 0);
+  return st;
+}
+
+// Shared mode: J, S and Q of a solved request back to host memory; the grid freed.
+void read_back(Request *r, int device) {
+  cudaSetDevice(device);
+  rt_status st = (rt_status)r->status;
+  if (r->g && (st == RT_OK || st == RT_ERR_NOT_CONVERGED)) {
+    const size_t N = r->chi.size(), C = N / (size_t)r->desc.nfreq;
+    r->J.resize(N);
+    r->S.resize(N);
+    r->Q.resize(C);
+    rt_status s2 = rt_moments(r->g, r->J.data(), nullptr, nullptr, nullptr, r->Q.data(), 0, nullptr);
+    if (s2 == RT_OK) s2 = rt_get_S(r->g, r->S.data(), 0, nullptr);
+    if (s2 != RT_OK) {
+      st = s2;
+      r->message = rt_last_error();
+    }
+  }
+  if (r->g) rt_destroy_grid(r->g);
+  r->g = nullptr;
+  r->status = st;
+}
+
+void finish_request(rt_server s, Request *r) {
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->resident -= r->footprint;
+    r->state = RT_REQ_DONE;
+    r->t_done = Clock::now();
+  }
+  s->cv.notify_all();
+}
+
+bool shareable(const rt_server_s *s, const Request *r) {
+  return s->cluster > 0 && r->iteration == RT_ITER_JACOBI && r->interp == RT_INTERP_LINEAR;
+}
+
 void worker_loop(rt_server s) {
   for (;;) {
     Request *r = nullptr;
+    bool readback = false;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait(lk, [&] {
         if (s->stop) return true;
+        if (!s->solved.empty()) return true;
         if (s->queue.empty()) return false;
         const long long fp = s->queue.front()->footprint;
         return s->resident == 0 || s->resident + fp <= s->budget;
       });
       if (s->stop) return;
-      r = s->queue.front();
-      s->queue.pop_front();
-      s->resident += r->footprint;
-      r->state = RT_REQ_RUNNING;
-      r->t_start = Clock::now();
+      if (!s->solved.empty()) {   // results first: they free device memory
+        r = s->solved.front();
+        s->solved.pop_front();
+        readback = true;
+      } else {
+        r = s->queue.front();
+        s->queue.pop_front();
+        s->resident += r->footprint;
+        r->state = RT_REQ_RUNNING;
+        r->t_start = Clock::now();
+      }
     }
-    run_solve(r, s->device);
+    if (readback) {
+      read_back(r, s->device);
+      finish_request(s, r);
+    } else if (shareable(s, r)) {
+      const rt_status st = prepare_grid(r, s->device, s->cluster);
+      if (st != RT_OK) {
+        r->status = st;
+        r->message = rt_last_error();
+        read_back(r, s->device);
+        finish_request(s, r);
+      } else {
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->ready.push_back(r);
+        }
+        s->cv.notify_all();
+      }
+    } else {
+      run_solve(r, s->device);
+      finish_request(s, r);
+    }
+  }
+}
+
+// Shared mode: every admitted request's Jacobi solve in lock-step on this
+// thread's stream; ready grids join at each step, solved ones go to `solved`.
+void scheduler_loop(rt_server s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  rt_lockstep L = nullptr;
+  ls_create(st, &L);
+  std::vector<LsResult> done;
+  for (;;) {
+    std::vector<Request *> join;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] { return s->stop || !s->ready.empty() || ls_size(L) > 0; });
+      if (s->stop) break;
+      join.assign(s->ready.begin(), s->ready.end());
+      s->ready.clear();
+    }
+    std::vector<Request *> out;
+    for (Request *r : join) {
+      rt_solve_opts o{};
+      o.tol = r->tol;
+      o.max_iter = r->max_iter;
+      const rt_status e = ls_add(L, r->g, &o, r);
+      if (e != RT_OK) {
+        r->status = e;
+        r->message = rt_last_error();
+        out.push_back(r);
+      } else {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->in_lockstep.push_back(r);
+      }
+    }
+    done.clear();
+    rt_status e = ls_size(L) > 0 ? ls_step(L, &done) : RT_OK;
+    if (e != RT_OK) {   // a shared launch out: every member fails with it
+      const std::string msg = rt_last_error();
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (Request *r : s->in_lockstep) {
+        r->status = e;
+        r->message = msg;
+        out.push_back(r);
+      }
+      s->in_lockstep.clear();
+      ls_destroy(L);
+      ls_create(st, &L);
+    }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->resident -= r->footprint;
-      r->state = RT_REQ_DONE;
-      r->t_done = Clock::now();
+      for (const LsResult &d : done) {
+        Request *r = (Request *)d.tag;
+        r->status = d.status;
+        r->iters = d.iters;
+        r->resid = d.resid;
+        r->message = d.message;
+        out.push_back(r);
+        for (size_t i = 0; i < s->in_lockstep.size(); ++i)
+          if (s->in_lockstep[i] == r) {
+            s->in_lockstep.erase(s->in_lockstep.begin() + i);
+            break;
+          }
+      }
+      for (Request *r : out) s->solved.push_back(r);
+      s->shared_launches = ls_shared_launches(L);
     }
-    s->cv.notify_all();
+    if (!out.empty()) s->cv.notify_all();
   }
+  // stopping: grids still in the set are freed with their requests
+  ls_destroy(L);
+  cudaStreamSynchronize(st);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (Request *r : s->in_lockstep)
+      if (r->g) {
+        rt_destroy_grid(r->g);
+        r->g = nullptr;
+      }
+    s->in_lockstep.clear();
+  }
+  cudaStreamDestroy(st);
 }
 
 void fill_info(const Request *r, rt_request_info *info) {
@@ -152,8 +314,21 @@ rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
     }
     s->budget = (long long)(0.8 * (double)fr);
   }
+  if (opts->shared_cluster < 0 || opts->shared_cluster > 16) {
+    delete s;
+    return rt_internal_error(RT_ERR_ARG, "rt_server_create: shared_cluster must be in 0..16");
+  }
+  s->cluster = opts->shared_cluster;
   for (int i = 0; i < opts->workers; ++i) s->workers.emplace_back(worker_loop, s);
+  if (s->cluster > 0) s->scheduler = std::thread(scheduler_loop, s);
   *out = s;
+  return RT_OK;
+}
+
+rt_status rt_server_shared_launches(rt_server s, long long *n) {
+  if (!s || !n) return rt_internal_error(RT_ERR_ARG, "rt_server_shared_launches: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *n = s->shared_launches;
   return RT_OK;
 }
 
@@ -165,6 +340,11 @@ rt_status rt_server_destroy(rt_server s) {
   }
   s->cv.notify_all();
   for (auto &t : s->workers) t.join();
+  if (s->scheduler.joinable()) s->scheduler.join();
+  for (Request *r : s->ready)
+    if (r->g) rt_destroy_grid(r->g);
+  for (Request *r : s->solved)
+    if (r->g) rt_destroy_grid(r->g);
   for (auto &kv : s->reqs) delete kv.second;
   delete s;
   return RT_OK;

@@ -46,11 +46,12 @@ class rt_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("resid", ctypes.c_double), ("sweep_ms", ctypes.c_double),
                 ("sweep_launches", ctypes.c_int), ("total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("updates", ctypes.c_longlong),
-                ("graph_launches", ctypes.c_longlong), ("first_fp64", ctypes.c_int)]
+                ("graph_launches", ctypes.c_longlong), ("first_fp64", ctypes.c_int),
+                ("fp64_anchors", ctypes.c_int), ("shared_launches", ctypes.c_longlong)]
 
 
 class rt_server_opts(ctypes.Structure):
-    _fields_ = [("device_bytes", ctypes.c_longlong), ("workers", ctypes.c_int)]
+    _fields_ = [("device_bytes", ctypes.c_longlong), ("workers", ctypes.c_int), ("shared_cluster", ctypes.c_int)]
 
 
 class rt_request(ctypes.Structure):
@@ -102,12 +103,16 @@ _SIGS = {
     "rt_grid_footprint": (ctypes.c_int, [ctypes.POINTER(rt_grid_desc), ctypes.POINTER(ctypes.c_longlong)]),
     "rt_server_create": (ctypes.c_int, [ctypes.POINTER(rt_server_opts), ctypes.POINTER(_VP)]),
     "rt_server_destroy": (ctypes.c_int, [_VP]),
+    "rt_server_shared_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "rt_ali_solve_many": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(rt_solve_opts), _VP, _VP, _VP]),
     "rt_submit": (ctypes.c_int, [_VP, ctypes.POINTER(rt_request), ctypes.POINTER(ctypes.c_longlong)]),
     "rt_poll": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.POINTER(rt_request_info)]),
     "rt_wait": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(rt_request_info)]),
     "rt_fetch": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP, _VP, _VP]),
     "rt_measure_rates": (ctypes.c_int, [_VP, ctypes.c_int]),
     "rt_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "rt_set_fp64_anchors": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "rt_set_fp64_bin_limit": (ctypes.c_int, [_VP, ctypes.c_double]),
     "rt_set_external_face": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int,
                                             ctypes.POINTER(rt_solve_opts)]),
     "rt_get_face_intensity": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int,
@@ -405,6 +410,15 @@ class Grid:
             scheme = {"jacobi": ITER_JACOBI, "gauss_seidel": ITER_GAUSS_SEIDEL}[scheme.lower()]
         _check(load().rt_set_iteration(self._h, int(scheme)))
 
+    def set_fp64_anchors(self, drop):
+        """Residual drop between FP64 iterations of mixed Jacobi solves (rt_set_fp64_anchors)."""
+        _check(load().rt_set_fp64_anchors(self._h, float(drop)))
+
+    def set_fp64_bin_limit(self, limit):
+        """Roundoff/eps limit above which a bin is solved in FP64 (rt_set_fp64_bin_limit);
+        applies from the next set_opacity_source."""
+        _check(load().rt_set_fp64_bin_limit(self._h, float(limit)))
+
     def set_wait_limit(self, polls):
         """Polls before a Gauss-Seidel grid-barrier wait gives up (rt_set_wait_limit)."""
         _check(load().rt_set_wait_limit(self._h, int(polls)))
@@ -446,14 +460,30 @@ def grid_footprint(p, prec=MIXED):
     return out.value
 
 
+def ali_solve_many(grids, tol=1e-6, max_iter=1000, check_every=0, raise_on_fail=True):
+    """Jacobi ALI solves of several Grids together, their sweeps merged into shared
+    launches (rt_ali_solve_many); returns per grid (iters, resid, status)."""
+    n = len(grids)
+    hs = (_VP * max(1, n))(*[g._h for g in grids])
+    it = (ctypes.c_int * max(1, n))()
+    rs = (ctypes.c_double * max(1, n))()
+    sts = (ctypes.c_int * max(1, n))()
+    o = rt_solve_opts(tol, max_iter, check_every, None)
+    st = load().rt_ali_solve_many(ctypes.cast(hs, _VP), n, ctypes.byref(o), ctypes.cast(it, _VP),
+                                  ctypes.cast(rs, _VP), ctypes.cast(sts, _VP))
+    if st != RT_OK and (raise_on_fail or st != RT_ERR_NOT_CONVERGED):
+        _check(st)
+    return [(it[i], rs[i], sts[i]) for i in range(n)]
+
+
 class Server:
     """Request server (rt_server_*): queued ALI solves on worker threads, admitted
     by estimated device footprint; results come back as host arrays."""
 
-    def __init__(self, workers=2, device_bytes=0):
+    def __init__(self, workers=2, device_bytes=0, shared_cluster=0):
         self._h = _VP()
-        _check(load().rt_server_create(ctypes.byref(rt_server_opts(int(device_bytes), int(workers))),
-                                       ctypes.byref(self._h)))
+        opts = rt_server_opts(int(device_bytes), int(workers), int(shared_cluster))
+        _check(load().rt_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
         self._shapes = {}
         self._keep = {}
 
@@ -481,6 +511,12 @@ class Server:
         _check(load().rt_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
         self._shapes[rid.value] = (p.nf, p.nz, p.ny, p.nx)
         return rid.value
+
+    def shared_launches(self):
+        """Shared sweep launches issued so far (rt_server_shared_launches)."""
+        n = ctypes.c_longlong(0)
+        _check(load().rt_server_shared_launches(self._h, ctypes.byref(n)))
+        return n.value
 
     @staticmethod
     def _info(i):

@@ -72,6 +72,38 @@ def test_results_in_the_mix_equal_results_alone(rt):
     srv.close()
 
 
+def test_shared_launches_equal_results_alone(rt):
+    # shared mode: the Jacobi requests run in lock-step on the scheduler, their
+    # sweeps merged; each equals the same solve alone with the server's cluster
+    # size (the Gauss-Seidel and second-order requests run on workers as before)
+    reqs = _mix()
+    srv = rt.Server(workers=3, shared_cluster=2)
+    ids = [srv.submit(p, prec=prec, interp=interp, iteration=scheme, max_iter=3000)
+           for p, prec, interp, scheme in reqs]
+    for rid, (p, prec, interp, scheme) in zip(ids, reqs):
+        info = srv.wait(rid, timeout=120)
+        assert info["status"] == rt.RT_OK and info["resid"] <= p.tol
+        J, S, Q, st = srv.fetch(rid)
+        g = rt.Grid.from_problem(p, prec=prec)
+        g.set_interpolation(interp)
+        g.set_iteration(scheme)
+        if interp == "linear" and scheme == "jacobi":
+            try:
+                g.set_sweep_config(0, 2, 0, 3)
+            except rt.RTError:
+                g.set_sweep_config(0, 0, 0, 0)
+        g.set_opacity_source(p.chi, p.eps, p.B, p.freq_w)
+        iters, resid, st1 = g.ali_solve(tol=p.tol, max_iter=3000)
+        m = g.moments()
+        assert info["iters"] == iters
+        np.testing.assert_array_equal(J, m["J"])
+        np.testing.assert_array_equal(S, g.get_S())
+        np.testing.assert_array_equal(Q, m["Q"])
+        g.close()
+    assert srv.shared_launches() > 0
+    srv.close()
+
+
 def test_admission_by_footprint(rt):
     reqs = _mix()[:5]
     fps = [rt.grid_footprint(p, prec) for p, prec, _, _ in reqs]

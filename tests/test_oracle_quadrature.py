@@ -63,7 +63,10 @@ def test_lq4_closed_form():
 
 
 @pytest.mark.parametrize("n_mu,levels,weights", [
-    # published S6 / S8 level-symmetric sets, weights normalised to 1 per octant
+    # the level-symmetric S6 / S8 sets as tabulated in E. E. Lewis & W. F. Miller,
+    # Computational Methods of Neutron Transport (Wiley 1984), Table 4-1 (weights
+    # normalised to 1 per octant); they are the Carlson sets (Sec. 3.2 cites
+    # Carlson 1963 for the construction)
     (6, [0.2666355, 0.6815076, 0.9261808], [0.1761263, 0.1572071]),
     (8, [0.2182179, 0.5773503, 0.7867958, 0.9511897], [0.1209877, 0.0907407, 0.0925926]),
 ])
