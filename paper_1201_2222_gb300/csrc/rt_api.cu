@@ -385,38 +385,70 @@ void build_rays(rt_grid g) {
   const double *dd = &g->desc.dx;
   int count[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   g->rays.resize(g->na);
+  for (int a = 0; a < 3; ++a) g->used_axis[a] = 0;
+  std::vector<std::array<double, 3>> tt(g->na);
+  std::vector<int> tied(g->na, 0);   // bit a: the ray may sweep along a
+  const int V = g->two_d ? 1 : 2;
+  auto cls = [&](int k, int a) -> int & { return count[a][g->rays[k].sgn[a] > 0 ? 0 : 1]; };
   for (int k = 0; k < g->na; ++k) {
     RayGeom r{};
     const double *m = &g->mu[3 * k];
-    double t[3];
+    double *t = tt[k].data();
     for (int a = 0; a < 3; ++a) {
       r.sgn[a] = m[a] >= 0.0 ? 1 : -1;
       t[a] = (a == 2 && g->two_d) ? std::numeric_limits<double>::infinity() : dd[a] / std::fabs(m[a]);
     }
+    g->rays[k] = r;
     const double tmin = std::min(t[0], std::min(t[1], t[2]));
     // first-crossed face; a tie (the ray leaves through an edge) gives identical
     // interpolants on either face, so tied rays go to the least-loaded sweep group
     // -- except under Gauss-Seidel, where a ray tied with the reverse axis V is a
     // V ray (its upwind vertices all lie on the plane of V it comes from)
     int best = -1;
-    const int V = g->two_d ? 1 : 2;
     for (int a = 2; a >= 0; --a) {
       if (t[a] != tmin) continue;
-      const int sd = r.sgn[a] > 0 ? 0 : 1;
-      if (best < 0 || count[a][sd] < count[best][r.sgn[best] > 0 ? 0 : 1]) best = a;
+      if (best < 0 || cls(k, a) < cls(k, best)) best = a;
     }
-    if (g->iteration == RT_ITER_GAUSS_SEIDEL && t[V] == tmin) best = V;
-    r.axis = best;
-    r.s = t[best];
+    if (g->iteration == RT_ITER_GAUSS_SEIDEL && t[V] == tmin) {
+      best = V;
+    } else {
+      for (int a = 0; a < 3; ++a)
+        if (t[a] == tmin) tied[k] |= 1 << a;
+    }
+    g->rays[k].axis = best;
+    cls(k, best)++;
+  }
+  // the greedy choice in angle order can leave the classes uneven (and with odd
+  // counts, whose groups then hold a ray fewer): move tied rays from a class to
+  // one of their other classes holding at least two rays fewer, until none can
+  // (each move lowers the sum of squared class sizes, so this ends)
+  for (bool moved = true; moved;) {
+    moved = false;
+    for (int k = 0; k < g->na; ++k) {
+      if (__builtin_popcount(tied[k]) < 2) continue;
+      const int a = g->rays[k].axis;
+      for (int b = 0; b < 3; ++b) {
+        if (b == a || !(tied[k] >> b & 1) || cls(k, a) - cls(k, b) < 2) continue;
+        cls(k, a)--;
+        cls(k, b)++;
+        g->rays[k].axis = b;
+        moved = true;
+        break;
+      }
+    }
+  }
+  for (int k = 0; k < g->na; ++k) {
+    RayGeom &r = g->rays[k];
+    const double *m = &g->mu[3 * k];
+    const int best = r.axis;
+    r.s = tt[k][best];
     r.w = g->wq[k];
     for (int a = 0; a < 3; ++a) {
       if (a == best) r.frac[a] = 1.0;
       else if (a == 2 && g->two_d) r.frac[a] = 0.0;
       else r.frac[a] = std::min(1.0, r.s * std::fabs(m[a]) / dd[a]);
     }
-    count[best][r.sgn[best] > 0 ? 0 : 1]++;
     g->used_axis[best] = 1;
-    g->rays[k] = r;
   }
 }
 
