@@ -422,11 +422,12 @@ typedef struct {
                                shared mode, grids being set up or read back at once */
   int shared_cluster;       /* 0: each solve on its worker.  1..16: shared mode -- every
                                admitted Jacobi solve with linear interpolation runs in
-                               lock-step with the others on one scheduler thread, as in
-                               rt_ali_solve_many, each grid planned with this many CTAs per
-                               cluster where that plan fits; the workers set grids up and
-                               read results back (Gauss-Seidel and quadratic requests still
-                               run on a worker) */
+                               lock-step with the others of its size class (cells x rays x
+                               frequencies below 2^22, below 2^26, above; one scheduler
+                               thread and stream each), as in rt_ali_solve_many, each grid
+                               planned with this many CTAs per cluster where that plan
+                               fits; the workers set grids up and read results back
+                               (Gauss-Seidel and quadratic requests still run on a worker) */
 } rt_server_opts;
 typedef struct {
   rt_grid_desc desc;

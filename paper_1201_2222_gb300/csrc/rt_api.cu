@@ -2286,6 +2286,9 @@ void ls_destroy(rt_lockstep L) {
 
 size_t ls_size(rt_lockstep L) { return L ? L->m.size() : 0; }
 long long ls_shared_launches(rt_lockstep L) { return L ? L->shared : 0; }
+void ls_reset_shared(rt_lockstep L) {
+  if (L) L->shared = 0;
+}
 
 rt_status ls_add(rt_lockstep L, rt_grid g, const rt_solve_opts *opts, void *tag) {
   if (!L || !g) return fail(RT_ERR_ARG, "NULL argument");

@@ -34,5 +34,7 @@ rt_status ls_add(rt_lockstep L, rt_grid g, const rt_solve_opts *opts, void *tag)
 // the shared launches fails the call.
 rt_status ls_step(rt_lockstep L, std::vector<LsResult> *done);
 size_t ls_size(rt_lockstep L);
-// Shared launches issued so far (each sweeps several grids).
+// Shared launches issued since the set was made or last reset (each sweeps
+// several grids).
 long long ls_shared_launches(rt_lockstep L);
+void ls_reset_shared(rt_lockstep L);

@@ -1,8 +1,9 @@
 // Request server: queued ALI solves on worker threads, admitted by estimated
 // device footprint, each on its own grid and CUDA stream (see rt_sc.h); in the
-// shared mode the Jacobi solves of every admitted request run in lock-step on
-// one scheduler thread, their sweeps merged into shared launches (rt_lockstep.h),
-// while the workers set grids up and take results back.  Host code only.
+// shared mode the Jacobi solves of the admitted requests run in lock-step, one
+// set per size class on its own scheduler thread, their sweeps merged into
+// shared launches (rt_lockstep.h), while the workers set grids up and take
+// results back.  Host code only.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -45,7 +46,19 @@ struct Request {
   std::vector<double> J, S, Q;
   std::string message;       // the solve's error message (worker thread's rt_last_error)
   rt_grid g = nullptr;       // shared mode: the grid while it is set up, solved and read
+  int lane = 0;              // shared mode: the lock-step set it joins
 };
+
+// Shared mode: requests are sorted into lock-step sets by the work of one of
+// their iterations (cells x rays x frequencies), each set iterating on its own
+// thread and stream, so that a small grid is not held to the pace of the largest
+// grid's sweep: below 2^22, below 2^26, and above.
+constexpr int kLanes = 3;
+int lane_of(const rt_grid_desc &d) {
+  const long long na = (long long)d.n_mu * (d.n_mu + 2) / (d.nz == 1 ? 2 : 1);
+  const long long u = (long long)d.nx * d.ny * d.nz * na * d.nfreq;
+  return u < (1LL << 22) ? 0 : (u < (1LL << 26) ? 1 : 2);
+}
 
 }  // namespace
 
@@ -63,10 +76,10 @@ struct rt_server_s {
   // shared mode (cluster > 0): grids set up by the workers wait in `ready` for
   // the scheduler, which moves solved ones to `solved` for a worker to read back
   int cluster = 0;
-  std::deque<Request *> ready, solved;
-  std::vector<Request *> in_lockstep;
-  long long shared_launches = 0;
-  std::thread scheduler;
+  std::deque<Request *> ready[kLanes], solved;
+  std::vector<Request *> in_lockstep[kLanes];
+  long long shared_launches[kLanes] = {0, 0, 0};
+  std::vector<std::thread> schedulers;
 };
 
 namespace {
@@ -191,7 +204,7 @@ void worker_loop(rt_server s) {
       } else {
         {
           std::lock_guard<std::mutex> lk(s->mu);
-          s->ready.push_back(r);
+          s->ready[r->lane].push_back(r);
         }
         s->cv.notify_all();
       }
@@ -202,9 +215,9 @@ void worker_loop(rt_server s) {
   }
 }
 
-// Shared mode: every admitted request's Jacobi solve in lock-step on this
-// thread's stream; ready grids join at each step, solved ones go to `solved`.
-void scheduler_loop(rt_server s) {
+// Shared mode: the Jacobi solves of one lane's admitted requests in lock-step on
+// this thread's stream; ready grids join at each step, solved ones go to `solved`.
+void scheduler_loop(rt_server s, int lane) {
   cudaSetDevice(s->device);
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -215,10 +228,10 @@ void scheduler_loop(rt_server s) {
     std::vector<Request *> join;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] { return s->stop || !s->ready.empty() || ls_size(L) > 0; });
+      s->cv.wait(lk, [&] { return s->stop || !s->ready[lane].empty() || ls_size(L) > 0; });
       if (s->stop) break;
-      join.assign(s->ready.begin(), s->ready.end());
-      s->ready.clear();
+      join.assign(s->ready[lane].begin(), s->ready[lane].end());
+      s->ready[lane].clear();
     }
     std::vector<Request *> out;
     for (Request *r : join) {
@@ -232,7 +245,7 @@ void scheduler_loop(rt_server s) {
         out.push_back(r);
       } else {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->in_lockstep.push_back(r);
+        s->in_lockstep[lane].push_back(r);
       }
     }
     done.clear();
@@ -240,12 +253,12 @@ void scheduler_loop(rt_server s) {
     if (e != RT_OK) {   // a shared launch out: every member fails with it
       const std::string msg = rt_last_error();
       std::lock_guard<std::mutex> lk(s->mu);
-      for (Request *r : s->in_lockstep) {
+      for (Request *r : s->in_lockstep[lane]) {
         r->status = e;
         r->message = msg;
         out.push_back(r);
       }
-      s->in_lockstep.clear();
+      s->in_lockstep[lane].clear();
       ls_destroy(L);
       ls_create(st, &L);
     }
@@ -258,14 +271,16 @@ void scheduler_loop(rt_server s) {
         r->resid = d.resid;
         r->message = d.message;
         out.push_back(r);
-        for (size_t i = 0; i < s->in_lockstep.size(); ++i)
-          if (s->in_lockstep[i] == r) {
-            s->in_lockstep.erase(s->in_lockstep.begin() + i);
+        auto &v = s->in_lockstep[lane];
+        for (size_t i = 0; i < v.size(); ++i)
+          if (v[i] == r) {
+            v.erase(v.begin() + i);
             break;
           }
       }
       for (Request *r : out) s->solved.push_back(r);
-      s->shared_launches = ls_shared_launches(L);
+      s->shared_launches[lane] += ls_shared_launches(L);
+      ls_reset_shared(L);
     }
     if (!out.empty()) s->cv.notify_all();
   }
@@ -274,12 +289,12 @@ void scheduler_loop(rt_server s) {
   cudaStreamSynchronize(st);
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    for (Request *r : s->in_lockstep)
+    for (Request *r : s->in_lockstep[lane])
       if (r->g) {
         rt_destroy_grid(r->g);
         r->g = nullptr;
       }
-    s->in_lockstep.clear();
+    s->in_lockstep[lane].clear();
   }
   cudaStreamDestroy(st);
 }
@@ -320,7 +335,8 @@ rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
   }
   s->cluster = opts->shared_cluster;
   for (int i = 0; i < opts->workers; ++i) s->workers.emplace_back(worker_loop, s);
-  if (s->cluster > 0) s->scheduler = std::thread(scheduler_loop, s);
+  if (s->cluster > 0)
+    for (int l = 0; l < kLanes; ++l) s->schedulers.emplace_back(scheduler_loop, s, l);
   *out = s;
   return RT_OK;
 }
@@ -328,7 +344,7 @@ rt_status rt_server_create(const rt_server_opts *opts, rt_server *out) {
 rt_status rt_server_shared_launches(rt_server s, long long *n) {
   if (!s || !n) return rt_internal_error(RT_ERR_ARG, "rt_server_shared_launches: NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
-  *n = s->shared_launches;
+  *n = s->shared_launches[0] + s->shared_launches[1] + s->shared_launches[2];
   return RT_OK;
 }
 
@@ -340,9 +356,10 @@ rt_status rt_server_destroy(rt_server s) {
   }
   s->cv.notify_all();
   for (auto &t : s->workers) t.join();
-  if (s->scheduler.joinable()) s->scheduler.join();
-  for (Request *r : s->ready)
-    if (r->g) rt_destroy_grid(r->g);
+  for (auto &t : s->schedulers) t.join();
+  for (auto &q : s->ready)
+    for (Request *r : q)
+      if (r->g) rt_destroy_grid(r->g);
   for (Request *r : s->solved)
     if (r->g) rt_destroy_grid(r->g);
   for (auto &kv : s->reqs) delete kv.second;
@@ -375,6 +392,7 @@ rt_status rt_submit(rt_server s, const rt_request *req, long long *id_out) {
   r->max_iter = req->max_iter;
   r->iteration = req->iteration;
   r->footprint = fp;
+  r->lane = lane_of(r->desc);
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
