@@ -450,7 +450,10 @@ typedef struct {
 } rt_request_info;
 
 /* Estimated device memory of a grid with this description (upper bound of the
- * arrays it allocates, with the moments pass).  Errors: RT_ERR_ARG. */
+ * arrays it allocates, with the moments pass; for RT_PREC_MIXED including the
+ * internal FP64 grid of its FP64 iterations, but not the FP64 grid of ill-
+ * conditioned bins that some media add: up to an RT_PREC_FP64 grid of those
+ * bins, see RT_PREC_MIXED).  Errors: RT_ERR_ARG. */
 rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes);
 rt_status rt_server_create(const rt_server_opts *opts, rt_server *out);
 /* Shared sweep launches issued by the server's scheduler so far (shared mode). */

@@ -1610,16 +1610,20 @@ rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes) {
   std::vector<double> m, q;
   if (!level_symmetric(D.n_mu, D.nz == 1, m, q)) return fail(RT_ERR_ARG, "bad n_mu %d", D.n_mu);
   const long long na = (long long)q.size();
-  const long long cells = (long long)D.nx * D.ny * D.nz, N = cells * D.nfreq;
-  const long long ts = D.prec == RT_PREC_FP64 ? 8 : 4;
+  const long long cells = (long long)D.nx * D.ny * D.nz;
   const long long gsize = (long long)D.nx * D.ny + (long long)D.ny * D.nz + (long long)D.nx * D.nz;
   const long long groups = (na + 1) / 2 + 6;   // the planner groups at least two rays where it can
+  const long long N = cells * D.nfreq;
+  const long long ts = D.prec == RT_PREC_FP64 ? 8 : 4;
   long long b = 8 * N * 11                     // FP64 fields and state
               + ts * N * 6                     // permuted chi, S copies
               + 6 * D.nfreq * na * gsize * ts  // ghosts (two parities, increments) and inflow faces
               + groups * N * ts * 11           // J, Lambda* and moment partials
               + 8 * (16 * N + cells);          // moments outputs
   if (D.prec == RT_PREC_FP64) b += 2 * na * N * 8;   // tabulated segment weights (one-cell sweep)
+  // a mixed grid's internal FP64 grid for its FP64 iterations: fields, FP64
+  // copies, ghosts, J partials (no moments pass, no table)
+  if (D.prec == RT_PREC_MIXED) b += 8 * N * 11 + 8 * N * 6 + 6 * D.nfreq * na * gsize * 8 + groups * N * 8;
   *bytes = b;
   return RT_OK;
 }
