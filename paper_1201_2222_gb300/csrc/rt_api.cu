@@ -461,7 +461,6 @@ int amax_for(int apg) { return apg <= 1 ? 1 : (apg <= 2 ? 2 : (apg <= 4 ? 4 : 8)
 // Largest CTA of a sweep variant in the grid's precision.
 int sweep_thread_cap(rt_grid g, int variant) {
   if (variant == 1) return 512;
-  if (g->interp == RT_INTERP_QUADRATIC) return rtk::kQuadThreads;
   return g->desc.prec == RT_PREC_FP64 ? rtk::sweep_max_threads<double>() : rtk::sweep_max_threads<float>();
 }
 

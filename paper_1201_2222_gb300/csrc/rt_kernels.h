@@ -146,12 +146,6 @@ struct MultiSweep {
 };
 template <typename T>
 cudaError_t launch_sweep_multi(const MultiSweep<T> &M, int amax, int threads, size_t smem, cudaStream_t s);
-// threads per CTA of the second-order sweep at most: its 3 x 3 stencils of chi,
-// S and I for the upwind and downwind points need more than the 128 registers a
-// thread of a 512-thread CTA may hold (they spilled to local memory); at 384
-// threads the sweep fits its 168 (156 used, no spills), at 256 it had 235 but
-// only 8 warps per SM to hide latency
-constexpr int kQuadThreads = 384;
 // second-order sweep (rt_quad.cu): monotonic quadratic face interpolation and
 // Bezier-controlled segment integration, chi/S staged in a four-plane ring
 template <typename T>
