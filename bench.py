@@ -56,16 +56,17 @@ SHARED_CLUSTER = 4
 
 # DRAM read + write bytes per launch of the sweep kernel from an ncu capture of
 # the same workload and plan (None when none was taken for the plan in use, or
-# the kernel has changed since); keyed by workload, plan and shared-memory size
+# the kernel has changed since); keyed by workload, plan, shared-memory size and groups
 PROFILED_TRAFFIC = {
     # one launch of the 256^3 x 48-ray solve's sweep (dram__bytes_read.sum +
     # dram__bytes_write.sum, one ncu pass)
-    ("stratified_turbulent_256^3_lq6", 3, 2, 16, 512, 197312): 1183264256 + 1617597440,
+    ("stratified_turbulent_256^3_lq6", 3, 2, 16, 512, 197312, 24): 1183264256 + 1617597440,
 }
 
 
 def profiled_traffic(plan, p):
-    key = (p.name, plan["variant"], plan["rays_per_group"], plan["cluster"], plan["threads"], plan["smem"])
+    key = (p.name, plan["variant"], plan["rays_per_group"], plan["cluster"], plan["threads"], plan["smem"],
+           plan["groups"])
     return PROFILED_TRAFFIC.get(key)
 
 

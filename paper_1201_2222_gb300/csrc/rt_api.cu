@@ -555,6 +555,59 @@ int resident_clusters(rt_grid g, int variant, int amax, int C, int threads, size
   return rtk::sweep_max_active_clusters<float>(kind, amax, C, threads, smem);
 }
 
+// A sweep launch whose group instances fill k waves of co-resident clusters and
+// part of one more ends with that last part running alone, each of its clusters
+// carrying a whole group.  Splitting s = (groups mod resident) groups into
+// halves (when 2s clusters fit one wave) leaves k full waves and a last wave of
+// 2s half groups, which ends sooner.  Only single-frequency Jacobi grids are
+// changed; only groups sweeping along y or z are split (the x groups stay
+// first: the float32 update reads their partials in their own layout), and the
+// halves go last, since clusters start in launch order.
+void split_last_wave(rt_grid g) {
+  if (g->iteration != RT_ITER_JACOBI || g->d.nf != 1 || g->apg < 2 || g->groups.empty()) return;
+  const int nres = resident_clusters(g, g->variant, g->amax, g->cluster, g->threads, g->smem);
+  const int G = (int)g->groups.size();
+  if (nres <= 0 || G <= nres) return;
+  const int s = G % nres;
+  if (s == 0 || 2 * s > nres) return;
+  std::vector<int> pick;   // the last s groups of two rays or more off the x axis
+  for (int gi = G - 1; gi >= 0 && (int)pick.size() < s; --gi)
+    if (g->groups[gi].axis != 0 && g->groups[gi].na >= 2) pick.push_back(gi);
+  if ((int)pick.size() < s) return;
+  auto set_kb = [&](GroupParam &gp) {   // stencil-key boundaries of a group's rays
+    int cax[3];
+    rtk::plane_axes(gp.axis, cax);
+    for (int k = 0; k <= 4; ++k) {
+      int q = 0;
+      while (q < gp.na) {
+        const RayGeom &r = g->rays[g->group_angles[gp.a0 + q]];
+        const int key = (r.sgn[cax[0]] > 0 ? 1 : 0) + (r.sgn[cax[1]] > 0 ? 2 : 0);
+        if (key >= k) break;
+        ++q;
+      }
+      gp.kb[k] = q;
+    }
+  };
+  std::vector<GroupParam> keep, halves;
+  for (int gi = 0; gi < G; ++gi) {
+    GroupParam gp = g->groups[gi];
+    if (std::find(pick.begin(), pick.end(), gi) == pick.end()) {
+      keep.push_back(gp);
+      continue;
+    }
+    GroupParam a = gp, b = gp;
+    a.na = gp.na / 2;
+    b.a0 = gp.a0 + a.na;
+    b.na = gp.na - a.na;
+    set_kb(a);
+    set_kb(b);
+    halves.push_back(a);
+    halves.push_back(b);
+  }
+  keep.insert(keep.end(), halves.begin(), halves.end());
+  g->groups.swap(keep);
+}
+
 // Choose rays per group and strips per plane: the estimated sweep time is
 // (waves of resident clusters) x (rays per group) x (cells per strip) x
 // (CTAs sharing an SM), from the runtime's count of co-resident clusters
@@ -632,6 +685,7 @@ void plan_groups(rt_grid g) {
   g->cluster = bC;
   sweep_shape(g, variant, namax, bC, &g->smem, &g->threads);
   if (g->req_threads > 0) g->threads = std::min(g->req_threads, sweep_thread_cap(g, variant));
+  split_last_wave(g);
 }
 
 template <typename T>
