@@ -274,6 +274,7 @@ struct rt_grid_s {
   double *chi = nullptr, *eps = nullptr, *B = nullptr, *fw = nullptr;
   double *S = nullptr, *Sfs = nullptr, *J = nullptr, *Jprev = nullptr;
   double *lstar = nullptr, *oml = nullptr, *iden = nullptr;
+  double *ia = nullptr, *ib = nullptr;   // mixed grids: (1 - eps) iden, eps B iden
   void *chiP[3] = {nullptr, nullptr, nullptr};
   void *SP[3] = {nullptr, nullptr, nullptr};
   void *G[2] = {nullptr, nullptr};
@@ -1058,6 +1059,8 @@ void solve_args(rt_grid g, int incremental, bool gs, rtk::SweepArgs<T> &A, rtk::
   L.eps = g->eps;
   L.B = g->B;
   L.iden = g->iden;
+  L.ia = g->ia;
+  L.ib = g->ib;
   L.Opart = g->interp == RT_INTERP_QUADRATIC ? (const T *)g->Opart : nullptr;
   L.S64 = g->S;
   L.Sfs = g->Sfs;
@@ -1584,6 +1587,10 @@ rt_status rt_create_grid(const rt_grid_desc *desc, rt_grid *out) {
   ALLOC(g->lstar, N * 8);
   ALLOC(g->oml, N * 8);
   ALLOC(g->iden, N * 8);
+  if (D.prec == RT_PREC_MIXED) {
+    ALLOC(g->ia, N * 8);
+    ALLOC(g->ib, N * 8);
+  }
   for (int a = 0; a < 3; ++a) {
     if (!g->used_axis[a]) continue;
     ALLOC(g->chiP[a], N * ts);
@@ -1636,7 +1643,7 @@ rt_status rt_destroy_grid(rt_grid g) {
   if (!g) return RT_OK;
   if (g->own) cudaStreamSynchronize(g->own);
   if (g->first64) rt_destroy_grid(g->first64);
-  void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml, g->iden,
+  void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml, g->iden, g->ia, g->ib,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
                   g->Gd[0], g->Gd[1],
                   g->Ibc[0], g->Ibc[1], g->Ibc[2], g->Ibc[3], g->Ibc[4], g->Ibc[5],
@@ -1668,7 +1675,7 @@ rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes) {
   const long long groups = (na + 1) / 2 + 6;   // the planner groups at least two rays where it can
   const long long N = cells * D.nfreq;
   const long long ts = D.prec == RT_PREC_FP64 ? 8 : 4;
-  long long b = 8 * N * 11                     // FP64 fields and state
+  long long b = 8 * N * (D.prec == RT_PREC_MIXED ? 13 : 11)   // FP64 fields and state
               + ts * N * 6                     // permuted chi, S copies
               + 6 * D.nfreq * na * gsize * ts  // ghosts (two parities, increments) and inflow faces
               + groups * N * ts * 11           // J, Lambda* and moment partials
@@ -1758,7 +1765,7 @@ rt_status rt_set_opacity_source(rt_grid g, const double *chi_tot, const double *
     } else {
       CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
     }
-    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
+    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, g->B, g->ia, g->ib, s));
     g->launches += 2;
   }
   CU(cudaMemcpyAsync(g->S, g->B, N * 8, cudaMemcpyDeviceToDevice, s));
@@ -1983,7 +1990,7 @@ rt_status rt_set_external_face(rt_grid g, int side, const double *chi, const dou
   if (I && (r = copy_in(g, g->xI[side], I, lay * g->na, on_device, s)) != RT_OK) return r;
   if (chi && g->have_medium) {   // Lambda* sees the ghost layer's chi
     CU(rtk::launch_lstar<double>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
-    CU(rtk::launch_inv_denominator((long long)N_of(g), g->eps, g->oml, g->iden, s));
+    CU(rtk::launch_inv_denominator((long long)N_of(g), g->eps, g->oml, g->iden, g->B, g->ia, g->ib, s));
     g->launches += 2;
   }
   if (!on_device || !opts || !opts->stream) CU(cudaStreamSynchronize(s));
@@ -2095,7 +2102,7 @@ rt_status rt_set_iteration(rt_grid g, int scheme) {
     } else {
       CU(rtk::launch_lstar<float>(g->d, g->chi, g->rays_d, g->na, g->lstar, g->oml, g->xchi, s));
     }
-    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, s));
+    CU(rtk::launch_inv_denominator((long long)N, g->eps, g->oml, g->iden, g->B, g->ia, g->ib, s));
     g->launches += 2;
     if ((r = permute_any(g, g->S, g->SP, s)) != RT_OK) return r;
     g->sp_is_delta = false;

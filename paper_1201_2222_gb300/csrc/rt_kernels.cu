@@ -1521,6 +1521,20 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
         r = first ? INFINITY : rel_change(inc ? dJ : J - Jp, J);
         A.Jprev[i] = J;
         snew = A.incremental ? T(0) : (T)A.S64[i];
+      } else if (sizeof(T) == 4 && A.ia && !A.Opart) {
+        // float32 sweeps: FP64 throughput is scarce on this part, so the update
+        // is two FMAs with the per-medium factors ia = (1-e) iden, ib = e B iden,
+        // and the stopping quantity is taken in float32 (within 1e-7 of it,
+        // relative) unless S is outside the float32 normal range
+        const double S = A.S64[i];
+        const double dS = fma(A.ia[i], J, fma(-S, A.iden[i], A.ib[i]));
+        const double Sn = S + dS;
+        A.S64[i] = Sn;
+        A.Sfs[i] = S;
+        const float df = (float)dS, sf = fabsf((float)Sn);
+        r = (sf > 1e-30f && sf < 1e30f && fabsf(df) < 1e30f) ? (double)__fdividef(fabsf(df), sf)
+                                                              : rel_change(dS, Sn);
+        snew = (T)(A.incremental ? df : (float)Sn);
       } else {
         const double S = A.S64[i], e = A.eps[i];
         double iden;
@@ -1579,10 +1593,17 @@ __global__ void f32_to_f64_kernel(long long n, const float *src, double *dst) {
 
 // Jacobi denominator of Eq. 24, inverted once per medium: the update then
 // multiplies instead of dividing in FP64 every iteration.
-__global__ void inv_denominator_kernel(long long n, const double *eps, const double *oml, double *iden) {
+__global__ void inv_denominator_kernel(long long n, const double *eps, const double *oml, double *iden,
+                                       const double *B, double *ia, double *ib) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    iden[i] = 1.0 / (eps[i] + (1.0 - eps[i]) * oml[i]);
+       i += (long long)gridDim.x * blockDim.x) {
+    const double d = 1.0 / (eps[i] + (1.0 - eps[i]) * oml[i]);
+    iden[i] = d;
+    if (ia) {
+      ia[i] = (1.0 - eps[i]) * d;
+      ib[i] = eps[i] * B[i] * d;
+    }
+  }
 }
 
 // Convergence decision after one ALI iteration (single thread).
@@ -2190,8 +2211,8 @@ cudaError_t launch_reduce_moments(const Dims &d, int ngroups, const T *Jpart, co
 
 
 cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
-                                   cudaStream_t s) {
-  inv_denominator_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, eps, oml, iden);
+                                   const double *B, double *ia, double *ib, cudaStream_t s) {
+  inv_denominator_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, eps, oml, iden, B, ia, ib);
   return cudaGetLastError();
 }
 

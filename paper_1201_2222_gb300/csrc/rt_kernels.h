@@ -53,6 +53,7 @@ struct AliArgs {
   int nxg;                   // the first nxg groups' partials are in the [x][z][y] layout (jx)
   const double *eps, *B;
   const double *iden;        // 1 / [eps + (1 - eps)(1 - Lambda*)], fixed for a medium
+  const double *ia, *ib;     // (1 - eps) iden and eps B iden (float32 sweeps; NULL = from eps, B)
   const T *Opart;            // second-order sweeps: group partials of 1 - Lambda* of this
                              // formal solution (used instead of iden; NULL = linear)
   double *S64, *Sfs, *J64, *Jprev;
@@ -170,8 +171,10 @@ cudaError_t launch_ghosts_from64(long long n, const double *Gout, const double *
                                  cudaStream_t s);
 cudaError_t launch_f32_to_f64(long long n, const float *src, double *dst, cudaStream_t s);
 // iden = 1 / [eps + (1 - eps)(1 - Lambda*)] (the Jacobi denominator of Eq. 24)
+// and, where ia is not NULL, the update's factors ia = (1 - eps) iden and
+// ib = eps B iden (dS = ia J + ib - S iden)
 cudaError_t launch_inv_denominator(long long n, const double *eps, const double *oml, double *iden,
-                                   cudaStream_t s);
+                                   const double *B, double *ia, double *ib, cudaStream_t s);
 cudaError_t launch_state_op(SolveState *st, int op, int a, double b, int c, cudaStream_t s);
 // xchi[2]: the ghost layers' chi [nf][ny][nx] beyond EXTERNAL z faces (NULL elsewhere)
 template <typename T>
