@@ -1450,6 +1450,7 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
   const bool inc = A.incremental && !first;
   const int x = x0 + tx;
   double rmax = 0.0;
+  float rmaxf = 0.f;   // float32 sweeps: the maximum of the quantities taken in float32
   // float32 partials are summed exactly into a float pair (TwoSum) in group
   // order; those of the first nxg groups (sweeps along x) are in the [x][z][y]
   // layout and come through a shared-memory transpose of the tile
@@ -1516,6 +1517,7 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
       // FP64 iteration's J replaces the accumulated one)
       const double J = (inc && A.Jpart) ? A.J64[i] + dJ : dJ;
       double r;
+      bool r64 = true;   // r holds this cell's quantity (else it went into rmaxf)
       if (A.lte) {
         const double Jp = A.incremental ? A.J64[i] : A.Jprev[i];
         r = first ? INFINITY : rel_change(inc ? dJ : J - Jp, J);
@@ -1532,8 +1534,13 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
         A.S64[i] = Sn;
         A.Sfs[i] = S;
         const float df = (float)dS, sf = fabsf((float)Sn);
-        r = (sf > 1e-30f && sf < 1e30f && fabsf(df) < 1e30f) ? (double)__fdividef(fabsf(df), sf)
-                                                              : rel_change(dS, Sn);
+        if (sf > 1e-30f && sf < 1e30f && fabsf(df) < 1e30f) {
+          rmaxf = fmaxf(rmaxf, __fdividef(fabsf(df), sf));   // the running maximum in float32 too
+          r = 0.0;
+          r64 = false;
+        } else {
+          r = rel_change(dS, Sn);
+        }
         snew = (T)(A.incremental ? df : (float)Sn);
       } else {
         const double S = A.S64[i], e = A.eps[i];
@@ -1557,7 +1564,7 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
         snew = (T)(A.incremental ? dS : Sn);
       }
       A.J64[i] = J;
-      rmax = fmax(rmax, r);
+      if (r64) rmax = fmax(rmax, r);
       if (A.SP[2]) A.SP[2][i] = snew;                                                 // [z][y][x]
       if (A.SP[1]) A.SP[1][fbase + ((long long)y * nz + z) * nx + x] = snew;          // [y][z][x]
     }
@@ -1571,7 +1578,7 @@ __global__ void __launch_bounds__(kAliTile * kAliRows) ali_update_kernel(const A
       if (xx < nx && yy < ny) A.SP[0][fbase + ((long long)xx * nz + z) * ny + yy] = tile[tx][ty + k * kAliRows];
     }
   }
-  block_max_to(rmax, &A.st->resid_bits);
+  block_max_to(fmax(rmax, (double)rmaxf), &A.st->resid_bits);
 }
 
 // Lagged ghosts after an FP64 formal solution done for a float32 grid: the
