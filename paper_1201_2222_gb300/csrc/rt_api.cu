@@ -1465,14 +1465,13 @@ rt_status plan_bins(rt_grid g) {
 // Mixed grids: the internal FP64 grid that does the first formal solution of
 // each Jacobi ALI solve with linear interpolation (not needed when every eps = 1,
 // whose solves only iterate the boundary ghosts).
+// Largest segment-weight table of a mixed grid's FP64-iteration grid.
+constexpr double kShadowTableMax = 16.0 * (1 << 30);
+
 rt_status plan_first64(rt_grid g) {
   g->fp64_first = !g->lte;
   if (!g->fp64_first) {
     if (g->first64) rt_destroy_grid(g->first64);
-  if (g->sub64) rt_destroy_grid(g->sub64);
-  if (g->fmask) cudaFree(g->fmask);
-  if (g->epsmin) cudaFree(g->epsmin);
-  if (g->tmp2) cudaFree(g->tmp2);
     g->first64 = nullptr;
     return RT_OK;
   }
@@ -1482,7 +1481,9 @@ rt_status plan_first64(rt_grid g) {
     rt_status r = rt_create_grid(&d, &g->first64);
     if (r != RT_OK) return r;
     g->first64->shadow = true;
-    g->first64->wt_off = true;   // one formal solution per solve: no segment-weight table
+    // a few FP64 iterations per solve: their segment weights are tabulated per
+    // medium when the table is modest (it holds E and Psi0 of every ray and cell)
+    g->first64->wt_off = 2.0 * g->na * (double)N_of(g) * 8.0 > kShadowTableMax;
   }
   rt_status r = rt_set_opacity_source(g->first64, g->chi, g->eps, g->B, g->fw, 1);
   if (r != RT_OK) return r;
@@ -1643,6 +1644,9 @@ rt_status rt_destroy_grid(rt_grid g) {
   if (!g) return RT_OK;
   if (g->own) cudaStreamSynchronize(g->own);
   if (g->first64) rt_destroy_grid(g->first64);
+  if (g->sub64) rt_destroy_grid(g->sub64);
+  for (void *p : {(void *)g->fmask, (void *)g->epsmin, (void *)g->tmp2})
+    if (p) cudaFree(p);
   void *ptrs[] = {g->chi, g->eps, g->B, g->fw, g->S, g->Sfs, g->J, g->Jprev, g->lstar, g->oml, g->iden, g->ia, g->ib,
                   g->chiP[0], g->chiP[1], g->chiP[2], g->SP[0], g->SP[1], g->SP[2], g->G[0], g->G[1],
                   g->Gd[0], g->Gd[1],
@@ -1683,7 +1687,10 @@ rt_status rt_grid_footprint(const rt_grid_desc *desc, long long *bytes) {
   if (D.prec == RT_PREC_FP64) b += 2 * na * N * 8;   // tabulated segment weights (one-cell sweep)
   // a mixed grid's internal FP64 grid for its FP64 iterations: fields, FP64
   // copies, ghosts, J partials (no moments pass, no table)
-  if (D.prec == RT_PREC_MIXED) b += 8 * N * 11 + 8 * N * 6 + 6 * D.nfreq * na * gsize * 8 + groups * N * 8;
+  if (D.prec == RT_PREC_MIXED) {
+    b += 8 * N * 11 + 8 * N * 6 + 6 * D.nfreq * na * gsize * 8 + groups * N * 8;
+    if (2.0 * na * (double)N * 8.0 <= kShadowTableMax) b += 2 * na * N * 8;   // its segment-weight table
+  }
   *bytes = b;
   return RT_OK;
 }
