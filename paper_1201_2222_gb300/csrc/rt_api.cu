@@ -478,12 +478,13 @@ void sweep_shape(rt_grid g, int variant, int slots, int C, size_t *smem, int *th
     if (variant == 3) {
       // two intensity planes per ray; chi and S rings of 3 planes (4 for the
       // second-order sweep, which also reads the downwind plane)
-      const size_t W = (size_t)rtk::pipe_row_len(Nu, rtk::kSweepSeg);
+      const int seg = g->interp == RT_INTERP_QUADRATIC ? rtk::kQuadSeg : rtk::kSweepSeg;
+      const size_t W = (size_t)rtk::pipe_row_len(Nu, seg);
       const size_t ring = g->interp == RT_INTERP_QUADRATIC ? 8 : 6;
       // plus, for the linear sweep, two buffers of prefetched ghosts per ray slot
       const size_t pre = g->interp == RT_INTERP_QUADRATIC ? 0 : (size_t)2 * slots * (Rmax + Nu);
       sm = std::max(sm, ((size_t)(2 * slots + ring) * (Rmax + 2) * W + pre) * g->tsize);
-      th = std::max(th, Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg));
+      th = std::max(th, Rmax * ((Nu + seg - 1) / seg));
     } else if (variant == 2) {
       const size_t W = (size_t)Nu + 2 + rtk::kSweepSeg;
       sm = std::max(sm, (size_t)(2 * slots + 4) * (Rmax + 2) * W * g->tsize);
@@ -648,7 +649,8 @@ void plan_groups(rt_grid g) {
         rtk::plane_axes(a, cax);
         const int Rmax = (g->d.n[cax[1]] + C - 1) / C;
         const int Nu = g->d.n[cax[0]];
-        raw_threads = std::max(raw_threads, variant >= 2 ? Rmax * ((Nu + rtk::kSweepSeg - 1) / rtk::kSweepSeg) : Rmax * Nu);
+        const int seg = g->interp == RT_INTERP_QUADRATIC ? rtk::kQuadSeg : rtk::kSweepSeg;
+        raw_threads = std::max(raw_threads, variant >= 2 ? Rmax * ((Nu + seg - 1) / seg) : Rmax * Nu);
       }
       int nres = resident_clusters(g, variant, amax_for(namax), C, threads, smem);
       if (nres <= 0) nres = 1;   // unknown occupancy: assume one resident cluster

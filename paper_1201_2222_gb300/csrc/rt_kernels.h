@@ -147,6 +147,8 @@ struct MultiSweep {
 };
 template <typename T>
 cudaError_t launch_sweep_multi(const MultiSweep<T> &M, int amax, int threads, size_t smem, cudaStream_t s);
+// cells per thread of the second-order sweep
+constexpr int kQuadSeg = 2;
 // second-order sweep (rt_quad.cu): monotonic quadratic face interpolation and
 // Bezier-controlled segment integration, chi/S staged in a four-plane ring
 template <typename T>

@@ -135,15 +135,15 @@ __device__ __forceinline__ T quad_update(const T (&Iu)[3][3], const T (&Su)[3][3
   return Im * E + a * Sm + b * S0 + c * Sc;
 }
 
-// At 512 threads (float32) the 3 x 3 stencils of chi, S and I for the upwind and
-// downwind points need more than the 128 registers a thread may hold and some
-// spill to local memory.  Capping the CTA at 384 (156 registers, no spills) or
-// 256 threads (235) was measured slower on the 128^3 x 80-ray box (6.75 and
-// 7.09 ms per sweep against 6.1 ms): 12 or 8 warps per SM hide less latency
-// than the spills cost.
+// Each thread takes segments of kQuadSeg = 2 cells: with 4-cell segments the 3 x 3
+// stencils of chi, S and I for the upwind and downwind points needed more than
+// the 128 registers a thread of a 512-thread CTA may hold and some spilled to
+// local memory (and capping the CTA at 384 or 256 threads to avoid that was
+// slower still: 12 or 8 warps per SM hide less latency); 2-cell segments fit in
+// 113 registers.
 template <typename T, int AMAX, bool MOM>
 __global__ void __launch_bounds__(sweep_max_threads<T>()) sc_sweep_quad_kernel(const SweepArgs<T> A) {
-  constexpr int SEG = kSweepSeg;
+  constexpr int SEG = kQuadSeg;
   if (A.skip_if_done && A.st->done) return;
   const int C = A.cluster;
   const int rank = blockIdx.x % C;
