@@ -1002,10 +1002,11 @@ __device__ __forceinline__ void pipe_body(const SweepArgs<T> &A, const int inst)
   };
   issue(0);
 
-  // packed-pair path with one task per thread: the J partials of a plane are
-  // stored after the plane's cluster barrier, so that the barrier's release does
-  // not wait for their global writes (they drain during the next plane)
-  const bool defer = VEC && !MOM && R * nseg <= (int)blockDim.x;
+  // packed-pair path: each task's J partials are stored at the end of the
+  // thread's next task, and its last task's of a plane after the plane's cluster
+  // barrier, so that the barrier's release does not wait for their global
+  // writes (they drain during the next task or plane)
+  const bool defer = VEC && !MOM;
   const bool jxl = VEC && !MOM && A.jx && gp.axis == 0;   // partials in this group's plane layout
   float4 Jpend = make_float4(0.f, 0.f, 0.f, 0.f);
   long long cpend = -1;
@@ -1148,10 +1149,10 @@ __device__ __forceinline__ void pipe_body(const SweepArgs<T> &A, const int inst)
         block(SignC<-1>{}, SignC<1>{}, gp.kb[2], gp.kb[3] - gp.kb[2]);
         block(SignC<1>{}, SignC<1>{}, gp.kb[3], gp.kb[4] - gp.kb[3]);
         if (active) {
+          flush_J();   // the thread's previous task of this plane, if any
           Jpend = make_float4(Jp[0].x, Jp[0].y, Jp[1].x, Jp[1].y);
           cpend = jxl ? (long long)u0 + (long long)v * Nu + (long long)w * plane
                       : (long long)(u0) * csu + (long long)v * csv + (long long)w * csw;
-          if (!defer) flush_J();
         }
       }
     } else if constexpr (VEC) {
