@@ -413,7 +413,8 @@ rt_status rt_formal_solve_noalloc(const rt_grid_desc *desc, const double *chi, c
  * frees the grid.  Solves on different workers overlap on the GPU; each result
  * is the same as that of the same solve run alone (deterministic kernels and a
  * plan that depends on the problem only; in the shared mode, alone with the
- * server's cluster size set by rt_set_sweep_config).  All calls are
+ * plan the server gives it: its cluster size set by rt_set_sweep_config, or
+ * its own plan in the largest size class).  All calls are
  * thread-safe. */
 typedef struct rt_server_s *rt_server;
 typedef struct {
@@ -425,8 +426,9 @@ typedef struct {
                                lock-step with the others of its size class (cells x rays x
                                frequencies below 2^22, below 2^26, above; one scheduler
                                thread and stream each), as in rt_ali_solve_many, each grid
-                               planned with this many CTAs per cluster where that plan
-                               fits; the workers set grids up and read results back
+                               of the two smaller classes planned with this many CTAs per
+                               cluster where that plan fits (the largest keep their own
+                               plan); the workers set grids up and read results back
                                (Gauss-Seidel and quadratic requests still run on a worker) */
 } rt_server_opts;
 typedef struct {

@@ -119,12 +119,15 @@ void run_solve(Request *r, int device) {
 
 // Shared mode: the request's grid, planned with the server's cluster size where
 // that plan fits (else the grid's own plan: it then shares launches only with
-// grids that ended up with the same one), with its medium set.
+// grids that ended up with the same one), with its medium set.  Grids of the
+// largest size class keep their own plan: they fill the GPU by themselves, and
+// the common cluster size would slow their sweeps.
 rt_status prepare_grid(Request *r, int device, int cluster) {
   cudaSetDevice(device);
   rt_status st = rt_create_grid(&r->desc, &r->g);
   if (st != RT_OK) return st;
-  if (rt_set_sweep_config(r->g, 0, cluster, 0, 3) != RT_OK) st = rt_set_sweep_config(r->g, 0, 0, 0, 0);
+  if (r->lane == kLanes - 1 || rt_set_sweep_config(r->g, 0, cluster, 0, 3) != RT_OK)
+    st = rt_set_sweep_config(r->g, 0, 0, 0, 0);
   if (st == RT_OK)
     st = rt_set_opacity_source(r->g, r->chi.data(), r->eps.data(), r->B.data(), r->fw.data(), 0);
   return st;
